@@ -1,0 +1,354 @@
+// ORACLE — test infrastructure only.
+//
+// Plain, slow, FP64 CPU implementation of the two-component Shan-Chen
+// lattice Boltzmann step with exact-flow ghost boundaries, written from the
+// paper's equations (Milan, Biferale, Sbragaglia, Toschi, "Sub-Kolmogorov
+// droplet dynamics in isotropic turbulence using a multiscale Lattice
+// Boltzmann scheme", Sec. 2 Eqs. 6-10 and Sec. 3 Eq. 14).  Only tests/,
+// __graft_entry__.smoke() and bench.py's CPU-baseline leg may load it.  It
+// shares no code, table or helper with the CUDA library.
+//
+// Every step is taken in the order the method states it, with no blocking,
+// fusion or reordering:
+//   (i)   ghost populations g_i^eq(rho_b, A(t) x) on the one-layer shell
+//         outside the box (Sec. 2, Eq. 8; Sec. 3, Eq. 14),
+//   (ii)  pull streaming g_i(x, t+1) = g*_i(x - c_i, t) (Eq. 9),
+//   (iii) component densities rho_sigma = sum_i g_i^sigma (Eq. 6),
+//   (iv)  Shan-Chen force F^sigma = -G rho_sigma sum_i w_i rho_sigma'(x+c_i) c_i
+//         (Eq. 7; out-of-box neighbours take the ghost density rho_b),
+//   (v)   common velocity u' = sum_s j_s/tau_s / sum_s rho_s/tau_s and the
+//         shifted equilibrium velocity u_s = u' + tau_s F^s / rho_s
+//         (Shan-Chen forcing, the model of Sec. 2),
+//   (vi)  BGK relaxation g* = g - (g - g^eq(rho_s, u_s)) / tau_s with
+//         nu = (tau - 1/2)/3 (Eqs. 9, 10).
+//
+// Build: g++ -O2 -ffp-contract=off -fopenmp -shared -fPIC (see build.py).
+// Loops over nodes run in parallel over z planes; every node's result is
+// independent of the thread count.  The moment and checksum sums are serial
+// and ordered z, y, x.
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// D3Q19 velocity set, in the order used throughout this repository:
+// rest, the six axis vectors (+x,-x,+y,-y,+z,-z), then the twelve
+// face diagonals, each followed by its opposite.
+const int CX[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+const int CY[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+const int CZ[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+
+double weight(int i) {
+    if (i == 0) return 1.0 / 3.0;
+    if (i <= 6) return 1.0 / 18.0;
+    return 1.0 / 36.0;
+}
+
+// Eq. 8: g_i^eq = rho w_i (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u)
+double equilibrium(int i, double rho, const double u[3]) {
+    double cu = CX[i] * u[0] + CY[i] * u[1] + CZ[i] * u[2];
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    return rho * weight(i) * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+}
+
+struct Oracle {
+    int L[3];
+    bool periodic;
+    double tau[2];
+    double G;
+    double rho_b[2];
+    std::vector<double> fpost;   // post-collision populations [2][19][z][y][x]
+    std::vector<double> fstream; // post-streaming populations, same layout
+    std::vector<double> rho;     // [2][z][y][x]
+
+    int64_t nodes() const { return (int64_t)L[0] * L[1] * L[2]; }
+    int64_t node(int x, int y, int z) const { return ((int64_t)z * L[1] + y) * L[0] + x; }
+    int64_t pidx(int s, int i, int64_t n) const { return ((int64_t)s * 19 + i) * nodes() + n; }
+    bool inside(int x, int y, int z) const {
+        return x >= 0 && x < L[0] && y >= 0 && y < L[1] && z >= 0 && z < L[2];
+    }
+    // Coordinates are measured from the box centre, where the droplet's
+    // centre of mass sits (Sec. 3, Eq. 14).
+    void position(int x, int y, int z, double p[3]) const {
+        p[0] = x - 0.5 * (L[0] - 1);
+        p[1] = y - 0.5 * (L[1] - 1);
+        p[2] = z - 0.5 * (L[2] - 1);
+    }
+    static int wrap(int a, int n) { return ((a % n) + n) % n; }
+
+    // Density of component s at (x, y, z) after streaming; nodes outside the
+    // box carry the ghost density rho_b (or the periodic image).
+    double density_at(int s, int x, int y, int z) const {
+        if (periodic) {
+            x = wrap(x, L[0]); y = wrap(y, L[1]); z = wrap(z, L[2]);
+        } else if (!inside(x, y, z)) {
+            return rho_b[s];
+        }
+        return rho[(int64_t)s * nodes() + node(x, y, z)];
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+void* orc_create(int Lx, int Ly, int Lz, int periodic, double tau_a, double tau_b, double G,
+                 double rho_b_a, double rho_b_b) {
+    Oracle* o = new Oracle();
+    o->L[0] = Lx; o->L[1] = Ly; o->L[2] = Lz;
+    o->periodic = periodic != 0;
+    o->tau[0] = tau_a; o->tau[1] = tau_b;
+    o->G = G;
+    o->rho_b[0] = rho_b_a; o->rho_b[1] = rho_b_b;
+    o->fpost.assign((size_t)(2 * 19 * o->nodes()), 0.0);
+    o->fstream.assign((size_t)(2 * 19 * o->nodes()), 0.0);
+    o->rho.assign((size_t)(2 * o->nodes()), 0.0);
+    return o;
+}
+
+void orc_destroy(void* h) { delete (Oracle*)h; }
+
+void orc_set_populations(void* h, const double* f) {
+    Oracle* o = (Oracle*)h;
+    std::memcpy(o->fpost.data(), f, o->fpost.size() * sizeof(double));
+}
+
+void orc_get_populations(void* h, double* f) {
+    Oracle* o = (Oracle*)h;
+    std::memcpy(f, o->fpost.data(), o->fpost.size() * sizeof(double));
+}
+
+// Initial state: component A (the droplet) follows a tanh profile of width
+// xi around radius R, component B its complement; every population starts at
+// the equilibrium of its local density and the linear flow u0 = A0 x.
+void orc_init_droplet(void* h, double R, double xi, double rho_hi, double rho_lo, const double* A0) {
+    Oracle* o = (Oracle*)h;
+    for (int z = 0; z < o->L[2]; ++z)
+        for (int y = 0; y < o->L[1]; ++y)
+            for (int x = 0; x < o->L[0]; ++x) {
+                double p[3];
+                o->position(x, y, z, p);
+                double r = std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+                double th = std::tanh((r - R) / xi);
+                double rho_s[2];
+                rho_s[0] = rho_lo + (rho_hi - rho_lo) * 0.5 * (1.0 - th);
+                rho_s[1] = rho_lo + (rho_hi - rho_lo) * 0.5 * (1.0 + th);
+                double u[3];
+                for (int a = 0; a < 3; ++a)
+                    u[a] = A0[3 * a + 0] * p[0] + A0[3 * a + 1] * p[1] + A0[3 * a + 2] * p[2];
+                int64_t n = o->node(x, y, z);
+                for (int s = 0; s < 2; ++s)
+                    for (int i = 0; i < 19; ++i) o->fpost[o->pidx(s, i, n)] = equilibrium(i, rho_s[s], u);
+            }
+}
+
+// One time step with the boundary gradient A (row-major, A[3*a+b] = d_b u_a).
+// If flux_in / flux_out are given, they receive per component the mass that
+// streamed in from ghost nodes and the post-collision mass that streamed out
+// of the box during this step (exact bookkeeping of the open boundary).
+void orc_step(void* h, const double* A, double* flux_in, double* flux_out) {
+    Oracle* o = (Oracle*)h;
+    const int Lx = o->L[0], Ly = o->L[1], Lz = o->L[2];
+    const int64_t N = o->nodes();
+
+    // (i)+(ii) pull streaming, with ghost equilibria outside the box.
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < Lz; ++z)
+        for (int y = 0; y < Ly; ++y)
+            for (int x = 0; x < Lx; ++x) {
+                int64_t n = o->node(x, y, z);
+                for (int s = 0; s < 2; ++s)
+                    for (int i = 0; i < 19; ++i) {
+                        int xs = x - CX[i], ys = y - CY[i], zs = z - CZ[i];
+                        double val;
+                        if (o->periodic) {
+                            int64_t m = o->node(Oracle::wrap(xs, Lx), Oracle::wrap(ys, Ly), Oracle::wrap(zs, Lz));
+                            val = o->fpost[o->pidx(s, i, m)];
+                        } else if (o->inside(xs, ys, zs)) {
+                            val = o->fpost[o->pidx(s, i, o->node(xs, ys, zs))];
+                        } else {
+                            double p[3], u[3];
+                            o->position(xs, ys, zs, p);
+                            for (int a = 0; a < 3; ++a)
+                                u[a] = A[3 * a + 0] * p[0] + A[3 * a + 1] * p[1] + A[3 * a + 2] * p[2];
+                            val = equilibrium(i, o->rho_b[s], u);
+                        }
+                        o->fstream[o->pidx(s, i, n)] = val;
+                    }
+            }
+
+    if (flux_in && flux_out) {
+        for (int s = 0; s < 2; ++s) {
+            double fin = 0.0, fout = 0.0;
+            for (int z = 0; z < Lz; ++z)
+                for (int y = 0; y < Ly; ++y)
+                    for (int x = 0; x < Lx; ++x) {
+                        int64_t n = o->node(x, y, z);
+                        for (int i = 0; i < 19; ++i) {
+                            if (o->periodic) continue;
+                            if (!o->inside(x - CX[i], y - CY[i], z - CZ[i])) fin += o->fstream[o->pidx(s, i, n)];
+                            if (!o->inside(x + CX[i], y + CY[i], z + CZ[i])) fout += o->fpost[o->pidx(s, i, n)];
+                        }
+                    }
+            flux_in[s] = fin;
+            flux_out[s] = fout;
+        }
+    }
+
+    // (iii) densities after streaming.
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < Lz; ++z)
+        for (int y = 0; y < Ly; ++y)
+            for (int x = 0; x < Lx; ++x) {
+                int64_t n = o->node(x, y, z);
+                for (int s = 0; s < 2; ++s) {
+                    double r = 0.0;
+                    for (int i = 0; i < 19; ++i) r += o->fstream[o->pidx(s, i, n)];
+                    o->rho[(int64_t)s * N + n] = r;
+                }
+            }
+
+    // (iv)-(vi) force, velocities, collision.
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < Lz; ++z)
+        for (int y = 0; y < Ly; ++y)
+            for (int x = 0; x < Lx; ++x) {
+                int64_t n = o->node(x, y, z);
+                double rho_s[2], j[2][3], F[2][3];
+                for (int s = 0; s < 2; ++s) {
+                    rho_s[s] = o->rho[(int64_t)s * N + n];
+                    j[s][0] = j[s][1] = j[s][2] = 0.0;
+                    for (int i = 0; i < 19; ++i) {
+                        double f = o->fstream[o->pidx(s, i, n)];
+                        j[s][0] += f * CX[i];
+                        j[s][1] += f * CY[i];
+                        j[s][2] += f * CZ[i];
+                    }
+                }
+                for (int s = 0; s < 2; ++s) {
+                    int sp = 1 - s;  // the other component (G_AA = G_BB = 0)
+                    double acc[3] = {0.0, 0.0, 0.0};
+                    for (int i = 1; i < 19; ++i) {
+                        double r = o->density_at(sp, x + CX[i], y + CY[i], z + CZ[i]);
+                        acc[0] += weight(i) * r * CX[i];
+                        acc[1] += weight(i) * r * CY[i];
+                        acc[2] += weight(i) * r * CZ[i];
+                    }
+                    for (int a = 0; a < 3; ++a) F[s][a] = -o->G * rho_s[s] * acc[a];
+                }
+                double den = rho_s[0] / o->tau[0] + rho_s[1] / o->tau[1];
+                double ucommon[3];
+                for (int a = 0; a < 3; ++a) ucommon[a] = (j[0][a] / o->tau[0] + j[1][a] / o->tau[1]) / den;
+                for (int s = 0; s < 2; ++s) {
+                    double ueq[3];
+                    for (int a = 0; a < 3; ++a) ueq[a] = ucommon[a] + o->tau[s] * F[s][a] / rho_s[s];
+                    for (int i = 0; i < 19; ++i) {
+                        double f = o->fstream[o->pidx(s, i, n)];
+                        double geq = equilibrium(i, rho_s[s], ueq);
+                        o->fpost[o->pidx(s, i, n)] = f - (f - geq) / o->tau[s];
+                    }
+                }
+            }
+}
+
+// Density and velocity of the stored (post-collision) populations (Eq. 6):
+// rho_s = sum_i g*_i^s, u = sum_s sum_i g*_i^s c_i / sum_s rho_s.
+void orc_fields(void* h, double* rho_a, double* rho_b, double* u) {
+    Oracle* o = (Oracle*)h;
+    const int64_t N = o->nodes();
+    for (int64_t n = 0; n < N; ++n) {
+        double r[2] = {0.0, 0.0}, m[3] = {0.0, 0.0, 0.0};
+        for (int s = 0; s < 2; ++s)
+            for (int i = 0; i < 19; ++i) {
+                double f = o->fpost[o->pidx(s, i, n)];
+                r[s] += f;
+                m[0] += f * CX[i];
+                m[1] += f * CY[i];
+                m[2] += f * CZ[i];
+            }
+        rho_a[n] = r[0];
+        rho_b[n] = r[1];
+        double tot = r[0] + r[1];
+        u[3 * n + 0] = m[0] / tot;
+        u[3 * n + 1] = m[1] / tot;
+        u[3 * n + 2] = m[2] / tot;
+    }
+}
+
+// Total mass of each component and total momentum of the stored populations.
+void orc_checksums(void* h, double* mass, double* mom) {
+    Oracle* o = (Oracle*)h;
+    const int64_t N = o->nodes();
+    mass[0] = mass[1] = 0.0;
+    mom[0] = mom[1] = mom[2] = 0.0;
+    for (int s = 0; s < 2; ++s)
+        for (int i = 0; i < 19; ++i)
+            for (int64_t n = 0; n < N; ++n) {
+                double f = o->fpost[o->pidx(s, i, n)];
+                mass[s] += f;
+                mom[0] += f * CX[i];
+                mom[1] += f * CY[i];
+                mom[2] += f * CZ[i];
+            }
+}
+
+// Ten FP64 moments of the droplet indicator w = max(phi, 0) with
+// phi = (rho_A - rho_B)/(rho_A + rho_B):
+// out = {sum w, sum w x, sum w y, sum w z, sum w xx, sum w xy, sum w xz,
+//        sum w yy, sum w yz, sum w zz}, coordinates from the box centre.
+void orc_moments(void* h, double* out) {
+    Oracle* o = (Oracle*)h;
+    for (int k = 0; k < 10; ++k) out[k] = 0.0;
+    for (int z = 0; z < o->L[2]; ++z)
+        for (int y = 0; y < o->L[1]; ++y)
+            for (int x = 0; x < o->L[0]; ++x) {
+                int64_t n = o->node(x, y, z);
+                double r[2] = {0.0, 0.0};
+                for (int s = 0; s < 2; ++s)
+                    for (int i = 0; i < 19; ++i) r[s] += o->fpost[o->pidx(s, i, n)];
+                double phi = (r[0] - r[1]) / (r[0] + r[1]);
+                double w = phi > 0.0 ? phi : 0.0;
+                double p[3];
+                o->position(x, y, z, p);
+                out[0] += w;
+                out[1] += w * p[0];
+                out[2] += w * p[1];
+                out[3] += w * p[2];
+                out[4] += w * p[0] * p[0];
+                out[5] += w * p[0] * p[1];
+                out[6] += w * p[0] * p[2];
+                out[7] += w * p[1] * p[1];
+                out[8] += w * p[1] * p[2];
+                out[9] += w * p[2] * p[2];
+            }
+}
+
+// The lattice tables, exported so tests can check them against the
+// moment identities of D3Q19 without retyping them.
+void orc_lattice(int* cx, int* cy, int* cz, double* w) {
+    for (int i = 0; i < 19; ++i) {
+        cx[i] = CX[i]; cy[i] = CY[i]; cz[i] = CZ[i];
+        w[i] = weight(i);
+    }
+}
+
+double orc_equilibrium(int i, double rho, const double* u) { return equilibrium(i, rho, u); }
+
+// Thread count of the node loops; returns the count in effect.
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+}  // extern "C"
