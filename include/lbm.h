@@ -1,0 +1,203 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) two-component Shan-Chen lattice
+ * Boltzmann solver for a droplet in an exact linear flow.
+ *
+ * The method is the multiscale scheme of Milan, Biferale, Sbragaglia and
+ * Toschi, "Sub-Kolmogorov droplet dynamics in isotropic turbulence using a
+ * multiscale Lattice Boltzmann scheme" (arXiv:2112.09972):
+ *   - two fluid components sigma = A (droplet) and B (solvent), D3Q19 lattice,
+ *     densities and momentum of Sec. 2, Eq. 6;
+ *   - Shan-Chen interaction force F^sigma of Sec. 2, Eq. 7 (psi = rho,
+ *     G_AB = G_BA = G, G_AA = G_BB = 0);
+ *   - ghost nodes one lattice layer outside the box that hold the equilibrium
+ *     of Eq. 8 at the boundary density rho_b and the linear flow u = A(t) x of
+ *     Sec. 3, Eq. 14, with x measured from the box centre (the droplet frame);
+ *   - pull streaming and BGK collision (Eq. 9) with nu = (tau - 1/2)/3
+ *     (Eq. 10), forcing by the Shan-Chen velocity shift;
+ *   - droplet deformation D = (L - W)/(L + W) (Sec. 2, Eq. 4), with L, W from
+ *     the principal second moments of the droplet indicator max(phi, 0),
+ *     phi = (rho_A - rho_B)/(rho_A + rho_B).
+ *
+ * Conventions for every call:
+ *   - Return value: an lbm_status (0 = LBM_OK).  No exception or abort ever
+ *     crosses this interface.
+ *   - Invalid arguments return LBM_EINVAL and leave the context unchanged.
+ *   - Work is enqueued on the context's CUDA stream and runs asynchronously;
+ *     a device-side fault condition (non-finite density, Mach guard) is latched
+ *     on the device and reported by the next call that synchronises
+ *     (lbm_sync, lbm_deformation, lbm_get_*, lbm_checksums, lbm_save).
+ *   - Host arrays are owned by the caller, copied in or out during the call and
+ *     never retained.  Device memory is owned by the context.
+ *   - Population layout exchanged with the host (lbm_get/set_populations):
+ *     float64 [component][direction][z][y][x], component 0 = A, 1 = B, x
+ *     fastest; directions in the D3Q19 order
+ *       0 (0,0,0); 1 (+1,0,0) 2 (-1,0,0) 3 (0,+1,0) 4 (0,-1,0) 5 (0,0,+1)
+ *       6 (0,0,-1); 7 (+1,+1,0) 8 (-1,-1,0) 9 (+1,-1,0) 10 (-1,+1,0)
+ *       11 (+1,0,+1) 12 (-1,0,-1) 13 (+1,0,-1) 14 (-1,0,+1)
+ *       15 (0,+1,+1) 16 (0,-1,-1) 17 (0,+1,-1) 18 (0,-1,+1).
+ *   - Gradients are row-major 3x3, A[3*a + b] = d u_a / d x_b.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,     /* invalid argument */
+    LBM_ENOMEM = -2,     /* device or host allocation failed */
+    LBM_ECUDA = -3,      /* a CUDA runtime call failed */
+    LBM_ENONFINITE = -4, /* a non-finite density appeared on the device */
+    LBM_EMACH = -5,      /* a ghost velocity exceeded the Mach guard */
+    LBM_ETIMEOUT = -6,   /* a bounded device-side wait gave up */
+    LBM_EIO = -7         /* checkpoint file missing, short or corrupt */
+} lbm_status;
+
+typedef enum {
+    LBM_FP64 = 0, /* populations stored and collided in float64 */
+    LBM_FP32 = 1  /* populations stored and collided in float32 */
+} lbm_precision;
+
+typedef enum {
+    LBM_BC_GHOST_LINEAR = 0, /* the paper's ghost nodes with u = A(t) x (Sec. 3) */
+    LBM_BC_PERIODIC_TEST = 1 /* periodic box with no boundary: a test mode */
+} lbm_bc;
+
+typedef struct {
+    int32_t precision;   /* lbm_precision, default LBM_FP32 */
+    int32_t bc;          /* lbm_bc, default LBM_BC_GHOST_LINEAR */
+    double rho_hi;       /* majority density of either phase; <= 0: 1.0 */
+    double rho_lo;       /* minority density; also the ghost density of A.
+                            <= 0: the flat-interface value ln(h/l) = G (h - l) */
+    double xi;           /* width of the initial tanh profile; <= 0: 1.0 */
+    double mach_limit;   /* guard on |u_ghost| / c_s; <= 0: 0.9 */
+    void* cuda_stream;   /* cudaStream_t to run on; NULL: the context creates
+                            its own non-blocking stream */
+    int32_t device;      /* CUDA device ordinal; < 0: the current device */
+    int32_t tile_y;      /* rows per CTA of the stream-collide kernel; 0: auto */
+    int32_t z_chunk;     /* z planes per CTA of the stream-collide kernel; 0: auto */
+} lbm_opts;
+
+/* Fill *opts with the defaults above. */
+void lbm_opts_default(lbm_opts* opts);
+
+/*
+ * Create a context: a box of box[0] x box[1] x box[2] fluid nodes (x, y, z),
+ * each >= 4, with a droplet of component A of radius R (0 < R, 2R <=
+ * min(box) - 2 for the ghost boundary) at the box centre, kinematic
+ * viscosities visc = {nu_A, nu_B} > 0 in lattice units (tau = 3 nu + 1/2,
+ * Eq. 10) and coupling G >= 0 (Eq. 7).  The populations start at the
+ * equilibrium of the tanh density profile rho_A = lo + (hi - lo)(1 -
+ * tanh((r - R)/xi))/2, rho_B = lo + (hi - lo)(1 + tanh((r - R)/xi))/2 and the
+ * flow u = A(0) x of the gradient table (zero until lbm_set_gradient).  The
+ * ghost densities are rho_b^A = rho_lo and rho_b^B = rho_hi (density ratio 1,
+ * Sec. 3).  Device memory: two population buffers of
+ * 38 (box[2]+2)(box[1]+2) pitch elements, pitch >= box[0] + 2.
+ * On success *out receives the context; on failure *out is NULL.
+ */
+int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[2], double G,
+               const lbm_opts* opts);
+
+/*
+ * Add a knot (t, A) to the context's velocity-gradient table.  Step n of the
+ * simulation drives the ghost nodes with A(t_n), t_n = n, linearly
+ * interpolated between knots and held constant before the first and after
+ * the last knot (the gradient "sampling time" of Sec. 4: one tracer sample
+ * every Delta t steps).  A must be traceless: |tr A| <= 1e-12 max(1, max|A_ij|),
+ * otherwise LBM_EINVAL; t must exceed the previous knot's t.  If the first
+ * knot is added before any step, the initial flow is re-initialised to
+ * A(0) x (it is the flow of the paper's initial condition).
+ */
+int lbm_set_gradient(lbm_ctx* ctx, const double A[9], int64_t t);
+
+/* Add n knots at once: t[k], A[9k .. 9k+8]; same rules as lbm_set_gradient. */
+int lbm_set_gradient_table(lbm_ctx* ctx, const int64_t* t, const double* A, int64_t n);
+
+/*
+ * Advance n >= 0 time steps.  Each step runs the ghost-boundary kernel
+ * (ghost equilibria from A(t_n) x, Eq. 8/14) and then the fused
+ * pull-stream + Shan-Chen force + collision kernel (Eqs. 6, 7, 9, 10).
+ * Asynchronous: returns once the work is enqueued.
+ */
+int lbm_step(lbm_ctx* ctx, int64_t n);
+
+/* Wait for the context's stream and report any latched device error. */
+int lbm_sync(lbm_ctx* ctx);
+
+/*
+ * Droplet deformation of the current state (Eq. 4): D = (sqrt(l1) - sqrt(l3))
+ * / (sqrt(l1) + sqrt(l3)) with l1 >= l2 >= l3 the eigenvalues of the central
+ * second-moment tensor of w = max(phi, 0).  axes (may be NULL) receives the
+ * unit principal axes as columns, axes[3*a + k] = component a of axis k, each
+ * signed so its largest-magnitude component is positive; lambda (may be NULL)
+ * receives l1, l2, l3; centre (may be NULL) the centre of mass of w.
+ * Synchronises.
+ */
+int lbm_deformation(lbm_ctx* ctx, double* D, double axes[9], double lambda[3], double centre[3]);
+
+/*
+ * The ten float64 moments of w = max(phi, 0) over the box:
+ * {sum w, sum w x, sum w y, sum w z, sum w xx, sum w xy, sum w xz, sum w yy,
+ *  sum w yz, sum w zz}, coordinates from the box centre.  Synchronises.
+ */
+int lbm_moments(lbm_ctx* ctx, double m[10]);
+
+/*
+ * Copy the fields of the current (post-collision) populations to the host
+ * (Eq. 6): rho_A[n], rho_B[n], u[3n + a] = sum_s sum_i g_i^s c_ia / (rho_A +
+ * rho_B), n = (z * box[1] + y) * box[0] + x.  Any pointer may be NULL.
+ * Synchronises.
+ */
+int lbm_get_fields(lbm_ctx* ctx, double* rho_A, double* rho_B, double* u);
+
+/* Copy all populations to / from the host (float64, layout above). */
+int lbm_get_populations(lbm_ctx* ctx, double* f);
+int lbm_set_populations(lbm_ctx* ctx, const double* f);
+
+/* float64 sums over the box: mass[s] = sum rho_s, mom[a] = sum rho u_a. */
+int lbm_checksums(lbm_ctx* ctx, double mass[2], double mom[3]);
+
+/* Step counter n of the next step (the number of steps taken so far). */
+int lbm_get_step(lbm_ctx* ctx, int64_t* step);
+
+/*
+ * Checkpoint: lbm_save writes the parameters, the step counter, the gradient
+ * table and the populations (float64) with a 64-bit FNV-1a checksum;
+ * lbm_load restores them into a context created with the same box, precision
+ * and boundary mode (LBM_EINVAL otherwise, LBM_EIO for a missing, short or
+ * corrupt file).  A resumed run is bit-identical to an uninterrupted one.
+ */
+int lbm_save(lbm_ctx* ctx, const char* path);
+int lbm_load(lbm_ctx* ctx, const char* path);
+
+/*
+ * Kernel timing: while enabled, every launch of the stream-collide kernel
+ * (kernel 0) and the ghost kernel (kernel 1) is bracketed by CUDA events on
+ * the context's stream.  lbm_profile_read synchronises and returns the summed
+ * device time in milliseconds and the number of launches since the last
+ * enable.
+ */
+int lbm_profile_enable(lbm_ctx* ctx, int enable);
+int lbm_profile_read(lbm_ctx* ctx, int kernel, double* total_ms, int64_t* launches);
+
+/* Launch shape of the stream-collide kernel in use: rows per CTA, z planes
+ * per CTA, CTAs. */
+int lbm_launch_shape(lbm_ctx* ctx, int32_t* tile_y, int32_t* z_chunk, int32_t* ctas);
+
+/* Free the context and its device memory (NULL is allowed). */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Static description of a status code. */
+const char* lbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

@@ -1,0 +1,587 @@
+// Host side of the C ABI declared in include/lbm.h: parameter validation,
+// device memory, the gradient knot table, launch orchestration, profiling
+// events and checkpoints.  Every entry point catches its own failures and
+// returns an lbm_status; nothing throws across the interface.
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbmgb;
+
+struct lbm_ctx {
+    int box[3];
+    double R, xi, rho_hi, rho_lo;
+    Model model;
+    int prec;       // 0 = fp64, 1 = fp32
+    int elem;       // bytes per stored population
+    Layout L;
+    Shape shape;
+    int device, num_sms;
+    cudaStream_t stream;
+    bool own_stream;
+    void* f[2];
+    int cur;                // buffer holding the current post-collision populations
+    bool initialised;       // populations hold a state (lazy init on first use)
+    int64_t step;           // host mirror of the step counter
+    long long* d_step;      // device step counter read by the ghost kernel
+    int* d_err;             // latched device error bits: 1 non-finite, 2 Mach
+    int* h_err;             // pinned mirror
+    int latched;            // latched status returned by later calls
+    // gradient knots
+    std::vector<double> kt, kA;
+    double* d_kt;
+    double* d_kA;
+    int d_kcap, d_kn;
+    // reduction scratch
+    double* d_partials;
+    int red_blocks;
+    double* d_result;  // 32 doubles
+    double* h_result;  // pinned
+    // profiling
+    bool prof;
+    std::vector<cudaEvent_t> ev[2];
+    int64_t prof_n[2];
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return LBM_OK;
+    if (e == cudaErrorMemoryAllocation) return LBM_ENOMEM;
+    return LBM_ECUDA;
+}
+
+#define LBM_TRY(expr)                               \
+    do {                                            \
+        cudaError_t e_ = (expr);                    \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+
+// Flat-interface minority density: ln(h/l) = G (h - l) with l < 1/G.
+double coexistence_lo(double G, double h) {
+    if (G * h <= 1.0) return -1.0;
+    double a = 1e-300, b = 1.0 / G;  // f(a) > 0 > f(b)
+    auto fn = [&](double l) { return std::log(h / l) - G * (h - l); };
+    for (int it = 0; it < 400; ++it) {
+        const double m = (a > 0 && b / a > 4.0) ? std::sqrt(a * b) : 0.5 * (a + b);
+        if (fn(m) > 0.0) a = m; else b = m;
+        if (b - a <= 1e-16 * b) break;
+    }
+    return 0.5 * (a + b);
+}
+
+int ensure_knots_on_device(lbm_ctx* c) {
+    const int n = (int)c->kt.size();
+    if (n == c->d_kn) return LBM_OK;
+    if (n > c->d_kcap) {
+        int cap = std::max(64, c->d_kcap);
+        while (cap < n) cap *= 2;
+        double *nt = nullptr, *nA = nullptr;
+        LBM_TRY(cudaStreamSynchronize(c->stream));
+        LBM_TRY(cudaMalloc(&nt, sizeof(double) * cap));
+        if (cudaMalloc(&nA, sizeof(double) * 9 * cap) != cudaSuccess) {
+            cudaFree(nt);
+            return LBM_ENOMEM;
+        }
+        cudaFree(c->d_kt);
+        cudaFree(c->d_kA);
+        c->d_kt = nt;
+        c->d_kA = nA;
+        c->d_kcap = cap;
+        c->d_kn = 0;
+    }
+    // Knots are append-only; copy the new ones synchronously (rare, small).
+    const int k0 = c->d_kn;
+    LBM_TRY(cudaMemcpyAsync(c->d_kt + k0, c->kt.data() + k0, sizeof(double) * (n - k0), cudaMemcpyHostToDevice, c->stream));
+    LBM_TRY(cudaMemcpyAsync(c->d_kA + 9 * k0, c->kA.data() + 9 * k0, sizeof(double) * 9 * (n - k0), cudaMemcpyHostToDevice, c->stream));
+    LBM_TRY(cudaStreamSynchronize(c->stream));
+    c->d_kn = n;
+    return LBM_OK;
+}
+
+Knots knots(const lbm_ctx* c) { return Knots{c->d_kt, c->d_kA, c->d_kn}; }
+
+int check_latched(lbm_ctx* c) {
+    if (c->latched) return c->latched;
+    // A Mach violation at the boundary is the usual cause of a later
+    // non-finite density, so it is reported first.
+    int bits = *c->h_err;
+    if (bits & 2) c->latched = LBM_EMACH;
+    else if (bits & 1) c->latched = LBM_ENONFINITE;
+    return c->latched;
+}
+
+// Synchronise and fold the device error word into the latched status.
+int sync_and_check(lbm_ctx* c) {
+    LBM_TRY(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LBM_TRY(cudaStreamSynchronize(c->stream));
+    return check_latched(c);
+}
+
+int lazy_init(lbm_ctx* c) {
+    if (c->initialised) return LBM_OK;
+    int st = ensure_knots_on_device(c);
+    if (st) return st;
+    LBM_TRY(launch_init(c->prec, c->f[c->cur], c->L, c->model, c->R, c->xi, c->rho_hi, c->rho_lo, knots(c), c->stream));
+    c->initialised = true;
+    return LBM_OK;
+}
+
+int set_device(lbm_ctx* c) { return cuda_status(cudaSetDevice(c->device)); }
+
+bool finite_all(const double* a, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+bool gradient_ok(const double* A) {
+    if (!finite_all(A, 9)) return false;
+    double mx = 1.0;
+    for (int j = 0; j < 9; ++j) mx = std::max(mx, std::fabs(A[j]));
+    return std::fabs(A[0] + A[4] + A[8]) <= 1e-12 * mx;
+}
+
+// 64-bit FNV-1a over a byte range.
+uint64_t fnv1a(const void* p, size_t n, uint64_t h = 1469598103934665603ULL) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ULL;
+    }
+    return h;
+}
+
+struct CkptHeader {
+    char magic[8];
+    int32_t version, box[3], prec, bc;
+    double R, xi, rho_hi, rho_lo, tau[2], G, rho_b[2];
+    int64_t step, nknots, npop;
+};
+
+}  // namespace
+
+extern "C" {
+
+void lbm_opts_default(lbm_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = LBM_FP32;
+    o->bc = LBM_BC_GHOST_LINEAR;
+    o->rho_hi = 0.0;
+    o->rho_lo = 0.0;
+    o->xi = 0.0;
+    o->mach_limit = 0.0;
+    o->cuda_stream = nullptr;
+    o->device = -1;
+    o->tile_y = 0;
+    o->z_chunk = 0;
+}
+
+const char* lbm_strerror(int code) {
+    switch (code) {
+        case LBM_OK: return "ok";
+        case LBM_EINVAL: return "invalid argument";
+        case LBM_ENOMEM: return "out of memory";
+        case LBM_ECUDA: return "CUDA runtime error";
+        case LBM_ENONFINITE: return "non-finite density on the device";
+        case LBM_EMACH: return "ghost velocity above the Mach guard";
+        case LBM_ETIMEOUT: return "bounded device wait timed out";
+        case LBM_EIO: return "checkpoint file missing, short or corrupt";
+        default: return "unknown status";
+    }
+}
+
+int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[2], double G, const lbm_opts* opts) {
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    if (!box || !visc) return LBM_EINVAL;
+    lbm_opts o;
+    lbm_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.precision != LBM_FP64 && o.precision != LBM_FP32) return LBM_EINVAL;
+    if (o.bc != LBM_BC_GHOST_LINEAR && o.bc != LBM_BC_PERIODIC_TEST) return LBM_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (box[a] < 4 || box[a] > 4096) return LBM_EINVAL;
+    const int mn = std::min(box[0], std::min(box[1], box[2]));
+    if (!(R >= 0.0) || !std::isfinite(R)) return LBM_EINVAL;
+    if (o.bc == LBM_BC_GHOST_LINEAR && 2.0 * R > mn - 2) return LBM_EINVAL;
+    if (!(visc[0] > 0.0) || !(visc[1] > 0.0) || !std::isfinite(visc[0]) || !std::isfinite(visc[1])) return LBM_EINVAL;
+    if (!(G >= 0.0) || !std::isfinite(G)) return LBM_EINVAL;
+    const double hi = o.rho_hi > 0.0 ? o.rho_hi : 1.0;
+    double lo = o.rho_lo;
+    if (!(lo > 0.0)) {
+        lo = coexistence_lo(G, hi);
+        if (!(lo > 0.0)) lo = hi;  // no phase separation: a uniform mixture
+    }
+    if (!(lo <= hi) || !std::isfinite(lo) || !std::isfinite(hi)) return LBM_EINVAL;
+    const double xi = o.xi > 0.0 ? o.xi : 1.0;
+    const double mach = o.mach_limit > 0.0 ? o.mach_limit : 0.9;
+
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ENOMEM;
+    int dev = o.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) { delete c; return LBM_ECUDA; }
+    c->device = dev;
+    if (cudaSetDevice(dev) != cudaSuccess) { delete c; return LBM_ECUDA; }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int a = 0; a < 3; ++a) c->box[a] = box[a];
+    c->R = R; c->xi = xi; c->rho_hi = hi; c->rho_lo = lo;
+    c->model.tau[0] = 3.0 * visc[0] + 0.5;  // Eq. 10
+    c->model.tau[1] = 3.0 * visc[1] + 0.5;
+    c->model.G = G;
+    c->model.rho_b[0] = lo;  // the droplet component is the minority at the boundary
+    c->model.rho_b[1] = hi;
+    c->model.periodic = o.bc == LBM_BC_PERIODIC_TEST;
+    c->model.mach2 = mach * mach / 3.0;
+    c->prec = o.precision == LBM_FP64 ? 0 : 1;
+    c->elem = c->prec == 0 ? 8 : 4;
+    c->L = make_layout(box[0], box[1], box[2], c->elem);
+    c->shape = choose_shape(c->L, c->elem, o.tile_y, o.z_chunk, c->num_sms);
+    c->cur = 0;
+    c->stream = (cudaStream_t)o.cuda_stream;
+    c->own_stream = false;
+    int st = LBM_OK;
+    if (!c->stream) {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return LBM_ECUDA; }
+        c->own_stream = true;
+    }
+    c->red_blocks = std::max(moments_blocks(c->L, c->num_sms), 1);
+    const size_t bytes = (size_t)c->L.total * c->elem;
+    cudaError_t e = cudaMalloc(&c->f[0], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->f[1], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_step, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_partials, sizeof(double) * 10 * c->red_blocks);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_result, sizeof(double) * 32);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_result, sizeof(double) * 32);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(int));
+    // Zero both buffers once: ghost entries that no direction reads stay defined.
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->f[0], 0, bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->f[1], 0, bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_step, 0, sizeof(long long), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        st = cuda_status(e);
+        lbm_destroy(c);
+        return st;
+    }
+    *c->h_err = 0;
+    *out = c;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFree(c->f[0]);
+    cudaFree(c->f[1]);
+    cudaFree(c->d_step);
+    cudaFree(c->d_err);
+    cudaFree(c->d_partials);
+    cudaFree(c->d_result);
+    cudaFree(c->d_kt);
+    cudaFree(c->d_kA);
+    if (c->h_result) cudaFreeHost(c->h_result);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    for (int k = 0; k < 2; ++k)
+        for (cudaEvent_t ev : c->ev[k]) cudaEventDestroy(ev);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int lbm_set_gradient_table(lbm_ctx* c, const int64_t* t, const double* A, int64_t n) {
+    if (!c || n < 0 || (n > 0 && (!t || !A))) return LBM_EINVAL;
+    double last = c->kt.empty() ? -INFINITY : c->kt.back();
+    for (int64_t k = 0; k < n; ++k) {
+        if (!gradient_ok(A + 9 * k)) return LBM_EINVAL;
+        if (!((double)t[k] > last)) return LBM_EINVAL;
+        last = (double)t[k];
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        c->kt.push_back((double)t[k]);
+        c->kA.insert(c->kA.end(), A + 9 * k, A + 9 * k + 9);
+    }
+    return LBM_OK;
+}
+
+int lbm_set_gradient(lbm_ctx* c, const double A[9], int64_t t) { return lbm_set_gradient_table(c, &t, A, 1); }
+
+int lbm_step(lbm_ctx* c, int64_t n) {
+    if (!c || n < 0) return LBM_EINVAL;
+    if (c->latched) return c->latched;
+    int st = set_device(c);
+    if (st) return st;
+    if ((st = lazy_init(c))) return st;
+    if ((st = ensure_knots_on_device(c))) return st;
+    for (int64_t k = 0; k < n; ++k) {
+        void* src = c->f[c->cur];
+        void* dst = c->f[1 - c->cur];
+        if (!c->model.periodic) {
+            if (c->prof) {
+                cudaEvent_t a, b;
+                cudaEventCreate(&a);
+                cudaEventCreate(&b);
+                cudaEventRecord(a, c->stream);
+                LBM_TRY(launch_ghost(c->prec, src, c->L, c->model, knots(c), c->d_step, c->d_err, c->stream));
+                cudaEventRecord(b, c->stream);
+                c->ev[1].push_back(a);
+                c->ev[1].push_back(b);
+            } else {
+                LBM_TRY(launch_ghost(c->prec, src, c->L, c->model, knots(c), c->d_step, c->d_err, c->stream));
+            }
+        }
+        if (c->prof) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            cudaEventRecord(a, c->stream);
+            LBM_TRY(launch_stream_collide(c->prec, src, dst, c->L, c->model, c->shape, c->d_step, 1, c->d_err, c->stream));
+            cudaEventRecord(b, c->stream);
+            c->ev[0].push_back(a);
+            c->ev[0].push_back(b);
+        } else {
+            LBM_TRY(launch_stream_collide(c->prec, src, dst, c->L, c->model, c->shape, c->d_step, 1, c->d_err, c->stream));
+        }
+        c->cur = 1 - c->cur;
+        c->step += 1;
+    }
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_ctx* c) {
+    if (!c) return LBM_EINVAL;
+    int st = set_device(c);
+    if (st) return st;
+    return sync_and_check(c);
+}
+
+int lbm_moments(lbm_ctx* c, double m[10]) {
+    if (!c || !m) return LBM_EINVAL;
+    int st = set_device(c);
+    if (st || (st = lazy_init(c))) return st;
+    LBM_TRY(launch_moments(c->prec, c->f[c->cur], c->L, c->d_partials, c->red_blocks, c->d_result, c->stream));
+    LBM_TRY(cudaMemcpyAsync(c->h_result, c->d_result, sizeof(double) * 26, cudaMemcpyDeviceToHost, c->stream));
+    if ((st = sync_and_check(c))) return st;
+    memcpy(m, c->h_result, sizeof(double) * 10);
+    return LBM_OK;
+}
+
+int lbm_deformation(lbm_ctx* c, double* D, double axes[9], double lambda[3], double centre[3]) {
+    if (!c || !D) return LBM_EINVAL;
+    double m[10];
+    int st = lbm_moments(c, m);
+    if (st) return st;
+    *D = c->h_result[10];
+    if (axes) memcpy(axes, c->h_result + 11, sizeof(double) * 9);
+    if (lambda) memcpy(lambda, c->h_result + 20, sizeof(double) * 3);
+    if (centre) memcpy(centre, c->h_result + 23, sizeof(double) * 3);
+    return LBM_OK;
+}
+
+int lbm_get_fields(lbm_ctx* c, double* rho_A, double* rho_B, double* u) {
+    if (!c) return LBM_EINVAL;
+    int st = set_device(c);
+    if (st || (st = lazy_init(c))) return st;
+    const size_t N = (size_t)c->box[0] * c->box[1] * c->box[2];
+    double* d = nullptr;
+    LBM_TRY(cudaMallocAsync(&d, sizeof(double) * 5 * N, c->stream));
+    cudaError_t e = launch_fields(c->prec, c->f[c->cur], c->L, d, d + N, d + 2 * N, c->stream);
+    if (e == cudaSuccess && rho_A) e = cudaMemcpyAsync(rho_A, d, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && rho_B) e = cudaMemcpyAsync(rho_B, d + N, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, d + 2 * N, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(d, c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return sync_and_check(c);
+}
+
+int lbm_get_populations(lbm_ctx* c, double* f) {
+    if (!c || !f) return LBM_EINVAL;
+    int st = set_device(c);
+    if (st || (st = lazy_init(c))) return st;
+    const size_t E = 38ull * c->box[0] * c->box[1] * c->box[2];
+    double* d = nullptr;
+    LBM_TRY(cudaMallocAsync(&d, sizeof(double) * E, c->stream));
+    cudaError_t e = launch_pack(c->prec, c->f[c->cur], c->L, d, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, sizeof(double) * E, cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(d, c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return sync_and_check(c);
+}
+
+int lbm_set_populations(lbm_ctx* c, const double* f) {
+    if (!c || !f) return LBM_EINVAL;
+    const size_t E = 38ull * c->box[0] * c->box[1] * c->box[2];
+    if (!finite_all(f, (int)std::min<size_t>(E, (size_t)INT32_MAX))) return LBM_EINVAL;
+    int st = set_device(c);
+    if (st) return st;
+    double* d = nullptr;
+    LBM_TRY(cudaMallocAsync(&d, sizeof(double) * E, c->stream));
+    cudaError_t e = cudaMemcpyAsync(d, f, sizeof(double) * E, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_unpack(c->prec, c->f[c->cur], c->L, d, c->stream);
+    cudaFreeAsync(d, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    c->initialised = true;
+    return LBM_OK;
+}
+
+int lbm_checksums(lbm_ctx* c, double mass[2], double mom[3]) {
+    if (!c) return LBM_EINVAL;
+    int st = set_device(c);
+    if (st || (st = lazy_init(c))) return st;
+    LBM_TRY(launch_checksums(c->prec, c->f[c->cur], c->L, c->d_partials, c->red_blocks, c->d_result, c->stream));
+    LBM_TRY(cudaMemcpyAsync(c->h_result, c->d_result, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->stream));
+    if ((st = sync_and_check(c))) return st;
+    if (mass) memcpy(mass, c->h_result, sizeof(double) * 2);
+    if (mom) memcpy(mom, c->h_result + 2, sizeof(double) * 3);
+    return LBM_OK;
+}
+
+int lbm_get_step(lbm_ctx* c, int64_t* step) {
+    if (!c || !step) return LBM_EINVAL;
+    *step = c->step;
+    return LBM_OK;
+}
+
+int lbm_save(lbm_ctx* c, const char* path) {
+    if (!c || !path) return LBM_EINVAL;
+    const size_t E = 38ull * c->box[0] * c->box[1] * c->box[2];
+    std::vector<double> pop;
+    try { pop.resize(E); } catch (...) { return LBM_ENOMEM; }
+    int st = lbm_get_populations(c, pop.data());
+    if (st) return st;
+    CkptHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, "LBMGB300", 8);
+    h.version = 1;
+    for (int a = 0; a < 3; ++a) h.box[a] = c->box[a];
+    h.prec = c->prec;
+    h.bc = c->model.periodic;
+    h.R = c->R; h.xi = c->xi; h.rho_hi = c->rho_hi; h.rho_lo = c->rho_lo;
+    h.tau[0] = c->model.tau[0]; h.tau[1] = c->model.tau[1];
+    h.G = c->model.G;
+    h.rho_b[0] = c->model.rho_b[0]; h.rho_b[1] = c->model.rho_b[1];
+    h.step = c->step;
+    h.nknots = (int64_t)c->kt.size();
+    h.npop = (int64_t)E;
+    uint64_t sum = fnv1a(&h, sizeof(h));
+    sum = fnv1a(c->kt.data(), sizeof(double) * c->kt.size(), sum);
+    sum = fnv1a(c->kA.data(), sizeof(double) * c->kA.size(), sum);
+    sum = fnv1a(pop.data(), sizeof(double) * E, sum);
+    FILE* fp = fopen(path, "wb");
+    if (!fp) return LBM_EIO;
+    bool ok = fwrite(&h, sizeof(h), 1, fp) == 1;
+    ok = ok && fwrite(c->kt.data(), sizeof(double), c->kt.size(), fp) == c->kt.size();
+    ok = ok && fwrite(c->kA.data(), sizeof(double), c->kA.size(), fp) == c->kA.size();
+    ok = ok && fwrite(pop.data(), sizeof(double), E, fp) == E;
+    ok = ok && fwrite(&sum, sizeof(sum), 1, fp) == 1;
+    ok = (fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : LBM_EIO;
+}
+
+int lbm_load(lbm_ctx* c, const char* path) {
+    if (!c || !path) return LBM_EINVAL;
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return LBM_EIO;
+    CkptHeader h;
+    if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 1) {
+        fclose(fp);
+        return LBM_EIO;
+    }
+    const size_t E = 38ull * c->box[0] * c->box[1] * c->box[2];
+    if (h.box[0] != c->box[0] || h.box[1] != c->box[1] || h.box[2] != c->box[2] || h.prec != c->prec ||
+        h.bc != c->model.periodic || h.npop != (int64_t)E || h.nknots < 0 || h.nknots > (1LL << 32)) {
+        fclose(fp);
+        return LBM_EINVAL;
+    }
+    std::vector<double> kt, kA, pop;
+    try {
+        kt.resize((size_t)h.nknots);
+        kA.resize((size_t)h.nknots * 9);
+        pop.resize(E);
+    } catch (...) {
+        fclose(fp);
+        return LBM_ENOMEM;
+    }
+    uint64_t stored = 0;
+    bool ok = fread(kt.data(), sizeof(double), kt.size(), fp) == kt.size();
+    ok = ok && fread(kA.data(), sizeof(double), kA.size(), fp) == kA.size();
+    ok = ok && fread(pop.data(), sizeof(double), E, fp) == E;
+    ok = ok && fread(&stored, sizeof(stored), 1, fp) == 1;
+    fclose(fp);
+    if (!ok) return LBM_EIO;
+    uint64_t sum = fnv1a(&h, sizeof(h));
+    sum = fnv1a(kt.data(), sizeof(double) * kt.size(), sum);
+    sum = fnv1a(kA.data(), sizeof(double) * kA.size(), sum);
+    sum = fnv1a(pop.data(), sizeof(double) * E, sum);
+    if (sum != stored) return LBM_EIO;
+    int st = set_device(c);
+    if (st) return st;
+    LBM_TRY(cudaStreamSynchronize(c->stream));
+    c->R = h.R; c->xi = h.xi; c->rho_hi = h.rho_hi; c->rho_lo = h.rho_lo;
+    c->model.tau[0] = h.tau[0]; c->model.tau[1] = h.tau[1];
+    c->model.G = h.G;
+    c->model.rho_b[0] = h.rho_b[0]; c->model.rho_b[1] = h.rho_b[1];
+    c->kt.swap(kt);
+    c->kA.swap(kA);
+    c->d_kn = 0;  // force a re-upload of the whole table
+    if ((st = ensure_knots_on_device(c))) return st;
+    if ((st = lbm_set_populations(c, pop.data()))) return st;
+    c->step = h.step;
+    const long long s64 = (long long)h.step;
+    LBM_TRY(cudaMemcpyAsync(c->d_step, &s64, sizeof(s64), cudaMemcpyHostToDevice, c->stream));
+    LBM_TRY(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_profile_enable(lbm_ctx* c, int enable) {
+    if (!c) return LBM_EINVAL;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (int k = 0; k < 2; ++k) {
+        for (cudaEvent_t ev : c->ev[k]) cudaEventDestroy(ev);
+        c->ev[k].clear();
+        c->prof_n[k] = 0;
+    }
+    c->prof = enable != 0;
+    return LBM_OK;
+}
+
+int lbm_profile_read(lbm_ctx* c, int kernel, double* total_ms, int64_t* launches) {
+    if (!c || kernel < 0 || kernel > 1 || !total_ms || !launches) return LBM_EINVAL;
+    cudaSetDevice(c->device);
+    LBM_TRY(cudaStreamSynchronize(c->stream));
+    double tot = 0.0;
+    const std::vector<cudaEvent_t>& v = c->ev[kernel];
+    for (size_t i = 0; i + 1 < v.size(); i += 2) {
+        float ms = 0.0f;
+        LBM_TRY(cudaEventElapsedTime(&ms, v[i], v[i + 1]));
+        tot += ms;
+    }
+    *total_ms = tot;
+    *launches = (int64_t)(v.size() / 2);
+    return LBM_OK;
+}
+
+int lbm_launch_shape(lbm_ctx* c, int32_t* tile_y, int32_t* z_chunk, int32_t* ctas) {
+    if (!c) return LBM_EINVAL;
+    if (tile_y) *tile_y = c->shape.ty;
+    if (z_chunk) *z_chunk = c->shape.zchunk;
+    if (ctas) *ctas = (int32_t)(c->shape.grid.x * c->shape.grid.y * c->shape.grid.z);
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// Internal declarations shared by the host ABI (lbm_abi.cu) and the kernel
+// translation units (lbm_step.cu, lbm_reduce.cu).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace lbmgb {
+
+// Padded structure-of-arrays population layout in device memory.
+//
+//   element (s, i, z, y, x) at  ((s*19 + i) * nz + (z + 1)) * ny + (y + 1)) * pitch + x0 + x
+//
+// for fluid nodes x in [0, Lx), y in [0, Ly), z in [0, Lz).  One ghost layer
+// surrounds the box: x = -1 .. Lx, y = -1 .. Ly, z = -1 .. Lz all have
+// storage.  x0 puts the first fluid node of every row on a 32-byte boundary,
+// and pitch (a multiple of 32 bytes) keeps every row, plane and population
+// array on that boundary.
+struct Layout {
+    int Lx, Ly, Lz;
+    int x0;           // elements before x = 0 in a row
+    int pitch;        // elements per row
+    int ny, nz;       // Ly + 2, Lz + 2
+    long long plane;  // ny * pitch
+    long long array;  // nz * plane: elements of one population array
+    long long total;  // 38 * array
+    __host__ __device__ long long at(int s, int i, int x, int y, int z) const {
+        return ((long long)(s * 19 + i) * nz + (z + 1)) * plane + (long long)(y + 1) * pitch + x0 + x;
+    }
+};
+
+Layout make_layout(int Lx, int Ly, int Lz, int elem_bytes);
+
+// Scalars of the model that every kernel needs.
+struct Model {
+    double tau[2];     // relaxation times (Eq. 10)
+    double G;          // Shan-Chen coupling (Eq. 7)
+    double rho_b[2];   // ghost densities of A and B (Sec. 3)
+    int periodic;      // 1: periodic test mode, no ghosts
+    double mach2;      // guard on |u_ghost|^2 (lattice units)
+};
+
+// Device gradient table (knots of A(t)).
+struct Knots {
+    const double* t;  // [n]
+    const double* A;  // [n][9]
+    int n;
+};
+
+// Launch shape of the stream-collide kernel.
+struct Shape {
+    int tx, ty;     // tile of the x-y plane per CTA
+    int zchunk;     // z planes marched per CTA
+    dim3 grid;
+    int threads;
+    size_t smem;
+};
+
+// ---- launchers (lbm_step.cu) ----
+Shape choose_shape(const Layout& L, int elem_bytes, int ty_req, int zchunk_req, int num_sms);
+cudaError_t launch_init(int prec, void* f, const Layout& L, const Model& m, double R, double xi,
+                        double rho_hi, double rho_lo, Knots k, cudaStream_t s);
+cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Knots k,
+                         const long long* d_step, int* d_err, cudaStream_t s);
+cudaError_t launch_stream_collide(int prec, const void* src, void* dst, const Layout& L, const Model& m,
+                                  const Shape& sh, long long* d_step, int step_inc, int* d_err,
+                                  cudaStream_t s);
+
+// ---- launchers (lbm_reduce.cu) ----
+// Ten moments of w = max(phi, 0) and the deformation: result[0..9] moments,
+// [10] D, [11..19] axes (column-major by axis), [20..22] lambda,
+// [23..25] centre.  partials: nblocks * 10 doubles of scratch.
+int moments_blocks(const Layout& L, int num_sms);
+cudaError_t launch_moments(int prec, const void* f, const Layout& L, double* partials, int nblocks,
+                           double* result, cudaStream_t s);
+cudaError_t launch_fields(int prec, const void* f, const Layout& L, double* rho_a, double* rho_b, double* u,
+                          cudaStream_t s);
+cudaError_t launch_checksums(int prec, const void* f, const Layout& L, double* partials, int nblocks,
+                             double* result5, cudaStream_t s);
+cudaError_t launch_pack(int prec, const void* f, const Layout& L, double* out, cudaStream_t s);
+cudaError_t launch_unpack(int prec, void* f, const Layout& L, const double* in, cudaStream_t s);
+
+}  // namespace lbmgb

@@ -1,0 +1,303 @@
+// Reductions and observables over the population field:
+//
+//   k_moments / k_moments_final -- the droplet's ten float64 moments of
+//       w = max(phi, 0), phi = (rho_A - rho_B)/(rho_A + rho_B), reduced with
+//       warp shuffles, then the central second-moment tensor, its eigenvalues
+//       and eigenvectors (cyclic Jacobi, float64) and the deformation
+//       D = (L - W)/(L + W) of Sec. 2, Eq. 4 with L, W proportional to
+//       sqrt(lambda_max), sqrt(lambda_min) (a uniform ellipsoid has principal
+//       second moments a_k^2 / 5);
+//   k_fields    -- rho_A, rho_B and u of the stored populations (Eq. 6);
+//   k_checksums -- float64 mass of each component and total momentum;
+//   k_pack / k_unpack -- float64 host layout <-> padded device layout.
+//
+// Reductions are deterministic: a fixed grid, a fixed in-block tree and a
+// fixed-order final pass.
+
+#include <cuda_runtime.h>
+
+#include "lbm_internal.h"
+
+namespace lbmgb {
+namespace {
+
+__host__ __device__ __forceinline__ constexpr int qx(int i) {
+    constexpr int t[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return t[i];
+}
+__host__ __device__ __forceinline__ constexpr int qy(int i) {
+    constexpr int t[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return t[i];
+}
+__host__ __device__ __forceinline__ constexpr int qz(int i) {
+    constexpr int t[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return t[i];
+}
+
+constexpr int kRedThreads = 256;
+
+// Block-wide sum of K doubles per thread; thread 0 writes them to out[0..K).
+template <int K>
+__device__ void block_sum(double (&v)[K], double* out) {
+    __shared__ double part[kRedThreads / 32][K];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double a = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        v[k] = a;
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) part[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double a = lane < kRedThreads / 32 ? part[lane][k] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) out[k] = a;
+        }
+    }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kRedThreads) k_moments(const S* __restrict__ f, Layout L, double* __restrict__ partials) {
+    double m[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) m[k] = 0.0;
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const double cx = 0.5 * (L.Lx - 1), cy = 0.5 * (L.Ly - 1), cz = 0.5 * (L.Lz - 1);
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
+        const long long b = L.at(0, 0, x, y, z);
+        double ra = 0.0, rb = 0.0;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            ra += (double)f[b + (long long)i * L.array];
+            rb += (double)f[b + (long long)(19 + i) * L.array];
+        }
+        const double phi = (ra - rb) / (ra + rb);
+        const double w = phi > 0.0 ? phi : 0.0;
+        const double px = x - cx, py = y - cy, pz = z - cz;
+        m[0] += w;
+        m[1] += w * px; m[2] += w * py; m[3] += w * pz;
+        m[4] += w * px * px; m[5] += w * px * py; m[6] += w * px * pz;
+        m[7] += w * py * py; m[8] += w * py * pz; m[9] += w * pz * pz;
+    }
+    block_sum<10>(m, partials + 10LL * blockIdx.x);
+}
+
+// Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations.  a is
+// overwritten; on return lam holds the eigenvalues and v the eigenvectors
+// (column k of v belongs to lam[k]).
+__device__ void jacobi3(double a[3][3], double lam[3], double v[3][3]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) v[i][j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        const double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
+        const double scale = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]);
+        if (off <= 1e-300 || off <= 1e-17 * scale) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (a[p][q] == 0.0) continue;
+                // rotation angle that annihilates a[p][q]
+                const double theta = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < 3; ++k) {  // A <- A J
+                    const double akp = a[k][p], akq = a[k][q];
+                    a[k][p] = c * akp - s * akq;
+                    a[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {  // A <- J^T A
+                    const double apk = a[p][k], aqk = a[q][k];
+                    a[p][k] = c * apk - s * aqk;
+                    a[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {  // V <- V J
+                    const double vkp = v[k][p], vkq = v[k][q];
+                    v[k][p] = c * vkp - s * vkq;
+                    v[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int k = 0; k < 3; ++k) lam[k] = a[k][k];
+}
+
+// Sum the per-block partials in block order, then derive D and the axes.
+__global__ void k_moments_final(const double* __restrict__ partials, int nblocks, double* __restrict__ result) {
+    const int lane = threadIdx.x;  // 32 threads
+    double m[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        double a = 0.0;
+        for (int b = lane; b < nblocks; b += 32) a += partials[10LL * b + k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        m[k] = a;
+    }
+    if (lane != 0) return;
+    for (int k = 0; k < 10; ++k) result[k] = m[k];
+    const double mass = m[0];
+    const double c[3] = {m[1] / mass, m[2] / mass, m[3] / mass};
+    double I[3][3];
+    I[0][0] = m[4] / mass - c[0] * c[0];
+    I[0][1] = I[1][0] = m[5] / mass - c[0] * c[1];
+    I[0][2] = I[2][0] = m[6] / mass - c[0] * c[2];
+    I[1][1] = m[7] / mass - c[1] * c[1];
+    I[1][2] = I[2][1] = m[8] / mass - c[1] * c[2];
+    I[2][2] = m[9] / mass - c[2] * c[2];
+    double lam[3], v[3][3];
+    jacobi3(I, lam, v);
+    // order by decreasing eigenvalue
+    int ord[3] = {0, 1, 2};
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j)
+            if (lam[ord[j]] > lam[ord[i]]) { const int tmp = ord[i]; ord[i] = ord[j]; ord[j] = tmp; }
+    for (int k = 0; k < 3; ++k) {
+        const int col = ord[k];
+        int big = 0;
+        for (int a = 1; a < 3; ++a)
+            if (fabs(v[a][col]) > fabs(v[big][col])) big = a;
+        const double sgn = v[big][col] < 0.0 ? -1.0 : 1.0;
+        for (int a = 0; a < 3; ++a) result[11 + 3 * a + k] = sgn * v[a][col];
+        result[20 + k] = lam[col];
+        result[23 + k] = c[k];
+    }
+    const double a1 = sqrt(fmax(lam[ord[0]], 0.0)), a3 = sqrt(fmax(lam[ord[2]], 0.0));
+    result[10] = (a1 - a3) / (a1 + a3);
+}
+
+template <typename S>
+__global__ void k_fields(const S* __restrict__ f, Layout L, double* __restrict__ ra_out, double* __restrict__ rb_out,
+                         double* __restrict__ u_out) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
+    const long long b = L.at(0, 0, x, y, z);
+    double r[2] = {0.0, 0.0}, j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const double v = (double)f[b + (long long)(s * 19 + i) * L.array];
+            r[s] += v;
+            j[0] += qx(i) * v; j[1] += qy(i) * v; j[2] += qz(i) * v;
+        }
+    if (ra_out) ra_out[n] = r[0];
+    if (rb_out) rb_out[n] = r[1];
+    if (u_out) {
+        const double tot = r[0] + r[1];
+        u_out[3 * n + 0] = j[0] / tot;
+        u_out[3 * n + 1] = j[1] / tot;
+        u_out[3 * n + 2] = j[2] / tot;
+    }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kRedThreads) k_checksums(const S* __restrict__ f, Layout L, double* __restrict__ partials) {
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
+        const long long b = L.at(0, 0, x, y, z);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 19; ++i) {
+                const double q = (double)f[b + (long long)(s * 19 + i) * L.array];
+                v[s] += q;
+                v[2] += qx(i) * q; v[3] += qy(i) * q; v[4] += qz(i) * q;
+            }
+    }
+    block_sum<5>(v, partials + 5LL * blockIdx.x);
+}
+
+__global__ void k_checksums_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
+    const int lane = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        double a = 0.0;
+        for (int b = lane; b < nblocks; b += 32) a += partials[5LL * b + k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) out[k] = a;
+    }
+}
+
+template <typename S>
+__global__ void k_pack(const S* __restrict__ f, Layout L, double* __restrict__ out) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 38 * N) return;
+    const int si = (int)(e / N);
+    const long long n = e - si * N;
+    const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
+    out[e] = (double)f[L.at(si / 19, si % 19, x, y, z)];
+}
+
+template <typename S>
+__global__ void k_unpack(S* __restrict__ f, Layout L, const double* __restrict__ in) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 38 * N) return;
+    const int si = (int)(e / N);
+    const long long n = e - si * N;
+    const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
+    f[L.at(si / 19, si % 19, x, y, z)] = (S)in[e];
+}
+
+}  // namespace
+
+int moments_blocks(const Layout& L, int num_sms) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    long long b = (N + kRedThreads - 1) / kRedThreads;
+    const long long cap = 4LL * (num_sms > 0 ? num_sms : 152);
+    return (int)(b < cap ? b : cap);
+}
+
+cudaError_t launch_moments(int prec, const void* f, const Layout& L, double* partials, int nblocks, double* result,
+                           cudaStream_t s) {
+    if (prec == 0) k_moments<double><<<nblocks, kRedThreads, 0, s>>>((const double*)f, L, partials);
+    else k_moments<float><<<nblocks, kRedThreads, 0, s>>>((const float*)f, L, partials);
+    k_moments_final<<<1, 32, 0, s>>>(partials, nblocks, result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields(int prec, const void* f, const Layout& L, double* ra, double* rb, double* u, cudaStream_t s) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const unsigned blocks = (unsigned)((N + 255) / 256);
+    if (prec == 0) k_fields<double><<<blocks, 256, 0, s>>>((const double*)f, L, ra, rb, u);
+    else k_fields<float><<<blocks, 256, 0, s>>>((const float*)f, L, ra, rb, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_checksums(int prec, const void* f, const Layout& L, double* partials, int nblocks, double* result5,
+                             cudaStream_t s) {
+    if (prec == 0) k_checksums<double><<<nblocks, kRedThreads, 0, s>>>((const double*)f, L, partials);
+    else k_checksums<float><<<nblocks, kRedThreads, 0, s>>>((const float*)f, L, partials);
+    k_checksums_final<<<1, 32, 0, s>>>(partials, nblocks, result5);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(int prec, const void* f, const Layout& L, double* out, cudaStream_t s) {
+    const long long E = 38LL * L.Lx * L.Ly * L.Lz;
+    const unsigned blocks = (unsigned)((E + 255) / 256);
+    if (prec == 0) k_pack<double><<<blocks, 256, 0, s>>>((const double*)f, L, out);
+    else k_pack<float><<<blocks, 256, 0, s>>>((const float*)f, L, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(int prec, void* f, const Layout& L, const double* in, cudaStream_t s) {
+    const long long E = 38LL * L.Lx * L.Ly * L.Lz;
+    const unsigned blocks = (unsigned)((E + 255) / 256);
+    if (prec == 0) k_unpack<double><<<blocks, 256, 0, s>>>((double*)f, L, in);
+    else k_unpack<float><<<blocks, 256, 0, s>>>((float*)f, L, in);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmgb

@@ -1,0 +1,450 @@
+// Time-step kernels of the two-component Shan-Chen lattice Boltzmann method
+// (Milan, Biferale, Sbragaglia, Toschi, arXiv:2112.09972, Sec. 2 Eqs. 6-10,
+// Sec. 3 Eq. 14) for sm_103a:
+//
+//   k_init            -- equilibrium initial state of a tanh droplet in u = A(0) x
+//   k_ghost           -- ghost-node rebuild: g_i^eq(rho_b, A(t) x) on the shell
+//                        one layer outside the box, for the directions that
+//                        stream into the box (Eq. 8, Eq. 14)
+//   k_stream_collide  -- fused pull streaming (Eq. 9), component densities
+//                        (Eq. 6), Shan-Chen force (Eq. 7), velocity-shift
+//                        forcing and BGK relaxation (Eqs. 9, 10)
+//
+// The stream-collide kernel is bandwidth bound (about 1.5 flop per byte), so
+// it uses no tensor cores.  Each CTA owns a TX x TY tile of the x-y plane and
+// marches along z.  The force at plane z needs the post-streaming densities
+// of planes z-1, z, z+1 including a one-node halo around the tile; those live
+// in a four-slot ring of density planes in shared memory.  The tile's own
+// populations are pulled once per plane and held in registers across one
+// plane of the march (pulled at z+1, collided at z+1 one iteration later), so
+// DRAM sees one read and one write of every population; only the halo rows
+// are pulled a second time, from L2, because the neighbouring tiles march the
+// same planes at the same time.
+
+#include <cuda_runtime.h>
+
+#include "lbm_internal.h"
+
+namespace lbmgb {
+namespace {
+
+// D3Q19 velocities in the order documented in lbm.h.  Every loop over
+// directions is unrolled, so these fold to immediates.
+__host__ __device__ __forceinline__ constexpr int cx_(int i) {
+    constexpr int t[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return t[i];
+}
+__host__ __device__ __forceinline__ constexpr int cy_(int i) {
+    constexpr int t[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return t[i];
+}
+__host__ __device__ __forceinline__ constexpr int cz_(int i) {
+    constexpr int t[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return t[i];
+}
+
+template <typename C>
+__host__ __device__ __forceinline__ constexpr C wgt(int i) {
+    return i == 0 ? C(1) / C(3) : (i < 7 ? C(1) / C(18) : C(1) / C(36));
+}
+
+// Eq. 8 with u2x = 1.5 |u|^2 precomputed.
+template <typename C>
+__device__ __forceinline__ C feq(int i, C rho, C ux, C uy, C uz, C u2x) {
+    const C cu = C(cx_(i)) * ux + C(cy_(i)) * uy + C(cz_(i)) * uz;
+    return rho * wgt<C>(i) * (C(1) + C(3) * cu + C(4.5) * cu * cu - u2x);
+}
+
+__device__ __forceinline__ int wrap(int a, int n) {
+    a = a < 0 ? a + n : a;
+    return a >= n ? a - n : a;
+}
+
+// A(t) from the knot table: linear between knots, constant outside.
+__device__ void eval_gradient(const Knots& k, double t, double A[9]) {
+    if (k.n <= 0) {
+        for (int j = 0; j < 9; ++j) A[j] = 0.0;
+        return;
+    }
+    if (t <= k.t[0]) {
+        for (int j = 0; j < 9; ++j) A[j] = k.A[j];
+        return;
+    }
+    if (t >= k.t[k.n - 1]) {
+        for (int j = 0; j < 9; ++j) A[j] = k.A[9 * (k.n - 1) + j];
+        return;
+    }
+    int lo = 0, hi = k.n - 1;  // invariant: t[lo] <= t < t[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (k.t[mid] <= t) lo = mid; else hi = mid;
+    }
+    const double w = (t - k.t[lo]) / (k.t[hi] - k.t[lo]);
+    for (int j = 0; j < 9; ++j) {
+        const double a = k.A[9 * lo + j], b = k.A[9 * hi + j];
+        A[j] = a + w * (b - a);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Initial state.
+template <typename S>
+__global__ void k_init(S* __restrict__ f, Layout L, double R, double xi, double rho_hi, double rho_lo, Knots k) {
+    __shared__ double A[9];
+    if (threadIdx.x == 0) eval_gradient(k, 0.0, A);
+    __syncthreads();
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    if (n >= N) return;
+    const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
+    const double px = x - 0.5 * (L.Lx - 1), py = y - 0.5 * (L.Ly - 1), pz = z - 0.5 * (L.Lz - 1);
+    const double r = sqrt(px * px + py * py + pz * pz);
+    const double th = tanh((r - R) / xi);
+    const double rho[2] = {rho_lo + (rho_hi - rho_lo) * 0.5 * (1.0 - th), rho_lo + (rho_hi - rho_lo) * 0.5 * (1.0 + th)};
+    const double ux = A[0] * px + A[1] * py + A[2] * pz;
+    const double uy = A[3] * px + A[4] * py + A[5] * pz;
+    const double uz = A[6] * px + A[7] * py + A[8] * pz;
+    const double u2x = 1.5 * (ux * ux + uy * uy + uz * uz);
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int i = 0; i < 19; ++i) f[L.at(s, i, x, y, z)] = (S)feq<double>(i, rho[s], ux, uy, uz, u2x);
+}
+
+// ----------------------------------------------------------------------------
+// Ghost nodes.  The shell is enumerated face by face without overlap:
+// x = -1 and x = Lx over y, z in [-1, L]; y = -1 and y = Ly over x in [0, Lx),
+// z in [-1, Lz]; z = -1 and z = Lz over x in [0, Lx), y in [0, Ly).  A ghost
+// population i is written only if it streams into the box (y + c_i inside).
+template <typename S>
+__global__ void k_ghost(S* __restrict__ f, Layout L, Model m, Knots k, const long long* __restrict__ d_step,
+                        int* __restrict__ d_err) {
+    __shared__ double A[9];
+    if (threadIdx.x == 0) eval_gradient(k, (double)(*d_step), A);
+    __syncthreads();
+    const long long nX = (long long)(L.Ly + 2) * (L.Lz + 2);
+    const long long nY = (long long)L.Lx * (L.Lz + 2);
+    const long long nZ = (long long)L.Lx * L.Ly;
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int x, y, z;
+    if (g < 2 * nX) {
+        const int side = (int)(g / nX);
+        const long long r = g - side * nX;
+        x = side ? L.Lx : -1;
+        y = (int)(r % (L.Ly + 2)) - 1;
+        z = (int)(r / (L.Ly + 2)) - 1;
+    } else if ((g -= 2 * nX) < 2 * nY) {
+        const int side = (int)(g / nY);
+        const long long r = g - side * nY;
+        y = side ? L.Ly : -1;
+        x = (int)(r % L.Lx);
+        z = (int)(r / L.Lx) - 1;
+    } else if ((g -= 2 * nY) < 2 * nZ) {
+        const int side = (int)(g / nZ);
+        const long long r = g - side * nZ;
+        z = side ? L.Lz : -1;
+        x = (int)(r % L.Lx);
+        y = (int)(r / L.Lx);
+    } else {
+        return;
+    }
+    const double px = x - 0.5 * (L.Lx - 1), py = y - 0.5 * (L.Ly - 1), pz = z - 0.5 * (L.Lz - 1);
+    const double ux = A[0] * px + A[1] * py + A[2] * pz;
+    const double uy = A[3] * px + A[4] * py + A[5] * pz;
+    const double uz = A[6] * px + A[7] * py + A[8] * pz;
+    const double usq = ux * ux + uy * uy + uz * uz;
+    const double u2x = 1.5 * usq;
+    bool any = false;
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        const int xi = x + cx_(i), yi = y + cy_(i), zi = z + cz_(i);
+        if (xi < 0 || xi >= L.Lx || yi < 0 || yi >= L.Ly || zi < 0 || zi >= L.Lz) continue;
+        any = true;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) f[L.at(s, i, x, y, z)] = (S)feq<double>(i, m.rho_b[s], ux, uy, uz, u2x);
+    }
+    if (any && usq > m.mach2) atomicOr(d_err, 2);
+}
+
+// ----------------------------------------------------------------------------
+// Fused pull-stream + Shan-Chen force + collision.
+template <typename C>
+struct ModelC {
+    C inv_tau[2], tau[2], G, rho_b[2];
+};
+
+template <typename S, typename C, bool PER>
+struct Puller {
+    const S* __restrict__ src;
+    Layout L;
+
+    // Element index of population (s, i) pulled into fluid node (x, y, z).
+    __device__ __forceinline__ long long idx(int s, int i, int x, int y, int z) const {
+        if (PER) {
+            return L.at(s, i, wrap(x - cx_(i), L.Lx), wrap(y - cy_(i), L.Ly), wrap(z - cz_(i), L.Lz));
+        }
+        return L.at(s, i, x, y, z) - ((long long)cz_(i) * L.plane + (long long)cy_(i) * L.pitch + cx_(i));
+    }
+
+    // Pull all 38 populations of fluid node (x, y, z).
+    __device__ __forceinline__ void pull(int x, int y, int z, C (&f)[2][19]) const {
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 19; ++i) f[s][i] = (C)__ldg(src + idx(s, i, x, y, z));
+    }
+
+    // Post-streaming densities at (x, y, z), any position: outside the box
+    // the ghost density (or the periodic image).
+    __device__ __forceinline__ void rho_at(int x, int y, int z, const ModelC<C>& m, C& ra, C& rb) const {
+        if (PER) {
+            x = wrap(x, L.Lx); y = wrap(y, L.Ly); z = wrap(z, L.Lz);
+        } else if (x < 0 || x >= L.Lx || y < 0 || y >= L.Ly || z < 0 || z >= L.Lz) {
+            ra = m.rho_b[0]; rb = m.rho_b[1];
+            return;
+        }
+        C a = C(0), b = C(0);
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            a += (C)__ldg(src + idx(0, i, x, y, z));
+            b += (C)__ldg(src + idx(1, i, x, y, z));
+        }
+        ra = a; rb = b;
+    }
+};
+
+template <typename S, typename C, bool PER, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, Layout L,
+                                                          ModelC<C> m, int TX, int TY, int zchunk,
+                                                          long long* __restrict__ d_step, int step_inc,
+                                                          int* __restrict__ d_err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* ring = reinterpret_cast<C*>(smem_raw);
+    const int RW = TX + 2, RS = RW * (TY + 2);
+    const int NT = TX * TY;
+    const int H = 2 * RW + 2 * TY;  // halo nodes per plane
+    const int t = threadIdx.x;
+    const int tx = t % TX, ty = t / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = x < L.Lx && y < L.Ly;
+    const int zc0 = blockIdx.z * zchunk;
+    const int zc1 = min(zc0 + zchunk, L.Lz);
+    Puller<S, C, PER> P{src, L};
+
+    auto R = [&](int slot, int s, int hx, int hy) -> C& { return ring[(slot * 2 + s) * RS + (hy + 1) * RW + (hx + 1)]; };
+
+    // Densities of the halo ring of plane z into ring slot `slot`.
+    auto halo = [&](int z, int slot) {
+        for (int h = t; h < H; h += NT) {
+            int hx, hy;
+            if (h < RW) { hx = h - 1; hy = -1; }
+            else if (h < 2 * RW) { hx = h - RW - 1; hy = TY; }
+            else if (h < 2 * RW + TY) { hx = -1; hy = h - 2 * RW; }
+            else { hx = TX; hy = h - 2 * RW - TY; }
+            C ra, rb;
+            P.rho_at(x0 + hx, y0 + hy, z, m, ra, rb);
+            R(slot, 0, hx, hy) = ra;
+            R(slot, 1, hx, hy) = rb;
+        }
+    };
+    // Densities only (tile + halo) of plane z.
+    auto rho_plane = [&](int z, int slot) {
+        C ra, rb;
+        P.rho_at(x, y, z, m, ra, rb);
+        R(slot, 0, tx, ty) = ra;
+        R(slot, 1, tx, ty) = rb;
+        halo(z, slot);
+    };
+    // Pull the tile's populations of plane z (z inside the box) into f and
+    // its densities (tile + halo) into the ring.
+    auto load_plane = [&](int z, int slot, C (&f)[2][19]) {
+        if (active) {
+            P.pull(x, y, z, f);
+            C ra = C(0), rb = C(0);
+#pragma unroll
+            for (int i = 0; i < 19; ++i) { ra += f[0][i]; rb += f[1][i]; }
+            R(slot, 0, tx, ty) = ra;
+            R(slot, 1, tx, ty) = rb;
+        } else {
+            C ra, rb;
+            P.rho_at(x, y, z, m, ra, rb);
+            R(slot, 0, tx, ty) = ra;
+            R(slot, 1, tx, ty) = rb;
+        }
+        halo(z, slot);
+    };
+
+    C fc[2][19], fn[2][19];
+    rho_plane(zc0 - 1, (zc0 - 1) & 3);
+    load_plane(zc0, zc0 & 3, fc);
+    __syncthreads();
+
+    for (int z = zc0; z < zc1; ++z) {
+        const int zn = z + 1;
+        if (zn < zc1) load_plane(zn, zn & 3, fn);
+        else rho_plane(zn, zn & 3);
+        __syncthreads();
+
+        if (active) {
+            const int s0 = (z - 1) & 3, s1 = z & 3, s2 = (z + 1) & 3;
+            const C rho[2] = {R(s1, 0, tx, ty), R(s1, 1, tx, ty)};
+            // momentum of each component (Eq. 6)
+            C j[2][3];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                C jx = C(0), jy = C(0), jz = C(0);
+#pragma unroll
+                for (int i = 1; i < 19; ++i) {
+                    if (cx_(i)) jx += C(cx_(i)) * fc[s][i];
+                    if (cy_(i)) jy += C(cy_(i)) * fc[s][i];
+                    if (cz_(i)) jz += C(cz_(i)) * fc[s][i];
+                }
+                j[s][0] = jx; j[s][1] = jy; j[s][2] = jz;
+            }
+            // Shan-Chen force (Eq. 7): F^s = -G rho_s sum_i w_i rho_s'(x + c_i) c_i
+            C acc[2][3] = {{C(0), C(0), C(0)}, {C(0), C(0), C(0)}};
+#pragma unroll
+            for (int i = 1; i < 19; ++i) {
+                const int sl = cz_(i) == 0 ? s1 : (cz_(i) > 0 ? s2 : s0);
+                const C wa = wgt<C>(i) * R(sl, 0, tx + cx_(i), ty + cy_(i));
+                const C wb = wgt<C>(i) * R(sl, 1, tx + cx_(i), ty + cy_(i));
+                if (cx_(i)) { acc[0][0] += C(cx_(i)) * wa; acc[1][0] += C(cx_(i)) * wb; }
+                if (cy_(i)) { acc[0][1] += C(cy_(i)) * wa; acc[1][1] += C(cy_(i)) * wb; }
+                if (cz_(i)) { acc[0][2] += C(cz_(i)) * wa; acc[1][2] += C(cz_(i)) * wb; }
+            }
+            // common velocity u' and per-component shifted velocity
+            const C den = rho[0] * m.inv_tau[0] + rho[1] * m.inv_tau[1];
+            C up[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) up[a] = (j[0][a] * m.inv_tau[0] + j[1][a] * m.inv_tau[1]) / den;
+            if (!(isfinite(rho[0]) && isfinite(rho[1]))) atomicOr(d_err, 1);
+            const long long base = L.at(0, 0, x, y, z);
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                // F^s / rho_s = -G * (sum over the other component)
+                const C sh = -m.G * m.tau[s];
+                const C ux = up[0] + sh * acc[1 - s][0];
+                const C uy = up[1] + sh * acc[1 - s][1];
+                const C uz = up[2] + sh * acc[1 - s][2];
+                const C u2x = C(1.5) * (ux * ux + uy * uy + uz * uz);
+#pragma unroll
+                for (int i = 0; i < 19; ++i) {
+                    const C f = fc[s][i];
+                    const C g = feq<C>(i, rho[s], ux, uy, uz, u2x);
+                    dst[base + (long long)(s * 19 + i) * L.array] = (S)(f - (f - g) * m.inv_tau[s]);
+                }
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 19; ++i) fc[s][i] = fn[s][i];
+    }
+    if (step_inc && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t == 0) *d_step += 1;
+}
+
+template <typename C>
+ModelC<C> model_c(const Model& m) {
+    ModelC<C> r;
+    for (int s = 0; s < 2; ++s) {
+        r.tau[s] = (C)m.tau[s];
+        r.inv_tau[s] = (C)(1.0 / m.tau[s]);
+        r.rho_b[s] = (C)m.rho_b[s];
+    }
+    r.G = (C)m.G;
+    return r;
+}
+
+template <typename S, typename C, int MAXT>
+cudaError_t stream_collide_t(const void* src, void* dst, const Layout& L, const Model& m, const Shape& sh,
+                             long long* d_step, int step_inc, int* d_err, cudaStream_t s) {
+    const ModelC<C> mc = model_c<C>(m);
+    if (m.periodic) {
+        auto k = k_stream_collide<S, C, true, MAXT>;
+        if (sh.smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+        k<<<sh.grid, sh.threads, sh.smem, s>>>((const S*)src, (S*)dst, L, mc, sh.tx, sh.ty, sh.zchunk, d_step,
+                                               step_inc, d_err);
+    } else {
+        auto k = k_stream_collide<S, C, false, MAXT>;
+        if (sh.smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+        k<<<sh.grid, sh.threads, sh.smem, s>>>((const S*)src, (S*)dst, L, mc, sh.tx, sh.ty, sh.zchunk, d_step,
+                                               step_inc, d_err);
+    }
+    return cudaGetLastError();
+}
+
+constexpr int kMaxThreadsF32 = 512;
+constexpr int kMaxThreadsF64 = 256;
+
+}  // namespace
+
+Layout make_layout(int Lx, int Ly, int Lz, int elem_bytes) {
+    Layout L;
+    L.Lx = Lx; L.Ly = Ly; L.Lz = Lz;
+    const int align = 32 / elem_bytes;  // elements per 32-byte sector
+    L.x0 = align;
+    L.pitch = ((L.x0 + Lx + 1 + align - 1) / align) * align;
+    L.ny = Ly + 2;
+    L.nz = Lz + 2;
+    L.plane = (long long)L.ny * L.pitch;
+    L.array = (long long)L.nz * L.plane;
+    L.total = 38LL * L.array;
+    return L;
+}
+
+Shape choose_shape(const Layout& L, int elem_bytes, int ty_req, int zchunk_req, int num_sms) {
+    Shape sh;
+    const int maxt = elem_bytes == 8 ? kMaxThreadsF64 : kMaxThreadsF32;
+    sh.tx = L.Lx <= maxt ? L.Lx : 128;
+    if (sh.tx > maxt) sh.tx = maxt;
+    int ty = ty_req > 0 ? ty_req : maxt / sh.tx;
+    if (ty < 1) ty = 1;
+    while (ty > 1 && sh.tx * ty > maxt) --ty;
+    if (ty > L.Ly) ty = L.Ly;
+    sh.ty = ty;
+    const int tiles = ((L.Lx + sh.tx - 1) / sh.tx) * ((L.Ly + sh.ty - 1) / sh.ty);
+    int zc = zchunk_req;
+    if (zc <= 0) {
+        const int want = 2 * (num_sms > 0 ? num_sms : 152);
+        int chunks = (want + tiles - 1) / tiles;
+        if (chunks < 1) chunks = 1;
+        zc = (L.Lz + chunks - 1) / chunks;
+        if (zc < 4) zc = 4;
+    }
+    if (zc > L.Lz) zc = L.Lz;
+    sh.zchunk = zc;
+    sh.grid = dim3((L.Lx + sh.tx - 1) / sh.tx, (L.Ly + sh.ty - 1) / sh.ty, (L.Lz + zc - 1) / zc);
+    sh.threads = sh.tx * sh.ty;
+    sh.smem = (size_t)4 * 2 * (sh.tx + 2) * (sh.ty + 2) * elem_bytes;
+    return sh;
+}
+
+cudaError_t launch_init(int prec, void* f, const Layout& L, const Model& m, double R, double xi, double rho_hi,
+                        double rho_lo, Knots k, cudaStream_t s) {
+    (void)m;
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const int T = 256;
+    const unsigned blocks = (unsigned)((N + T - 1) / T);
+    if (prec == 0) k_init<double><<<blocks, T, 0, s>>>((double*)f, L, R, xi, rho_hi, rho_lo, k);
+    else k_init<float><<<blocks, T, 0, s>>>((float*)f, L, R, xi, rho_hi, rho_lo, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Knots k, const long long* d_step,
+                         int* d_err, cudaStream_t s) {
+    const long long n = 2LL * (L.Ly + 2) * (L.Lz + 2) + 2LL * L.Lx * (L.Lz + 2) + 2LL * L.Lx * L.Ly;
+    const int T = 256;
+    const unsigned blocks = (unsigned)((n + T - 1) / T);
+    if (prec == 0) k_ghost<double><<<blocks, T, 0, s>>>((double*)f, L, m, k, d_step, d_err);
+    else k_ghost<float><<<blocks, T, 0, s>>>((float*)f, L, m, k, d_step, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_collide(int prec, const void* src, void* dst, const Layout& L, const Model& m,
+                                  const Shape& sh, long long* d_step, int step_inc, int* d_err, cudaStream_t s) {
+    if (prec == 0) return stream_collide_t<double, double, kMaxThreadsF64>(src, dst, L, m, sh, d_step, step_inc, d_err, s);
+    return stream_collide_t<float, float, kMaxThreadsF32>(src, dst, L, m, sh, d_step, step_inc, d_err, s);
+}
+
+}  // namespace lbmgb

@@ -1,0 +1,252 @@
+"""Thin Python binding of the C ABI in ``include/lbm.h`` (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``_build/liblbm_gb300.so``;
+this module only converts arguments.  There is no CPU fallback: if the
+library is missing or cannot be loaded, importing the functions raises.
+
+The raw entry points keep the C names (``lbm_create``, ``lbm_set_gradient``,
+``lbm_step``, ``lbm_deformation`` ...); ``DropletLBM`` wraps them with numpy
+arrays and raises ``LBMError`` on a non-zero status.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "liblbm_gb300.so")
+
+LBM_FP64, LBM_FP32 = 0, 1
+LBM_BC_GHOST_LINEAR, LBM_BC_PERIODIC_TEST = 0, 1
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32}
+
+# Every function the header declares, for the export check.
+ABI_FUNCTIONS = [
+    "lbm_opts_default", "lbm_create", "lbm_set_gradient", "lbm_set_gradient_table", "lbm_step", "lbm_sync",
+    "lbm_deformation", "lbm_moments", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
+    "lbm_checksums", "lbm_get_step", "lbm_save", "lbm_load", "lbm_profile_enable", "lbm_profile_read",
+    "lbm_launch_shape", "lbm_destroy", "lbm_strerror",
+]
+
+
+class lbm_opts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("bc", ctypes.c_int32),
+        ("rho_hi", ctypes.c_double),
+        ("rho_lo", ctypes.c_double),
+        ("xi", ctypes.c_double),
+        ("mach_limit", ctypes.c_double),
+        ("cuda_stream", ctypes.c_void_p),
+        ("device", ctypes.c_int32),
+        ("tile_y", ctypes.c_int32),
+        ("z_chunk", ctypes.c_int32),
+    ]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+_lib = None
+_DP = ctypes.POINTER(ctypes.c_double)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+
+
+def load_library(path=LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    sig = {
+        "lbm_opts_default": (None, [ctypes.POINTER(lbm_opts)]),
+        "lbm_create": (ctypes.c_int, [ctypes.POINTER(vp), _I32P, ctypes.c_double, _DP, ctypes.c_double,
+                                      ctypes.POINTER(lbm_opts)]),
+        "lbm_set_gradient": (ctypes.c_int, [vp, _DP, ctypes.c_int64]),
+        "lbm_set_gradient_table": (ctypes.c_int, [vp, _I64P, _DP, ctypes.c_int64]),
+        "lbm_step": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "lbm_sync": (ctypes.c_int, [vp]),
+        "lbm_deformation": (ctypes.c_int, [vp, _DP, _DP, _DP, _DP]),
+        "lbm_moments": (ctypes.c_int, [vp, _DP]),
+        "lbm_get_fields": (ctypes.c_int, [vp, _DP, _DP, _DP]),
+        "lbm_get_populations": (ctypes.c_int, [vp, _DP]),
+        "lbm_set_populations": (ctypes.c_int, [vp, _DP]),
+        "lbm_checksums": (ctypes.c_int, [vp, _DP, _DP]),
+        "lbm_get_step": (ctypes.c_int, [vp, _I64P]),
+        "lbm_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
+        "lbm_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
+        "lbm_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lbm_profile_read": (ctypes.c_int, [vp, ctypes.c_int, _DP, _I64P]),
+        "lbm_launch_shape": (ctypes.c_int, [vp, _I32P, _I32P, _I32P]),
+        "lbm_destroy": (None, [vp]),
+        "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(code):
+    return load_library().lbm_strerror(int(code)).decode()
+
+
+def _check(code, what):
+    if code != 0:
+        raise LBMError(code, what)
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_DP)
+
+
+def current_torch_stream():
+    """The current torch CUDA stream handle, or None if torch has no CUDA."""
+    try:
+        import torch
+    except ImportError:
+        return None
+    if not torch.cuda.is_available():
+        return None
+    return torch.cuda.current_stream().cuda_stream
+
+
+class DropletLBM:
+    """A droplet box behind the C ABI.
+
+    ``box`` is (Lx, Ly, Lz) or an int; ``visc`` (nu_A, nu_B) in lattice units;
+    ``precision`` "fp32" or "fp64"; ``periodic`` selects the periodic test
+    mode instead of the ghost-node boundary.
+    """
+
+    def __init__(self, box, R, visc, G, precision="fp32", periodic=False, rho_hi=0.0, rho_lo=0.0, xi=0.0,
+                 mach_limit=0.0, stream=None, device=-1, tile_y=0, z_chunk=0):
+        lib = load_library()
+        self._lib = lib
+        if isinstance(box, int):
+            box = (box, box, box)
+        self.box = tuple(int(v) for v in box)
+        self.nodes = self.box[0] * self.box[1] * self.box[2]
+        o = lbm_opts()
+        lib.lbm_opts_default(ctypes.byref(o))
+        o.precision = PRECISIONS[precision]
+        o.bc = LBM_BC_PERIODIC_TEST if periodic else LBM_BC_GHOST_LINEAR
+        o.rho_hi, o.rho_lo, o.xi, o.mach_limit = float(rho_hi), float(rho_lo), float(xi), float(mach_limit)
+        if stream is None:
+            stream = current_torch_stream()
+        o.cuda_stream = stream
+        o.device = int(device)
+        o.tile_y, o.z_chunk = int(tile_y), int(z_chunk)
+        b = (ctypes.c_int32 * 3)(*self.box)
+        v = (ctypes.c_double * 2)(float(visc[0]), float(visc[1]))
+        h = ctypes.c_void_p()
+        _check(lib.lbm_create(ctypes.byref(h), b, float(R), v, float(G), ctypes.byref(o)), "lbm_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        Lx, Ly, Lz = self.box
+        return (2, 19, Lz, Ly, Lx)
+
+    def set_gradient(self, A, t):
+        A = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(9))
+        _check(self._lib.lbm_set_gradient(self._h, _dptr(A), int(t)), "lbm_set_gradient")
+
+    def set_gradient_table(self, t, A):
+        t = np.ascontiguousarray(np.asarray(t, dtype=np.int64).reshape(-1))
+        A = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(-1, 9))
+        _check(self._lib.lbm_set_gradient_table(self._h, t.ctypes.data_as(_I64P), _dptr(A), int(t.size)),
+               "lbm_set_gradient_table")
+
+    def step(self, n=1):
+        _check(self._lib.lbm_step(self._h, int(n)), "lbm_step")
+
+    def sync(self):
+        _check(self._lib.lbm_sync(self._h), "lbm_sync")
+
+    def deformation(self):
+        """(D, axes[3,3] columns, lambda[3], centre[3])."""
+        D = np.zeros(1)
+        axes = np.zeros(9)
+        lam = np.zeros(3)
+        c = np.zeros(3)
+        _check(self._lib.lbm_deformation(self._h, _dptr(D), _dptr(axes), _dptr(lam), _dptr(c)), "lbm_deformation")
+        return float(D[0]), axes.reshape(3, 3), lam, c
+
+    def moments(self):
+        m = np.zeros(10)
+        _check(self._lib.lbm_moments(self._h, _dptr(m)), "lbm_moments")
+        return m
+
+    def fields(self):
+        Lx, Ly, Lz = self.box
+        ra = np.zeros(self.nodes)
+        rb = np.zeros(self.nodes)
+        u = np.zeros(3 * self.nodes)
+        _check(self._lib.lbm_get_fields(self._h, _dptr(ra), _dptr(rb), _dptr(u)), "lbm_get_fields")
+        return ra.reshape(Lz, Ly, Lx), rb.reshape(Lz, Ly, Lx), u.reshape(Lz, Ly, Lx, 3)
+
+    def populations(self):
+        f = np.zeros(self.shape)
+        _check(self._lib.lbm_get_populations(self._h, _dptr(f)), "lbm_get_populations")
+        return f
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(self.shape))
+        _check(self._lib.lbm_set_populations(self._h, _dptr(f)), "lbm_set_populations")
+
+    def checksums(self):
+        mass = np.zeros(2)
+        mom = np.zeros(3)
+        _check(self._lib.lbm_checksums(self._h, _dptr(mass), _dptr(mom)), "lbm_checksums")
+        return mass, mom
+
+    def step_count(self):
+        s = ctypes.c_int64()
+        _check(self._lib.lbm_get_step(self._h, ctypes.byref(s)), "lbm_get_step")
+        return s.value
+
+    def save(self, path):
+        _check(self._lib.lbm_save(self._h, str(path).encode()), "lbm_save")
+
+    def load(self, path):
+        _check(self._lib.lbm_load(self._h, str(path).encode()), "lbm_load")
+
+    def profile(self, enable=True):
+        _check(self._lib.lbm_profile_enable(self._h, int(bool(enable))), "lbm_profile_enable")
+
+    def profile_read(self, kernel=0):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(self._lib.lbm_profile_read(self._h, int(kernel), ctypes.byref(ms), ctypes.byref(n)), "lbm_profile_read")
+        return ms.value, n.value
+
+    def launch_shape(self):
+        ty, zc, ctas = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.lbm_launch_shape(self._h, ctypes.byref(ty), ctypes.byref(zc), ctypes.byref(ctas)),
+               "lbm_launch_shape")
+        return ty.value, zc.value, ctas.value
