@@ -11,7 +11,8 @@
  *     G_AB = G_BA = G, G_AA = G_BB = 0);
  *   - ghost nodes one lattice layer outside the box that hold the equilibrium
  *     of Eq. 8 at the boundary density rho_b and the linear flow u = A(t) x of
- *     Sec. 3, Eq. 14, with x measured from the box centre (the droplet frame);
+ *     Sec. 3, Eq. 14, with x measured from the droplet's centre of mass (the
+ *     droplet frame, lbm_frame) or from the box centre;
  *   - pull streaming and BGK collision (Eq. 9) with nu = (tau - 1/2)/3
  *     (Eq. 10), forcing by the Shan-Chen velocity shift;
  *   - droplet deformation D = (L - W)/(L + W) (Sec. 2, Eq. 4), with L, W from
@@ -69,6 +70,16 @@ typedef enum {
     LBM_BC_PERIODIC_TEST = 1 /* periodic box with no boundary: a test mode */
 } lbm_bc;
 
+typedef enum {
+    /* x in the ghost flow A(t) x is measured from the droplet's centre of
+       mass, recomputed before every step from the current state (the frame
+       of Sec. 3, Eq. 14, in which the droplet's centre stays fixed); the box
+       centre when there is no droplet (sum of max(phi, 0) is zero) */
+    LBM_FRAME_DROPLET = 0,
+    /* x is measured from the box centre */
+    LBM_FRAME_BOX = 1
+} lbm_frame;
+
 typedef struct {
     int32_t precision;   /* lbm_precision, default LBM_FP32 */
     int32_t bc;          /* lbm_bc, default LBM_BC_GHOST_LINEAR */
@@ -82,6 +93,7 @@ typedef struct {
     int32_t device;      /* CUDA device ordinal; < 0: the current device */
     int32_t tile_y;      /* rows per CTA of the stream-collide kernel; 0: auto */
     int32_t z_chunk;     /* z planes per CTA of the stream-collide kernel; 0: auto */
+    int32_t frame;       /* lbm_frame, default LBM_FRAME_DROPLET */
 } lbm_opts;
 
 /* Fill *opts with the defaults above. */
@@ -121,8 +133,10 @@ int lbm_set_gradient_table(lbm_ctx* ctx, const int64_t* t, const double* A, int6
 
 /*
  * Advance n >= 0 time steps.  Each step runs the ghost-boundary kernel
- * (ghost equilibria from A(t_n) x, Eq. 8/14) and then the fused
- * pull-stream + Shan-Chen force + collision kernel (Eqs. 6, 7, 9, 10).
+ * (ghost equilibria from A(t_n) (x - x_c), Eq. 8/14, x_c the frame origin of
+ * lbm_frame) and then the fused pull-stream + Shan-Chen force + collision
+ * kernel (Eqs. 6, 7, 9, 10), which also accumulates the droplet's centre of
+ * mass of the state it writes for the next step's frame.
  * Asynchronous: returns once the work is enqueued.
  */
 int lbm_step(lbm_ctx* ctx, int64_t n);

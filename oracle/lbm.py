@@ -28,7 +28,7 @@ def _load():
         lib.orc_set_populations.argtypes = [ctypes.c_void_p, _DP]
         lib.orc_get_populations.argtypes = [ctypes.c_void_p, _DP]
         lib.orc_init_droplet.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 4 + [_DP]
-        lib.orc_step.argtypes = [ctypes.c_void_p, _DP, _DP, _DP]
+        lib.orc_step.argtypes = [ctypes.c_void_p, _DP, _DP, _DP, _DP]
         lib.orc_fields.argtypes = [ctypes.c_void_p, _DP, _DP, _DP]
         lib.orc_checksums.argtypes = [ctypes.c_void_p, _DP, _DP]
         lib.orc_moments.argtypes = [ctypes.c_void_p, _DP]
@@ -91,15 +91,24 @@ class OracleLBM:
     ``periodic=False`` is the paper's setup: ghost nodes one layer outside the
     box hold g^eq(rho_b, A(t) x) (Sec. 2, Eq. 8; Sec. 3, Eq. 14).
     ``periodic=True`` is a test mode with no boundary at all.
+
+    ``frame="droplet"`` measures x in the ghost flow A(t) x from the droplet's
+    centre of mass (the frame of Sec. 3, Eq. 14: "the droplet's centre of mass
+    remains fixed ... linear in the distance from the droplet's centre of
+    mass"), recomputed from the stored populations before every step;
+    ``frame="box"`` measures it from the box centre.
     """
 
-    def __init__(self, box, tau, G, rho_b, periodic=False):
+    def __init__(self, box, tau, G, rho_b, periodic=False, frame="droplet"):
         self.box = tuple(int(v) for v in box)
         self.nodes = self.box[0] * self.box[1] * self.box[2]
         self.tau = (float(tau[0]), float(tau[1]))
         self.G = float(G)
         self.rho_b = (float(rho_b[0]), float(rho_b[1]))
         self.periodic = bool(periodic)
+        if frame not in ("droplet", "box"):
+            raise ValueError(frame)
+        self.frame = frame
         self._lib = _load()
         self._h = self._lib.orc_create(
             self.box[0], self.box[1], self.box[2], int(self.periodic),
@@ -131,16 +140,28 @@ class OracleLBM:
         self._lib.orc_get_populations(self._h, _ptr(f))
         return f
 
+    def centre_of_mass(self):
+        """Centre of mass of w = max(phi, 0) of the stored populations (box-centred
+        coordinates); the box centre (0, 0, 0) when there is no droplet (sum w = 0)."""
+        m = self.moments()
+        if not m[0] > 0.0:
+            return np.zeros(3)
+        return m[1:4] / m[0]
+
     def step(self, A=None, fluxes=False):
         """One step with boundary gradient A (row-major A[a,b] = d_b u_a)."""
         A = np.zeros(9) if A is None else np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(9))
+        c = None
+        if self.frame == "droplet" and not self.periodic:
+            c = np.ascontiguousarray(self.centre_of_mass())
+        cp = None if c is None else _ptr(c)
         if fluxes:
             fin = np.zeros(2)
             fout = np.zeros(2)
-            self._lib.orc_step(self._h, _ptr(A), _ptr(fin), _ptr(fout))
+            self._lib.orc_step(self._h, _ptr(A), cp, _ptr(fin), _ptr(fout))
             self.step_count += 1
             return fin, fout
-        self._lib.orc_step(self._h, _ptr(A), None, None)
+        self._lib.orc_step(self._h, _ptr(A), cp, None, None)
         self.step_count += 1
         return None
 

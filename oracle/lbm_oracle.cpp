@@ -149,10 +149,13 @@ void orc_init_droplet(void* h, double R, double xi, double rho_hi, double rho_lo
 }
 
 // One time step with the boundary gradient A (row-major, A[3*a+b] = d_b u_a).
+// The ghost flow is u = A (x - x_c): linear in the distance from the frame
+// origin x_c (Sec. 3, Eq. 14), which is the droplet's centre of mass when
+// `centre` is given and the box centre when it is NULL.
 // If flux_in / flux_out are given, they receive per component the mass that
 // streamed in from ghost nodes and the post-collision mass that streamed out
 // of the box during this step (exact bookkeeping of the open boundary).
-void orc_step(void* h, const double* A, double* flux_in, double* flux_out) {
+void orc_step(void* h, const double* A, const double* centre, double* flux_in, double* flux_out) {
     Oracle* o = (Oracle*)h;
     const int Lx = o->L[0], Ly = o->L[1], Lz = o->L[2];
     const int64_t N = o->nodes();
@@ -175,6 +178,8 @@ void orc_step(void* h, const double* A, double* flux_in, double* flux_out) {
                         } else {
                             double p[3], u[3];
                             o->position(xs, ys, zs, p);
+                            if (centre)
+                                for (int a = 0; a < 3; ++a) p[a] -= centre[a];
                             for (int a = 0; a < 3; ++a)
                                 u[a] = A[3 * a + 0] * p[0] + A[3 * a + 1] * p[1] + A[3 * a + 2] * p[2];
                             val = equilibrium(i, o->rho_b[s], u);

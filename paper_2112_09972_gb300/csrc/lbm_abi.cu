@@ -42,6 +42,8 @@ struct lbm_ctx {
     double* d_kt;
     double* d_kA;
     int d_kcap, d_kn;
+    // per-CTA droplet moments of the current state (frame origin of the next step)
+    CentreParts centre;
     // reduction scratch
     double* d_partials;
     int red_blocks;
@@ -133,6 +135,7 @@ int lazy_init(lbm_ctx* c) {
     int st = ensure_knots_on_device(c);
     if (st) return st;
     LBM_TRY(launch_init(c->prec, c->f[c->cur], c->L, c->model, c->R, c->xi, c->rho_hi, c->rho_lo, knots(c), c->stream));
+    LBM_TRY(launch_centre(c->prec, c->f[c->cur], c->L, c->centre, c->stream));
     c->initialised = true;
     return LBM_OK;
 }
@@ -166,7 +169,7 @@ struct CkptHeader {
     char magic[8];
     int32_t version, box[3], prec, bc;
     double R, xi, rho_hi, rho_lo, tau[2], G, rho_b[2];
-    int64_t step, nknots, npop;
+    int64_t step, nknots, npop, ncentre;
 };
 
 }  // namespace
@@ -211,6 +214,7 @@ int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[
     if (opts) o = *opts;
     if (o.precision != LBM_FP64 && o.precision != LBM_FP32) return LBM_EINVAL;
     if (o.bc != LBM_BC_GHOST_LINEAR && o.bc != LBM_BC_PERIODIC_TEST) return LBM_EINVAL;
+    if (o.frame != LBM_FRAME_DROPLET && o.frame != LBM_FRAME_BOX) return LBM_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (box[a] < 4 || box[a] > 4096) return LBM_EINVAL;
     const int mn = std::min(box[0], std::min(box[1], box[2]));
@@ -244,6 +248,7 @@ int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[
     c->model.rho_b[1] = hi;
     c->model.periodic = o.bc == LBM_BC_PERIODIC_TEST;
     c->model.mach2 = mach * mach / 3.0;
+    c->model.droplet_frame = o.frame == LBM_FRAME_DROPLET;
     c->prec = o.precision == LBM_FP64 ? 0 : 1;
     c->elem = c->prec == 0 ? 8 : 4;
     c->L = make_layout(box[0], box[1], box[2], c->elem);
@@ -263,6 +268,9 @@ int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[
     if (e == cudaSuccess) e = cudaMalloc(&c->d_step, sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_partials, sizeof(double) * 10 * c->red_blocks);
+    c->centre.n = (int)(c->shape.grid.x * c->shape.grid.y * c->shape.grid.z);
+    if (e == cudaSuccess) e = cudaMalloc(&c->centre.p, sizeof(double) * 4 * c->centre.n);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->centre.p, 0, sizeof(double) * 4 * c->centre.n, c->stream);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_result, sizeof(double) * 32);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_result, sizeof(double) * 32);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(int));
@@ -291,6 +299,7 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->d_step);
     cudaFree(c->d_err);
     cudaFree(c->d_partials);
+    cudaFree(c->centre.p);
     cudaFree(c->d_result);
     cudaFree(c->d_kt);
     cudaFree(c->d_kA);
@@ -335,12 +344,12 @@ int lbm_step(lbm_ctx* c, int64_t n) {
                 cudaEventCreate(&a);
                 cudaEventCreate(&b);
                 cudaEventRecord(a, c->stream);
-                LBM_TRY(launch_ghost(c->prec, src, c->L, c->model, knots(c), c->d_step, c->d_err, c->stream));
+                LBM_TRY(launch_ghost(c->prec, src, c->L, c->model, knots(c), c->centre, c->d_step, c->d_err, c->stream));
                 cudaEventRecord(b, c->stream);
                 c->ev[1].push_back(a);
                 c->ev[1].push_back(b);
             } else {
-                LBM_TRY(launch_ghost(c->prec, src, c->L, c->model, knots(c), c->d_step, c->d_err, c->stream));
+                LBM_TRY(launch_ghost(c->prec, src, c->L, c->model, knots(c), c->centre, c->d_step, c->d_err, c->stream));
             }
         }
         if (c->prof) {
@@ -348,12 +357,12 @@ int lbm_step(lbm_ctx* c, int64_t n) {
             cudaEventCreate(&a);
             cudaEventCreate(&b);
             cudaEventRecord(a, c->stream);
-            LBM_TRY(launch_stream_collide(c->prec, src, dst, c->L, c->model, c->shape, c->d_step, 1, c->d_err, c->stream));
+            LBM_TRY(launch_stream_collide(c->prec, src, dst, c->L, c->model, c->shape, c->centre, c->d_step, 1, c->d_err, c->stream));
             cudaEventRecord(b, c->stream);
             c->ev[0].push_back(a);
             c->ev[0].push_back(b);
         } else {
-            LBM_TRY(launch_stream_collide(c->prec, src, dst, c->L, c->model, c->shape, c->d_step, 1, c->d_err, c->stream));
+            LBM_TRY(launch_stream_collide(c->prec, src, dst, c->L, c->model, c->shape, c->centre, c->d_step, 1, c->d_err, c->stream));
         }
         c->cur = 1 - c->cur;
         c->step += 1;
@@ -431,6 +440,7 @@ int lbm_set_populations(lbm_ctx* c, const double* f) {
     LBM_TRY(cudaMallocAsync(&d, sizeof(double) * E, c->stream));
     cudaError_t e = cudaMemcpyAsync(d, f, sizeof(double) * E, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = launch_unpack(c->prec, c->f[c->cur], c->L, d, c->stream);
+    if (e == cudaSuccess) e = launch_centre(c->prec, c->f[c->cur], c->L, c->centre, c->stream);
     cudaFreeAsync(d, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_status(e);
@@ -463,6 +473,9 @@ int lbm_save(lbm_ctx* c, const char* path) {
     try { pop.resize(E); } catch (...) { return LBM_ENOMEM; }
     int st = lbm_get_populations(c, pop.data());
     if (st) return st;
+    // the frame origin of the next step is part of the state
+    std::vector<double> cparts((size_t)4 * c->centre.n);
+    LBM_TRY(cudaMemcpy(cparts.data(), c->centre.p, sizeof(double) * cparts.size(), cudaMemcpyDeviceToHost));
     CkptHeader h;
     memset(&h, 0, sizeof(h));
     memcpy(h.magic, "LBMGB300", 8);
@@ -477,16 +490,19 @@ int lbm_save(lbm_ctx* c, const char* path) {
     h.step = c->step;
     h.nknots = (int64_t)c->kt.size();
     h.npop = (int64_t)E;
+    h.ncentre = (int64_t)c->centre.n;
     uint64_t sum = fnv1a(&h, sizeof(h));
     sum = fnv1a(c->kt.data(), sizeof(double) * c->kt.size(), sum);
     sum = fnv1a(c->kA.data(), sizeof(double) * c->kA.size(), sum);
     sum = fnv1a(pop.data(), sizeof(double) * E, sum);
+    sum = fnv1a(cparts.data(), sizeof(double) * cparts.size(), sum);
     FILE* fp = fopen(path, "wb");
     if (!fp) return LBM_EIO;
     bool ok = fwrite(&h, sizeof(h), 1, fp) == 1;
     ok = ok && fwrite(c->kt.data(), sizeof(double), c->kt.size(), fp) == c->kt.size();
     ok = ok && fwrite(c->kA.data(), sizeof(double), c->kA.size(), fp) == c->kA.size();
     ok = ok && fwrite(pop.data(), sizeof(double), E, fp) == E;
+    ok = ok && fwrite(cparts.data(), sizeof(double), cparts.size(), fp) == cparts.size();
     ok = ok && fwrite(&sum, sizeof(sum), 1, fp) == 1;
     ok = (fclose(fp) == 0) && ok;
     return ok ? LBM_OK : LBM_EIO;
@@ -503,15 +519,17 @@ int lbm_load(lbm_ctx* c, const char* path) {
     }
     const size_t E = 38ull * c->box[0] * c->box[1] * c->box[2];
     if (h.box[0] != c->box[0] || h.box[1] != c->box[1] || h.box[2] != c->box[2] || h.prec != c->prec ||
-        h.bc != c->model.periodic || h.npop != (int64_t)E || h.nknots < 0 || h.nknots > (1LL << 32)) {
+        h.bc != c->model.periodic || h.npop != (int64_t)E || h.nknots < 0 || h.nknots > (1LL << 32) ||
+        h.ncentre < 0 || h.ncentre > (1LL << 30)) {
         fclose(fp);
         return LBM_EINVAL;
     }
-    std::vector<double> kt, kA, pop;
+    std::vector<double> kt, kA, pop, cparts;
     try {
         kt.resize((size_t)h.nknots);
         kA.resize((size_t)h.nknots * 9);
         pop.resize(E);
+        cparts.resize((size_t)h.ncentre * 4);
     } catch (...) {
         fclose(fp);
         return LBM_ENOMEM;
@@ -520,6 +538,7 @@ int lbm_load(lbm_ctx* c, const char* path) {
     bool ok = fread(kt.data(), sizeof(double), kt.size(), fp) == kt.size();
     ok = ok && fread(kA.data(), sizeof(double), kA.size(), fp) == kA.size();
     ok = ok && fread(pop.data(), sizeof(double), E, fp) == E;
+    ok = ok && fread(cparts.data(), sizeof(double), cparts.size(), fp) == cparts.size();
     ok = ok && fread(&stored, sizeof(stored), 1, fp) == 1;
     fclose(fp);
     if (!ok) return LBM_EIO;
@@ -527,6 +546,7 @@ int lbm_load(lbm_ctx* c, const char* path) {
     sum = fnv1a(kt.data(), sizeof(double) * kt.size(), sum);
     sum = fnv1a(kA.data(), sizeof(double) * kA.size(), sum);
     sum = fnv1a(pop.data(), sizeof(double) * E, sum);
+    sum = fnv1a(cparts.data(), sizeof(double) * cparts.size(), sum);
     if (sum != stored) return LBM_EIO;
     int st = set_device(c);
     if (st) return st;
@@ -540,6 +560,11 @@ int lbm_load(lbm_ctx* c, const char* path) {
     c->d_kn = 0;  // force a re-upload of the whole table
     if ((st = ensure_knots_on_device(c))) return st;
     if ((st = lbm_set_populations(c, pop.data()))) return st;
+    // restore the saved frame origin partials when the launch shape matches
+    // (otherwise the ones just recomputed from the populations stay)
+    if (h.ncentre == c->centre.n)
+        LBM_TRY(cudaMemcpyAsync(c->centre.p, cparts.data(), sizeof(double) * cparts.size(), cudaMemcpyHostToDevice,
+                                c->stream));
     c->step = h.step;
     const long long s64 = (long long)h.step;
     LBM_TRY(cudaMemcpyAsync(c->d_step, &s64, sizeof(s64), cudaMemcpyHostToDevice, c->stream));

@@ -40,6 +40,16 @@ struct Model {
     double rho_b[2];   // ghost densities of A and B (Sec. 3)
     int periodic;      // 1: periodic test mode, no ghosts
     double mach2;      // guard on |u_ghost|^2 (lattice units)
+    int droplet_frame; // 1: ghost flow A (x - x_c), x_c the droplet's centre of mass
+};
+
+// Per-CTA partial sums {sum w, sum w x, sum w y, sum w z} of the droplet
+// indicator w = max(phi, 0) of the current state, written by the
+// stream-collide kernel (one row per CTA) or by launch_centre; the ghost
+// kernel reduces them in CTA order to the frame origin x_c.
+struct CentreParts {
+    double* p;  // [n][4]
+    int n;
 };
 
 // Device gradient table (knots of A(t)).
@@ -62,11 +72,13 @@ struct Shape {
 Shape choose_shape(const Layout& L, int elem_bytes, int ty_req, int zchunk_req, int num_sms);
 cudaError_t launch_init(int prec, void* f, const Layout& L, const Model& m, double R, double xi,
                         double rho_hi, double rho_lo, Knots k, cudaStream_t s);
-cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Knots k,
+cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Knots k, CentreParts cp,
                          const long long* d_step, int* d_err, cudaStream_t s);
 cudaError_t launch_stream_collide(int prec, const void* src, void* dst, const Layout& L, const Model& m,
-                                  const Shape& sh, long long* d_step, int step_inc, int* d_err,
+                                  const Shape& sh, CentreParts cp, long long* d_step, int step_inc, int* d_err,
                                   cudaStream_t s);
+// Centre-of-mass partials of the stored populations f (cp.n CTAs, grid-stride).
+cudaError_t launch_centre(int prec, const void* f, const Layout& L, CentreParts cp, cudaStream_t s);
 
 // ---- launchers (lbm_reduce.cu) ----
 // Ten moments of w = max(phi, 0) and the deformation: result[0..9] moments,

@@ -117,10 +117,29 @@ __global__ void k_init(S* __restrict__ f, Layout L, double R, double xi, double 
 // z in [-1, Lz]; z = -1 and z = Lz over x in [0, Lx), y in [0, Ly).  A ghost
 // population i is written only if it streams into the box (y + c_i inside).
 template <typename S>
-__global__ void k_ghost(S* __restrict__ f, Layout L, Model m, Knots k, const long long* __restrict__ d_step,
-                        int* __restrict__ d_err) {
+__global__ void k_ghost(S* __restrict__ f, Layout L, Model m, Knots k, CentreParts cp,
+                        const long long* __restrict__ d_step, int* __restrict__ d_err) {
     __shared__ double A[9];
-    if (threadIdx.x == 0) eval_gradient(k, (double)(*d_step), A);
+    __shared__ double xc[3];
+    if (threadIdx.x < 32) {
+        // frame origin: the droplet's centre of mass from the per-CTA partial
+        // sums of the current state, summed in CTA order (deterministic)
+        const int lane = threadIdx.x;
+        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        if (m.droplet_frame)
+            for (int b = lane; b < cp.n; b += 32)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s4[q] += cp.p[4LL * b + q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s4[q] += __shfl_down_sync(0xffffffffu, s4[q], o);
+        if (lane == 0) {
+            eval_gradient(k, (double)(*d_step), A);
+            const bool have = m.droplet_frame && s4[0] > 0.0;
+            for (int q = 0; q < 3; ++q) xc[q] = have ? s4[q + 1] / s4[0] : 0.0;
+        }
+    }
     __syncthreads();
     const long long nX = (long long)(L.Ly + 2) * (L.Lz + 2);
     const long long nY = (long long)L.Lx * (L.Lz + 2);
@@ -148,7 +167,7 @@ __global__ void k_ghost(S* __restrict__ f, Layout L, Model m, Knots k, const lon
     } else {
         return;
     }
-    const double px = x - 0.5 * (L.Lx - 1), py = y - 0.5 * (L.Ly - 1), pz = z - 0.5 * (L.Lz - 1);
+    const double px = x - 0.5 * (L.Lx - 1) - xc[0], py = y - 0.5 * (L.Ly - 1) - xc[1], pz = z - 0.5 * (L.Lz - 1) - xc[2];
     const double ux = A[0] * px + A[1] * py + A[2] * pz;
     const double uy = A[3] * px + A[4] * py + A[5] * pz;
     const double uz = A[6] * px + A[7] * py + A[8] * pz;
@@ -216,6 +235,7 @@ struct Puller {
 template <typename S, typename C, bool PER, int MAXT>
 __global__ void __launch_bounds__(MAXT) k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, Layout L,
                                                           ModelC<C> m, int TX, int TY, int zchunk,
+                                                          double* __restrict__ centre_parts,
                                                           long long* __restrict__ d_step, int step_inc,
                                                           int* __restrict__ d_err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -275,6 +295,11 @@ __global__ void __launch_bounds__(MAXT) k_stream_collide(const S* __restrict__ s
         halo(z, slot);
     };
 
+    // droplet moments {sum w, sum w x, sum w y, sum w z} of the state written
+    // here, w = max(phi, 0); they give the next step's frame origin
+    C cm[4] = {C(0), C(0), C(0), C(0)};
+    const C pxc = C(x) - C(0.5) * C(L.Lx - 1), pyc = C(y) - C(0.5) * C(L.Ly - 1);
+
     C fc[2][19], fn[2][19];
     rho_plane(zc0 - 1, (zc0 - 1) & 3);
     load_plane(zc0, zc0 & 3, fc);
@@ -319,6 +344,14 @@ __global__ void __launch_bounds__(MAXT) k_stream_collide(const S* __restrict__ s
 #pragma unroll
             for (int a = 0; a < 3; ++a) up[a] = (j[0][a] * m.inv_tau[0] + j[1][a] * m.inv_tau[1]) / den;
             if (!(isfinite(rho[0]) && isfinite(rho[1]))) atomicOr(d_err, 1);
+            {
+                const C phi = (rho[0] - rho[1]) / (rho[0] + rho[1]);
+                const C wphi = phi > C(0) ? phi : C(0);
+                cm[0] += wphi;
+                cm[1] += wphi * pxc;
+                cm[2] += wphi * pyc;
+                cm[3] += wphi * (C(z) - C(0.5) * C(L.Lz - 1));
+            }
             const long long base = L.at(0, 0, x, y, z);
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
@@ -341,7 +374,75 @@ __global__ void __launch_bounds__(MAXT) k_stream_collide(const S* __restrict__ s
 #pragma unroll
             for (int i = 0; i < 19; ++i) fc[s][i] = fn[s][i];
     }
+    // Block reduction of the moments in a fixed order: warp shuffles, then
+    // warp 0 over the per-warp sums (the ring is free after the last sync).
+    __syncthreads();
+    double* red = reinterpret_cast<double*>(smem_raw);
+    const int lane = t & 31, warp = t >> 5, nwarps = (NT + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double a = (double)cm[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) red[4 * warp + q] = a;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            double a = lane < nwarps ? red[4 * lane + q] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) {
+                const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+                centre_parts[4 * cta + q] = a;
+            }
+        }
+    }
     if (step_inc && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t == 0) *d_step += 1;
+}
+
+// Centre-of-mass partials of the stored populations (the first step's frame
+// origin after an initialisation or an upload of populations).
+template <typename S>
+__global__ void __launch_bounds__(256) k_centre(const S* __restrict__ f, Layout L, double* __restrict__ parts) {
+    double cm[4] = {0.0, 0.0, 0.0, 0.0};
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
+        const long long b = L.at(0, 0, x, y, z);
+        double ra = 0.0, rb = 0.0;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            ra += (double)f[b + (long long)i * L.array];
+            rb += (double)f[b + (long long)(19 + i) * L.array];
+        }
+        const double phi = (ra - rb) / (ra + rb);
+        const double w = phi > 0.0 ? phi : 0.0;
+        cm[0] += w;
+        cm[1] += w * (x - 0.5 * (L.Lx - 1));
+        cm[2] += w * (y - 0.5 * (L.Ly - 1));
+        cm[3] += w * (z - 0.5 * (L.Lz - 1));
+    }
+    __shared__ double red[8][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double a = cm[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) red[warp][q] = a;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            double a = lane < 8 ? red[lane][q] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) parts[4LL * blockIdx.x + q] = a;
+        }
+    }
 }
 
 template <typename C>
@@ -358,18 +459,18 @@ ModelC<C> model_c(const Model& m) {
 
 template <typename S, typename C, int MAXT>
 cudaError_t stream_collide_t(const void* src, void* dst, const Layout& L, const Model& m, const Shape& sh,
-                             long long* d_step, int step_inc, int* d_err, cudaStream_t s) {
+                             CentreParts cp, long long* d_step, int step_inc, int* d_err, cudaStream_t s) {
     const ModelC<C> mc = model_c<C>(m);
     if (m.periodic) {
         auto k = k_stream_collide<S, C, true, MAXT>;
         if (sh.smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
-        k<<<sh.grid, sh.threads, sh.smem, s>>>((const S*)src, (S*)dst, L, mc, sh.tx, sh.ty, sh.zchunk, d_step,
-                                               step_inc, d_err);
+        k<<<sh.grid, sh.threads, sh.smem, s>>>((const S*)src, (S*)dst, L, mc, sh.tx, sh.ty, sh.zchunk, cp.p,
+                                               d_step, step_inc, d_err);
     } else {
         auto k = k_stream_collide<S, C, false, MAXT>;
         if (sh.smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
-        k<<<sh.grid, sh.threads, sh.smem, s>>>((const S*)src, (S*)dst, L, mc, sh.tx, sh.ty, sh.zchunk, d_step,
-                                               step_inc, d_err);
+        k<<<sh.grid, sh.threads, sh.smem, s>>>((const S*)src, (S*)dst, L, mc, sh.tx, sh.ty, sh.zchunk, cp.p,
+                                               d_step, step_inc, d_err);
     }
     return cudaGetLastError();
 }
@@ -417,6 +518,8 @@ Shape choose_shape(const Layout& L, int elem_bytes, int ty_req, int zchunk_req, 
     sh.grid = dim3((L.Lx + sh.tx - 1) / sh.tx, (L.Ly + sh.ty - 1) / sh.ty, (L.Lz + zc - 1) / zc);
     sh.threads = sh.tx * sh.ty;
     sh.smem = (size_t)4 * 2 * (sh.tx + 2) * (sh.ty + 2) * elem_bytes;
+    const size_t red = (size_t)((sh.threads + 31) / 32) * 4 * sizeof(double);
+    if (sh.smem < red) sh.smem = red;
     return sh;
 }
 
@@ -431,20 +534,27 @@ cudaError_t launch_init(int prec, void* f, const Layout& L, const Model& m, doub
     return cudaGetLastError();
 }
 
-cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Knots k, const long long* d_step,
-                         int* d_err, cudaStream_t s) {
+cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Knots k, CentreParts cp,
+                         const long long* d_step, int* d_err, cudaStream_t s) {
     const long long n = 2LL * (L.Ly + 2) * (L.Lz + 2) + 2LL * L.Lx * (L.Lz + 2) + 2LL * L.Lx * L.Ly;
     const int T = 256;
     const unsigned blocks = (unsigned)((n + T - 1) / T);
-    if (prec == 0) k_ghost<double><<<blocks, T, 0, s>>>((double*)f, L, m, k, d_step, d_err);
-    else k_ghost<float><<<blocks, T, 0, s>>>((float*)f, L, m, k, d_step, d_err);
+    if (prec == 0) k_ghost<double><<<blocks, T, 0, s>>>((double*)f, L, m, k, cp, d_step, d_err);
+    else k_ghost<float><<<blocks, T, 0, s>>>((float*)f, L, m, k, cp, d_step, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_centre(int prec, const void* f, const Layout& L, CentreParts cp, cudaStream_t s) {
+    if (prec == 0) k_centre<double><<<cp.n, 256, 0, s>>>((const double*)f, L, cp.p);
+    else k_centre<float><<<cp.n, 256, 0, s>>>((const float*)f, L, cp.p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stream_collide(int prec, const void* src, void* dst, const Layout& L, const Model& m,
-                                  const Shape& sh, long long* d_step, int step_inc, int* d_err, cudaStream_t s) {
-    if (prec == 0) return stream_collide_t<double, double, kMaxThreadsF64>(src, dst, L, m, sh, d_step, step_inc, d_err, s);
-    return stream_collide_t<float, float, kMaxThreadsF32>(src, dst, L, m, sh, d_step, step_inc, d_err, s);
+                                  const Shape& sh, CentreParts cp, long long* d_step, int step_inc, int* d_err,
+                                  cudaStream_t s) {
+    if (prec == 0) return stream_collide_t<double, double, kMaxThreadsF64>(src, dst, L, m, sh, cp, d_step, step_inc, d_err, s);
+    return stream_collide_t<float, float, kMaxThreadsF32>(src, dst, L, m, sh, cp, d_step, step_inc, d_err, s);
 }
 
 }  // namespace lbmgb

@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(HERE, "_build", "liblbm_gb300.so")
 
 LBM_FP64, LBM_FP32 = 0, 1
 LBM_BC_GHOST_LINEAR, LBM_BC_PERIODIC_TEST = 0, 1
+LBM_FRAME_DROPLET, LBM_FRAME_BOX = 0, 1
+FRAMES = {"droplet": LBM_FRAME_DROPLET, "box": LBM_FRAME_BOX}
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32}
 
 # Every function the header declares, for the export check.
@@ -42,6 +44,7 @@ class lbm_opts(ctypes.Structure):
         ("device", ctypes.c_int32),
         ("tile_y", ctypes.c_int32),
         ("z_chunk", ctypes.c_int32),
+        ("frame", ctypes.c_int32),
     ]
 
 
@@ -129,11 +132,12 @@ class DropletLBM:
 
     ``box`` is (Lx, Ly, Lz) or an int; ``visc`` (nu_A, nu_B) in lattice units;
     ``precision`` "fp32" or "fp64"; ``periodic`` selects the periodic test
-    mode instead of the ghost-node boundary.
+    mode instead of the ghost-node boundary; ``frame`` "droplet" (the ghost
+    flow is linear in the distance from the droplet's centre of mass) or "box".
     """
 
     def __init__(self, box, R, visc, G, precision="fp32", periodic=False, rho_hi=0.0, rho_lo=0.0, xi=0.0,
-                 mach_limit=0.0, stream=None, device=-1, tile_y=0, z_chunk=0):
+                 mach_limit=0.0, stream=None, device=-1, tile_y=0, z_chunk=0, frame="droplet"):
         lib = load_library()
         self._lib = lib
         if isinstance(box, int):
@@ -150,6 +154,7 @@ class DropletLBM:
         o.cuda_stream = stream
         o.device = int(device)
         o.tile_y, o.z_chunk = int(tile_y), int(z_chunk)
+        o.frame = FRAMES[frame]
         b = (ctypes.c_int32 * 3)(*self.box)
         v = (ctypes.c_double * 2)(float(visc[0]), float(visc[1]))
         h = ctypes.c_void_p()

@@ -215,3 +215,21 @@ def test_non_finite_input_rejected_on_host(built):
     assert e.value.code == -1
     with pytest.raises(LBMError):
         g.set_gradient(np.eye(3).reshape(9), 0)  # not traceless
+
+
+def test_box_frame_short_run(built, oracle_mod):
+    """The box-centred frame (ghost flow A x from the box centre), fp64."""
+    box = (18, 16, 20)
+    tau = (1.0, 1.1)
+    o = oracle_mod.OracleLBM(box, tau, 3.5, (workloads.RHO_LO, 1.0), frame="box")
+    g = DropletLBM(box, 4.0, ((tau[0] - 0.5) / 3, (tau[1] - 0.5) / 3), 3.5, precision="fp64", rho_hi=1.0,
+                   rho_lo=workloads.RHO_LO, frame="box")
+    A = inputs.simple_shear(0.01)
+    o.init_droplet(4.0, 1.0, 1.0, workloads.RHO_LO, A)
+    f0 = inputs.perturbed_populations(o.populations(), 1e-3, seed=6)
+    o.set_populations(f0)
+    g.set_populations(f0)
+    g.set_gradient(A, 0)
+    o.run(30, [0.0], [A])
+    g.step(30)
+    assert rel_linf(g.populations(), o.populations()) <= 1e-12
