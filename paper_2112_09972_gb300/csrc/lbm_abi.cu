@@ -32,16 +32,12 @@ struct lbm_ctx {
     void* f[2];
     int cur;                // buffer holding the current post-collision populations
     bool initialised;       // populations hold a state (lazy init on first use)
-    int64_t step;           // host mirror of the step counter
-    long long* d_step;      // device step counter read by the ghost kernel
+    int64_t step;           // steps taken; step n uses A(t_n = n)
     int* d_err;             // latched device error bits: 1 non-finite, 2 Mach
     int* h_err;             // pinned mirror
     int latched;            // latched status returned by later calls
-    // gradient knots
+    // gradient knots (host); A(t_n) is evaluated here and passed by value
     std::vector<double> kt, kA;
-    double* d_kt;
-    double* d_kA;
-    int d_kcap, d_kn;
     // per-CTA droplet moments of the current state (frame origin of the next step)
     CentreParts centre;
     // reduction scratch
@@ -82,36 +78,32 @@ double coexistence_lo(double G, double h) {
     return 0.5 * (a + b);
 }
 
-int ensure_knots_on_device(lbm_ctx* c) {
-    const int n = (int)c->kt.size();
-    if (n == c->d_kn) return LBM_OK;
-    if (n > c->d_kcap) {
-        int cap = std::max(64, c->d_kcap);
-        while (cap < n) cap *= 2;
-        double *nt = nullptr, *nA = nullptr;
-        LBM_TRY(cudaStreamSynchronize(c->stream));
-        LBM_TRY(cudaMalloc(&nt, sizeof(double) * cap));
-        if (cudaMalloc(&nA, sizeof(double) * 9 * cap) != cudaSuccess) {
-            cudaFree(nt);
-            return LBM_ENOMEM;
-        }
-        cudaFree(c->d_kt);
-        cudaFree(c->d_kA);
-        c->d_kt = nt;
-        c->d_kA = nA;
-        c->d_kcap = cap;
-        c->d_kn = 0;
+// A(t) from the knot table: linear between knots, constant outside.
+Grad gradient_at(const lbm_ctx* c, double t) {
+    Grad g;
+    const size_t n = c->kt.size();
+    if (n == 0) {
+        for (int j = 0; j < 9; ++j) g.a[j] = 0.0;
+        return g;
     }
-    // Knots are append-only; copy the new ones synchronously (rare, small).
-    const int k0 = c->d_kn;
-    LBM_TRY(cudaMemcpyAsync(c->d_kt + k0, c->kt.data() + k0, sizeof(double) * (n - k0), cudaMemcpyHostToDevice, c->stream));
-    LBM_TRY(cudaMemcpyAsync(c->d_kA + 9 * k0, c->kA.data() + 9 * k0, sizeof(double) * 9 * (n - k0), cudaMemcpyHostToDevice, c->stream));
-    LBM_TRY(cudaStreamSynchronize(c->stream));
-    c->d_kn = n;
-    return LBM_OK;
+    if (t <= c->kt[0]) {
+        for (int j = 0; j < 9; ++j) g.a[j] = c->kA[j];
+        return g;
+    }
+    if (t >= c->kt[n - 1]) {
+        for (int j = 0; j < 9; ++j) g.a[j] = c->kA[9 * (n - 1) + j];
+        return g;
+    }
+    // first knot with t_k > t
+    const size_t hi = (size_t)(std::upper_bound(c->kt.begin(), c->kt.end(), t) - c->kt.begin());
+    const size_t lo = hi - 1;
+    const double w = (t - c->kt[lo]) / (c->kt[hi] - c->kt[lo]);
+    for (int j = 0; j < 9; ++j) {
+        const double a = c->kA[9 * lo + j], b = c->kA[9 * hi + j];
+        g.a[j] = a + w * (b - a);
+    }
+    return g;
 }
-
-Knots knots(const lbm_ctx* c) { return Knots{c->d_kt, c->d_kA, c->d_kn}; }
 
 int check_latched(lbm_ctx* c) {
     if (c->latched) return c->latched;
@@ -132,9 +124,7 @@ int sync_and_check(lbm_ctx* c) {
 
 int lazy_init(lbm_ctx* c) {
     if (c->initialised) return LBM_OK;
-    int st = ensure_knots_on_device(c);
-    if (st) return st;
-    LBM_TRY(launch_init(c->prec, c->f[c->cur], c->L, c->model, c->R, c->xi, c->rho_hi, c->rho_lo, knots(c), c->stream));
+    LBM_TRY(launch_init(c->prec, c->f[c->cur], c->L, c->R, c->xi, c->rho_hi, c->rho_lo, gradient_at(c, 0.0), c->stream));
     LBM_TRY(launch_centre(c->prec, c->f[c->cur], c->L, c->centre, c->stream));
     c->initialised = true;
     return LBM_OK;
@@ -265,19 +255,21 @@ int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[
     const size_t bytes = (size_t)c->L.total * c->elem;
     cudaError_t e = cudaMalloc(&c->f[0], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->f[1], bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_step, sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_partials, sizeof(double) * 10 * c->red_blocks);
     c->centre.n = (int)(c->shape.grid.x * c->shape.grid.y * c->shape.grid.z);
-    if (e == cudaSuccess) e = cudaMalloc(&c->centre.p, sizeof(double) * 4 * c->centre.n);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->centre.p, 0, sizeof(double) * 4 * c->centre.n, c->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&c->centre.p, sizeof(double) * 4 * (c->centre.n + 1) + 16);
+    if (e == cudaSuccess) {
+        c->centre.sum = c->centre.p + 4 * c->centre.n;
+        c->centre.counter = (unsigned*)(c->centre.sum + 4);
+        e = cudaMemsetAsync(c->centre.p, 0, sizeof(double) * 4 * (c->centre.n + 1) + 16, c->stream);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&c->d_result, sizeof(double) * 32);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_result, sizeof(double) * 32);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(int));
     // Zero both buffers once: ghost entries that no direction reads stay defined.
     if (e == cudaSuccess) e = cudaMemsetAsync(c->f[0], 0, bytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->f[1], 0, bytes, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_step, 0, sizeof(long long), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -296,13 +288,10 @@ void lbm_destroy(lbm_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     cudaFree(c->f[0]);
     cudaFree(c->f[1]);
-    cudaFree(c->d_step);
     cudaFree(c->d_err);
     cudaFree(c->d_partials);
     cudaFree(c->centre.p);
     cudaFree(c->d_result);
-    cudaFree(c->d_kt);
-    cudaFree(c->d_kA);
     if (c->h_result) cudaFreeHost(c->h_result);
     if (c->h_err) cudaFreeHost(c->h_err);
     for (int k = 0; k < 2; ++k)
@@ -334,35 +323,35 @@ int lbm_step(lbm_ctx* c, int64_t n) {
     int st = set_device(c);
     if (st) return st;
     if ((st = lazy_init(c))) return st;
-    if ((st = ensure_knots_on_device(c))) return st;
     for (int64_t k = 0; k < n; ++k) {
         void* src = c->f[c->cur];
         void* dst = c->f[1 - c->cur];
         if (!c->model.periodic) {
+            const Grad A = gradient_at(c, (double)c->step);
+            cudaEvent_t a = nullptr, b = nullptr;
             if (c->prof) {
-                cudaEvent_t a, b;
                 cudaEventCreate(&a);
                 cudaEventCreate(&b);
                 cudaEventRecord(a, c->stream);
-                LBM_TRY(launch_ghost(c->prec, src, c->L, c->model, knots(c), c->centre, c->d_step, c->d_err, c->stream));
+            }
+            LBM_TRY(launch_ghost(c->prec, src, c->L, c->model, A, c->centre, c->d_err, c->stream));
+            if (c->prof) {
                 cudaEventRecord(b, c->stream);
                 c->ev[1].push_back(a);
                 c->ev[1].push_back(b);
-            } else {
-                LBM_TRY(launch_ghost(c->prec, src, c->L, c->model, knots(c), c->centre, c->d_step, c->d_err, c->stream));
             }
         }
+        cudaEvent_t a = nullptr, b = nullptr;
         if (c->prof) {
-            cudaEvent_t a, b;
             cudaEventCreate(&a);
             cudaEventCreate(&b);
             cudaEventRecord(a, c->stream);
-            LBM_TRY(launch_stream_collide(c->prec, src, dst, c->L, c->model, c->shape, c->centre, c->d_step, 1, c->d_err, c->stream));
+        }
+        LBM_TRY(launch_stream_collide(c->prec, src, dst, c->L, c->model, c->shape, c->centre, c->d_err, c->stream));
+        if (c->prof) {
             cudaEventRecord(b, c->stream);
             c->ev[0].push_back(a);
             c->ev[0].push_back(b);
-        } else {
-            LBM_TRY(launch_stream_collide(c->prec, src, dst, c->L, c->model, c->shape, c->centre, c->d_step, 1, c->d_err, c->stream));
         }
         c->cur = 1 - c->cur;
         c->step += 1;
@@ -557,8 +546,6 @@ int lbm_load(lbm_ctx* c, const char* path) {
     c->model.rho_b[0] = h.rho_b[0]; c->model.rho_b[1] = h.rho_b[1];
     c->kt.swap(kt);
     c->kA.swap(kA);
-    c->d_kn = 0;  // force a re-upload of the whole table
-    if ((st = ensure_knots_on_device(c))) return st;
     if ((st = lbm_set_populations(c, pop.data()))) return st;
     // restore the saved frame origin partials when the launch shape matches
     // (otherwise the ones just recomputed from the populations stay)
@@ -566,8 +553,6 @@ int lbm_load(lbm_ctx* c, const char* path) {
         LBM_TRY(cudaMemcpyAsync(c->centre.p, cparts.data(), sizeof(double) * cparts.size(), cudaMemcpyHostToDevice,
                                 c->stream));
     c->step = h.step;
-    const long long s64 = (long long)h.step;
-    LBM_TRY(cudaMemcpyAsync(c->d_step, &s64, sizeof(s64), cudaMemcpyHostToDevice, c->stream));
     LBM_TRY(cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }

@@ -45,18 +45,19 @@ struct Model {
 
 // Per-CTA partial sums {sum w, sum w x, sum w y, sum w z} of the droplet
 // indicator w = max(phi, 0) of the current state, written by the
-// stream-collide kernel (one row per CTA) or by launch_centre; the ghost
-// kernel reduces them in CTA order to the frame origin x_c.
+// stream-collide kernel (one row per CTA) or by launch_centre.  The last CTA
+// to finish sums the rows in CTA order into `sum` (deterministic) and resets
+// `counter`; the ghost kernel of the next step reads `sum`.
 struct CentreParts {
-    double* p;  // [n][4]
-    int n;
+    double* p;          // [n][4]
+    int n;              // CTAs of the stream-collide launch
+    double* sum;        // [4]
+    unsigned* counter;  // CTAs finished, 0 between launches
 };
 
-// Device gradient table (knots of A(t)).
-struct Knots {
-    const double* t;  // [n]
-    const double* A;  // [n][9]
-    int n;
+// A velocity gradient passed by value, row-major A[3a+b] = d u_a / d x_b.
+struct Grad {
+    double a[9];
 };
 
 // Launch shape of the stream-collide kernel.
@@ -70,13 +71,12 @@ struct Shape {
 
 // ---- launchers (lbm_step.cu) ----
 Shape choose_shape(const Layout& L, int elem_bytes, int ty_req, int zchunk_req, int num_sms);
-cudaError_t launch_init(int prec, void* f, const Layout& L, const Model& m, double R, double xi,
-                        double rho_hi, double rho_lo, Knots k, cudaStream_t s);
-cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Knots k, CentreParts cp,
-                         const long long* d_step, int* d_err, cudaStream_t s);
+cudaError_t launch_init(int prec, void* f, const Layout& L, double R, double xi, double rho_hi, double rho_lo,
+                        Grad A0, cudaStream_t s);
+cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Grad A, CentreParts cp, int* d_err,
+                         cudaStream_t s);
 cudaError_t launch_stream_collide(int prec, const void* src, void* dst, const Layout& L, const Model& m,
-                                  const Shape& sh, CentreParts cp, long long* d_step, int step_inc, int* d_err,
-                                  cudaStream_t s);
+                                  const Shape& sh, CentreParts cp, int* d_err, cudaStream_t s);
 // Centre-of-mass partials of the stored populations f (cp.n CTAs, grid-stride).
 cudaError_t launch_centre(int prec, const void* f, const Layout& L, CentreParts cp, cudaStream_t s);
 

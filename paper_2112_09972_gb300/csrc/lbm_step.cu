@@ -3,12 +3,15 @@
 // Sec. 3 Eq. 14) for sm_103a:
 //
 //   k_init            -- equilibrium initial state of a tanh droplet in u = A(0) x
-//   k_ghost           -- ghost-node rebuild: g_i^eq(rho_b, A(t) x) on the shell
-//                        one layer outside the box, for the directions that
-//                        stream into the box (Eq. 8, Eq. 14)
+//   k_ghost           -- ghost-node rebuild: g_i^eq(rho_b, A(t) (x - x_c)) on the
+//                        shell one layer outside the box, for the directions
+//                        that stream into the box (Eq. 8, Eq. 14)
 //   k_stream_collide  -- fused pull streaming (Eq. 9), component densities
 //                        (Eq. 6), Shan-Chen force (Eq. 7), velocity-shift
-//                        forcing and BGK relaxation (Eqs. 9, 10)
+//                        forcing and BGK relaxation (Eqs. 9, 10); its epilogue
+//                        reduces the droplet's centre of mass x_c of the state
+//                        it writes (the frame origin of the next step)
+//   k_centre          -- the same centre of mass from stored populations
 //
 // The stream-collide kernel is bandwidth bound (about 1.5 flop per byte), so
 // it uses no tensor cores.  Each CTA owns a TX x TY tile of the x-y plane and
@@ -16,10 +19,14 @@
 // of planes z-1, z, z+1 including a one-node halo around the tile; those live
 // in a four-slot ring of density planes in shared memory.  The tile's own
 // populations are pulled once per plane and held in registers across one
-// plane of the march (pulled at z+1, collided at z+1 one iteration later), so
-// DRAM sees one read and one write of every population; only the halo rows
-// are pulled a second time, from L2, because the neighbouring tiles march the
-// same planes at the same time.
+// plane of the march (pulled at z+1, collided one iteration later), so DRAM
+// sees one read and one write of every population; only the halo rows are
+// pulled a second time, from L2, because the neighbouring tiles march the
+// same planes at about the same time.
+//
+// Sums of populations with opposite velocities are formed as differences of
+// the pair first (c_{2k} = -c_{2k-1}); in fp32 this keeps the cancellation in
+// momentum and force sums exact where the pair values are close.
 
 #include <cuda_runtime.h>
 
@@ -28,8 +35,9 @@
 namespace lbmgb {
 namespace {
 
-// D3Q19 velocities in the order documented in lbm.h.  Every loop over
-// directions is unrolled, so these fold to immediates.
+// D3Q19 velocities in the order documented in lbm.h: direction 2k is the
+// opposite of direction 2k-1.  Every loop over directions is unrolled, so
+// these fold to immediates.
 __host__ __device__ __forceinline__ constexpr int cx_(int i) {
     constexpr int t[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
     return t[i];
@@ -60,39 +68,19 @@ __device__ __forceinline__ int wrap(int a, int n) {
     return a >= n ? a - n : a;
 }
 
-// A(t) from the knot table: linear between knots, constant outside.
-__device__ void eval_gradient(const Knots& k, double t, double A[9]) {
-    if (k.n <= 0) {
-        for (int j = 0; j < 9; ++j) A[j] = 0.0;
-        return;
-    }
-    if (t <= k.t[0]) {
-        for (int j = 0; j < 9; ++j) A[j] = k.A[j];
-        return;
-    }
-    if (t >= k.t[k.n - 1]) {
-        for (int j = 0; j < 9; ++j) A[j] = k.A[9 * (k.n - 1) + j];
-        return;
-    }
-    int lo = 0, hi = k.n - 1;  // invariant: t[lo] <= t < t[hi]
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (k.t[mid] <= t) lo = mid; else hi = mid;
-    }
-    const double w = (t - k.t[lo]) / (k.t[hi] - k.t[lo]);
-    for (int j = 0; j < 9; ++j) {
-        const double a = k.A[9 * lo + j], b = k.A[9 * hi + j];
-        A[j] = a + w * (b - a);
-    }
+// Sum of 19 values as f0 + sum over opposite pairs.
+template <typename C>
+__device__ __forceinline__ C sum19(const C (&f)[19]) {
+    C s = f[0];
+#pragma unroll
+    for (int i = 1; i < 19; i += 2) s += f[i] + f[i + 1];
+    return s;
 }
 
 // ----------------------------------------------------------------------------
 // Initial state.
 template <typename S>
-__global__ void k_init(S* __restrict__ f, Layout L, double R, double xi, double rho_hi, double rho_lo, Knots k) {
-    __shared__ double A[9];
-    if (threadIdx.x == 0) eval_gradient(k, 0.0, A);
-    __syncthreads();
+__global__ void k_init(S* __restrict__ f, Layout L, double R, double xi, double rho_hi, double rho_lo, Grad A) {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long N = (long long)L.Lx * L.Ly * L.Lz;
     if (n >= N) return;
@@ -101,9 +89,9 @@ __global__ void k_init(S* __restrict__ f, Layout L, double R, double xi, double 
     const double r = sqrt(px * px + py * py + pz * pz);
     const double th = tanh((r - R) / xi);
     const double rho[2] = {rho_lo + (rho_hi - rho_lo) * 0.5 * (1.0 - th), rho_lo + (rho_hi - rho_lo) * 0.5 * (1.0 + th)};
-    const double ux = A[0] * px + A[1] * py + A[2] * pz;
-    const double uy = A[3] * px + A[4] * py + A[5] * pz;
-    const double uz = A[6] * px + A[7] * py + A[8] * pz;
+    const double ux = A.a[0] * px + A.a[1] * py + A.a[2] * pz;
+    const double uy = A.a[3] * px + A.a[4] * py + A.a[5] * pz;
+    const double uz = A.a[6] * px + A.a[7] * py + A.a[8] * pz;
     const double u2x = 1.5 * (ux * ux + uy * uy + uz * uz);
 #pragma unroll
     for (int s = 0; s < 2; ++s)
@@ -117,30 +105,18 @@ __global__ void k_init(S* __restrict__ f, Layout L, double R, double xi, double 
 // z in [-1, Lz]; z = -1 and z = Lz over x in [0, Lx), y in [0, Ly).  A ghost
 // population i is written only if it streams into the box (y + c_i inside).
 template <typename S>
-__global__ void k_ghost(S* __restrict__ f, Layout L, Model m, Knots k, CentreParts cp,
-                        const long long* __restrict__ d_step, int* __restrict__ d_err) {
-    __shared__ double A[9];
-    __shared__ double xc[3];
-    if (threadIdx.x < 32) {
-        // frame origin: the droplet's centre of mass from the per-CTA partial
-        // sums of the current state, summed in CTA order (deterministic)
-        const int lane = threadIdx.x;
-        double s4[4] = {0.0, 0.0, 0.0, 0.0};
-        if (m.droplet_frame)
-            for (int b = lane; b < cp.n; b += 32)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) s4[q] += cp.p[4LL * b + q];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s4[q] += __shfl_down_sync(0xffffffffu, s4[q], o);
-        if (lane == 0) {
-            eval_gradient(k, (double)(*d_step), A);
-            const bool have = m.droplet_frame && s4[0] > 0.0;
-            for (int q = 0; q < 3; ++q) xc[q] = have ? s4[q + 1] / s4[0] : 0.0;
+__global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, Model m, Grad A, CentreParts cp,
+                                               int* __restrict__ d_err) {
+    // frame origin: the droplet's centre of mass of the current state
+    double xc = 0.0, yc = 0.0, zc = 0.0;
+    if (m.droplet_frame) {
+        const double w0 = cp.sum[0];
+        if (w0 > 0.0) {
+            xc = cp.sum[1] / w0;
+            yc = cp.sum[2] / w0;
+            zc = cp.sum[3] / w0;
         }
     }
-    __syncthreads();
     const long long nX = (long long)(L.Ly + 2) * (L.Lz + 2);
     const long long nY = (long long)L.Lx * (L.Lz + 2);
     const long long nZ = (long long)L.Lx * L.Ly;
@@ -167,10 +143,10 @@ __global__ void k_ghost(S* __restrict__ f, Layout L, Model m, Knots k, CentrePar
     } else {
         return;
     }
-    const double px = x - 0.5 * (L.Lx - 1) - xc[0], py = y - 0.5 * (L.Ly - 1) - xc[1], pz = z - 0.5 * (L.Lz - 1) - xc[2];
-    const double ux = A[0] * px + A[1] * py + A[2] * pz;
-    const double uy = A[3] * px + A[4] * py + A[5] * pz;
-    const double uz = A[6] * px + A[7] * py + A[8] * pz;
+    const double px = x - 0.5 * (L.Lx - 1) - xc, py = y - 0.5 * (L.Ly - 1) - yc, pz = z - 0.5 * (L.Lz - 1) - zc;
+    const double ux = A.a[0] * px + A.a[1] * py + A.a[2] * pz;
+    const double uy = A.a[3] * px + A.a[4] * py + A.a[5] * pz;
+    const double uz = A.a[6] * px + A.a[7] * py + A.a[8] * pz;
     const double usq = ux * ux + uy * uy + uz * uz;
     const double u2x = 1.5 * usq;
     bool any = false;
@@ -183,6 +159,56 @@ __global__ void k_ghost(S* __restrict__ f, Layout L, Model m, Knots k, CentrePar
         for (int s = 0; s < 2; ++s) f[L.at(s, i, x, y, z)] = (S)feq<double>(i, m.rho_b[s], ux, uy, uz, u2x);
     }
     if (any && usq > m.mach2) atomicOr(d_err, 2);
+}
+
+// Fixed-order reduction of the per-CTA centre partials by the last CTA to
+// finish (threadfence-reduction pattern); every thread of the CTA calls it.
+// `scratch` holds 4 doubles per warp of shared memory.
+__device__ void centre_epilogue(double (&cm)[4], CentreParts cp, double* scratch) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = (blockDim.x + 31) >> 5;
+    const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+    __shared__ unsigned last;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double a = cm[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) scratch[4 * warp + q] = a;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            double a = lane < nwarps ? scratch[4 * lane + q] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) cp.p[4 * cta + q] = a;
+        }
+        if (lane == 0) {
+            __threadfence();
+            last = atomicAdd(cp.counter, 1u) == total - 1 ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+    if (last && warp == 0) {
+        __threadfence();
+        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        for (unsigned b = lane; b < total; b += 32)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s4[q] += __ldcg(cp.p + 4LL * b + q);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s4[q] += __shfl_down_sync(0xffffffffu, s4[q], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cp.sum[q] = s4[q];
+            *cp.counter = 0u;
+        }
+    }
 }
 
 // ----------------------------------------------------------------------------
@@ -222,21 +248,16 @@ struct Puller {
             ra = m.rho_b[0]; rb = m.rho_b[1];
             return;
         }
-        C a = C(0), b = C(0);
-#pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            a += (C)__ldg(src + idx(0, i, x, y, z));
-            b += (C)__ldg(src + idx(1, i, x, y, z));
-        }
-        ra = a; rb = b;
+        C f[2][19];
+        pull(x, y, z, f);
+        ra = sum19<C>(f[0]);
+        rb = sum19<C>(f[1]);
     }
 };
 
 template <typename S, typename C, bool PER, int MAXT>
 __global__ void __launch_bounds__(MAXT) k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, Layout L,
-                                                          ModelC<C> m, int TX, int TY, int zchunk,
-                                                          double* __restrict__ centre_parts,
-                                                          long long* __restrict__ d_step, int step_inc,
+                                                          ModelC<C> m, int TX, int TY, int zchunk, CentreParts cp,
                                                           int* __restrict__ d_err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* ring = reinterpret_cast<C*>(smem_raw);
@@ -281,11 +302,8 @@ __global__ void __launch_bounds__(MAXT) k_stream_collide(const S* __restrict__ s
     auto load_plane = [&](int z, int slot, C (&f)[2][19]) {
         if (active) {
             P.pull(x, y, z, f);
-            C ra = C(0), rb = C(0);
-#pragma unroll
-            for (int i = 0; i < 19; ++i) { ra += f[0][i]; rb += f[1][i]; }
-            R(slot, 0, tx, ty) = ra;
-            R(slot, 1, tx, ty) = rb;
+            R(slot, 0, tx, ty) = sum19<C>(f[0]);
+            R(slot, 1, tx, ty) = sum19<C>(f[1]);
         } else {
             C ra, rb;
             P.rho_at(x, y, z, m, ra, rb);
@@ -296,7 +314,8 @@ __global__ void __launch_bounds__(MAXT) k_stream_collide(const S* __restrict__ s
     };
 
     // droplet moments {sum w, sum w x, sum w y, sum w z} of the state written
-    // here, w = max(phi, 0); they give the next step's frame origin
+    // here, w = max(phi, 0); they give the next step's frame origin.  Summed
+    // over the thread's z column in the compute type, then reduced in double.
     C cm[4] = {C(0), C(0), C(0), C(0)};
     const C pxc = C(x) - C(0.5) * C(L.Lx - 1), pyc = C(y) - C(0.5) * C(L.Ly - 1);
 
@@ -314,29 +333,32 @@ __global__ void __launch_bounds__(MAXT) k_stream_collide(const S* __restrict__ s
         if (active) {
             const int s0 = (z - 1) & 3, s1 = z & 3, s2 = (z + 1) & 3;
             const C rho[2] = {R(s1, 0, tx, ty), R(s1, 1, tx, ty)};
-            // momentum of each component (Eq. 6)
+            // momentum of each component (Eq. 6), opposite pairs first
             C j[2][3];
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 C jx = C(0), jy = C(0), jz = C(0);
 #pragma unroll
-                for (int i = 1; i < 19; ++i) {
-                    if (cx_(i)) jx += C(cx_(i)) * fc[s][i];
-                    if (cy_(i)) jy += C(cy_(i)) * fc[s][i];
-                    if (cz_(i)) jz += C(cz_(i)) * fc[s][i];
+                for (int i = 1; i < 19; i += 2) {
+                    const C d = fc[s][i] - fc[s][i + 1];
+                    if (cx_(i)) jx += C(cx_(i)) * d;
+                    if (cy_(i)) jy += C(cy_(i)) * d;
+                    if (cz_(i)) jz += C(cz_(i)) * d;
                 }
                 j[s][0] = jx; j[s][1] = jy; j[s][2] = jz;
             }
-            // Shan-Chen force (Eq. 7): F^s = -G rho_s sum_i w_i rho_s'(x + c_i) c_i
+            // Shan-Chen force (Eq. 7): F^s = -G rho_s sum_i w_i rho_s'(x + c_i) c_i,
+            // with the neighbour pair x + c_i, x - c_i differenced first
             C acc[2][3] = {{C(0), C(0), C(0)}, {C(0), C(0), C(0)}};
 #pragma unroll
-            for (int i = 1; i < 19; ++i) {
-                const int sl = cz_(i) == 0 ? s1 : (cz_(i) > 0 ? s2 : s0);
-                const C wa = wgt<C>(i) * R(sl, 0, tx + cx_(i), ty + cy_(i));
-                const C wb = wgt<C>(i) * R(sl, 1, tx + cx_(i), ty + cy_(i));
-                if (cx_(i)) { acc[0][0] += C(cx_(i)) * wa; acc[1][0] += C(cx_(i)) * wb; }
-                if (cy_(i)) { acc[0][1] += C(cy_(i)) * wa; acc[1][1] += C(cy_(i)) * wb; }
-                if (cz_(i)) { acc[0][2] += C(cz_(i)) * wa; acc[1][2] += C(cz_(i)) * wb; }
+            for (int i = 1; i < 19; i += 2) {
+                const int sp = cz_(i) == 0 ? s1 : (cz_(i) > 0 ? s2 : s0);
+                const int sm = cz_(i) == 0 ? s1 : (cz_(i) > 0 ? s0 : s2);
+                const C da = wgt<C>(i) * (R(sp, 0, tx + cx_(i), ty + cy_(i)) - R(sm, 0, tx - cx_(i), ty - cy_(i)));
+                const C db = wgt<C>(i) * (R(sp, 1, tx + cx_(i), ty + cy_(i)) - R(sm, 1, tx - cx_(i), ty - cy_(i)));
+                if (cx_(i)) { acc[0][0] += C(cx_(i)) * da; acc[1][0] += C(cx_(i)) * db; }
+                if (cy_(i)) { acc[0][1] += C(cy_(i)) * da; acc[1][1] += C(cy_(i)) * db; }
+                if (cz_(i)) { acc[0][2] += C(cz_(i)) * da; acc[1][2] += C(cz_(i)) * db; }
             }
             // common velocity u' and per-component shifted velocity
             const C den = rho[0] * m.inv_tau[0] + rho[1] * m.inv_tau[1];
@@ -355,7 +377,7 @@ __global__ void __launch_bounds__(MAXT) k_stream_collide(const S* __restrict__ s
             const long long base = L.at(0, 0, x, y, z);
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
-                // F^s / rho_s = -G * (sum over the other component)
+                // tau_s F^s / rho_s = -G tau_s * (the other component's sum)
                 const C sh = -m.G * m.tau[s];
                 const C ux = up[0] + sh * acc[1 - s][0];
                 const C uy = up[1] + sh * acc[1 - s][1];
@@ -374,38 +396,15 @@ __global__ void __launch_bounds__(MAXT) k_stream_collide(const S* __restrict__ s
 #pragma unroll
             for (int i = 0; i < 19; ++i) fc[s][i] = fn[s][i];
     }
-    // Block reduction of the moments in a fixed order: warp shuffles, then
-    // warp 0 over the per-warp sums (the ring is free after the last sync).
-    __syncthreads();
-    double* red = reinterpret_cast<double*>(smem_raw);
-    const int lane = t & 31, warp = t >> 5, nwarps = (NT + 31) >> 5;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        double a = (double)cm[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) red[4 * warp + q] = a;
-    }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            double a = lane < nwarps ? red[4 * lane + q] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-            if (lane == 0) {
-                const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-                centre_parts[4 * cta + q] = a;
-            }
-        }
-    }
-    if (step_inc && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t == 0) *d_step += 1;
+    double cmd[4] = {(double)cm[0], (double)cm[1], (double)cm[2], (double)cm[3]};
+    centre_epilogue(cmd, cp, reinterpret_cast<double*>(smem_raw));
 }
 
 // Centre-of-mass partials of the stored populations (the first step's frame
 // origin after an initialisation or an upload of populations).
 template <typename S>
-__global__ void __launch_bounds__(256) k_centre(const S* __restrict__ f, Layout L, double* __restrict__ parts) {
+__global__ void __launch_bounds__(256) k_centre(const S* __restrict__ f, Layout L, CentreParts cp) {
+    __shared__ double scratch[32];
     double cm[4] = {0.0, 0.0, 0.0, 0.0};
     const long long N = (long long)L.Lx * L.Ly * L.Lz;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
@@ -424,25 +423,7 @@ __global__ void __launch_bounds__(256) k_centre(const S* __restrict__ f, Layout 
         cm[2] += w * (y - 0.5 * (L.Ly - 1));
         cm[3] += w * (z - 0.5 * (L.Lz - 1));
     }
-    __shared__ double red[8][4];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        double a = cm[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) red[warp][q] = a;
-    }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            double a = lane < 8 ? red[lane][q] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-            if (lane == 0) parts[4LL * blockIdx.x + q] = a;
-        }
-    }
+    centre_epilogue(cm, cp, scratch);
 }
 
 template <typename C>
@@ -459,18 +440,16 @@ ModelC<C> model_c(const Model& m) {
 
 template <typename S, typename C, int MAXT>
 cudaError_t stream_collide_t(const void* src, void* dst, const Layout& L, const Model& m, const Shape& sh,
-                             CentreParts cp, long long* d_step, int step_inc, int* d_err, cudaStream_t s) {
+                             CentreParts cp, int* d_err, cudaStream_t s) {
     const ModelC<C> mc = model_c<C>(m);
     if (m.periodic) {
         auto k = k_stream_collide<S, C, true, MAXT>;
         if (sh.smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
-        k<<<sh.grid, sh.threads, sh.smem, s>>>((const S*)src, (S*)dst, L, mc, sh.tx, sh.ty, sh.zchunk, cp.p,
-                                               d_step, step_inc, d_err);
+        k<<<sh.grid, sh.threads, sh.smem, s>>>((const S*)src, (S*)dst, L, mc, sh.tx, sh.ty, sh.zchunk, cp, d_err);
     } else {
         auto k = k_stream_collide<S, C, false, MAXT>;
         if (sh.smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
-        k<<<sh.grid, sh.threads, sh.smem, s>>>((const S*)src, (S*)dst, L, mc, sh.tx, sh.ty, sh.zchunk, cp.p,
-                                               d_step, step_inc, d_err);
+        k<<<sh.grid, sh.threads, sh.smem, s>>>((const S*)src, (S*)dst, L, mc, sh.tx, sh.ty, sh.zchunk, cp, d_err);
     }
     return cudaGetLastError();
 }
@@ -523,38 +502,36 @@ Shape choose_shape(const Layout& L, int elem_bytes, int ty_req, int zchunk_req, 
     return sh;
 }
 
-cudaError_t launch_init(int prec, void* f, const Layout& L, const Model& m, double R, double xi, double rho_hi,
-                        double rho_lo, Knots k, cudaStream_t s) {
-    (void)m;
+cudaError_t launch_init(int prec, void* f, const Layout& L, double R, double xi, double rho_hi, double rho_lo,
+                        Grad A0, cudaStream_t s) {
     const long long N = (long long)L.Lx * L.Ly * L.Lz;
     const int T = 256;
     const unsigned blocks = (unsigned)((N + T - 1) / T);
-    if (prec == 0) k_init<double><<<blocks, T, 0, s>>>((double*)f, L, R, xi, rho_hi, rho_lo, k);
-    else k_init<float><<<blocks, T, 0, s>>>((float*)f, L, R, xi, rho_hi, rho_lo, k);
+    if (prec == 0) k_init<double><<<blocks, T, 0, s>>>((double*)f, L, R, xi, rho_hi, rho_lo, A0);
+    else k_init<float><<<blocks, T, 0, s>>>((float*)f, L, R, xi, rho_hi, rho_lo, A0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Knots k, CentreParts cp,
-                         const long long* d_step, int* d_err, cudaStream_t s) {
+cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Grad A, CentreParts cp, int* d_err,
+                         cudaStream_t s) {
     const long long n = 2LL * (L.Ly + 2) * (L.Lz + 2) + 2LL * L.Lx * (L.Lz + 2) + 2LL * L.Lx * L.Ly;
     const int T = 256;
     const unsigned blocks = (unsigned)((n + T - 1) / T);
-    if (prec == 0) k_ghost<double><<<blocks, T, 0, s>>>((double*)f, L, m, k, cp, d_step, d_err);
-    else k_ghost<float><<<blocks, T, 0, s>>>((float*)f, L, m, k, cp, d_step, d_err);
+    if (prec == 0) k_ghost<double><<<blocks, T, 0, s>>>((double*)f, L, m, A, cp, d_err);
+    else k_ghost<float><<<blocks, T, 0, s>>>((float*)f, L, m, A, cp, d_err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_centre(int prec, const void* f, const Layout& L, CentreParts cp, cudaStream_t s) {
-    if (prec == 0) k_centre<double><<<cp.n, 256, 0, s>>>((const double*)f, L, cp.p);
-    else k_centre<float><<<cp.n, 256, 0, s>>>((const float*)f, L, cp.p);
+    if (prec == 0) k_centre<double><<<cp.n, 256, 0, s>>>((const double*)f, L, cp);
+    else k_centre<float><<<cp.n, 256, 0, s>>>((const float*)f, L, cp);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stream_collide(int prec, const void* src, void* dst, const Layout& L, const Model& m,
-                                  const Shape& sh, CentreParts cp, long long* d_step, int step_inc, int* d_err,
-                                  cudaStream_t s) {
-    if (prec == 0) return stream_collide_t<double, double, kMaxThreadsF64>(src, dst, L, m, sh, cp, d_step, step_inc, d_err, s);
-    return stream_collide_t<float, float, kMaxThreadsF32>(src, dst, L, m, sh, cp, d_step, step_inc, d_err, s);
+                                  const Shape& sh, CentreParts cp, int* d_err, cudaStream_t s) {
+    if (prec == 0) return stream_collide_t<double, double, kMaxThreadsF64>(src, dst, L, m, sh, cp, d_err, s);
+    return stream_collide_t<float, float, kMaxThreadsF32>(src, dst, L, m, sh, cp, d_err, s);
 }
 
 }  // namespace lbmgb
