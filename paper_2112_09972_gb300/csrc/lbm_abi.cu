@@ -242,7 +242,7 @@ int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[
     c->prec = o.precision == LBM_FP64 ? 0 : 1;
     c->elem = c->prec == 0 ? 8 : 4;
     c->L = make_layout(box[0], box[1], box[2], c->elem);
-    c->shape = choose_shape(c->L, c->elem, o.tile_y, o.z_chunk, c->num_sms);
+    c->shape = choose_shape(c->L, c->elem, o.bc == LBM_BC_PERIODIC_TEST, o.tile_y, o.z_chunk, c->num_sms);
     c->cur = 0;
     c->stream = (cudaStream_t)o.cuda_stream;
     c->own_stream = false;

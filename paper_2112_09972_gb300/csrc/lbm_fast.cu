@@ -1,0 +1,380 @@
+// Row-tiled, cluster-pipelined variant of the fused pull-stream + Shan-Chen
+// force + collision step (Sec. 2, Eqs. 6-10 of Milan et al., arXiv:2112.09972)
+// for boxes whose x extent is one CTA row (Lx = TX in {32, 64, 128}), fp32.
+//
+// Work decomposition.  A CTA of TX threads owns one row y of the box and
+// marches a chunk of z planes; CY consecutive rows form a thread-block
+// cluster.  Per plane and thread (one node x):
+//   * the 38 populations pulled into the node (x - c_i) are copied from HBM
+//     into a three-stage shared-memory ring with cp.async, two planes ahead
+//     of the plane being collided, so the copies of plane z+2 are in flight
+//     while plane z is collided;
+//   * the node's post-streaming densities go into a four-slot ring of
+//     density planes in shared memory;
+//   * the force (Eq. 7) reads the 18 neighbour densities: those of its own
+//     row from its own ring, those of rows y -/+ 1 from the rings of the
+//     neighbouring CTAs of the cluster through distributed shared memory.
+//     Only the two rows just outside the cluster are pulled a second time
+//     (ratio 2/CY); that work is split evenly over the CTAs of the cluster,
+//     which write the densities into the edge CTAs' rings remotely.
+// One cluster barrier per plane publishes the densities.  DRAM therefore sees
+// one read and one write of every population plus (2/CY) of a read from L2.
+//
+// Sums over opposite velocity pairs are differenced first (c_{2k} = -c_{2k-1}),
+// and the equilibria of a pair share their even part.
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "lbm_internal.h"
+#include "lbm_lattice.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace lbmgb {
+namespace {
+
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+struct FastModel {
+    float inv_tau[2], tau[2], G, rho_b[2];
+};
+
+template <int TX, int CY>
+struct FastLayout {
+    static constexpr int RW = TX + 2;              // ring row width (x halo columns -1, TX)
+    static constexpr int HN = 2 * TX / CY;         // outer-halo nodes pulled per CTA
+    static constexpr int STAGE = 38 * TX;          // floats per population stage
+    static constexpr int HSTAGE = 38 * HN;         // floats per outer-halo stage
+    static constexpr int RING = 4 * 2 * 3 * RW;    // [slot][component][row -1..1][col]
+    static constexpr size_t bytes = sizeof(float) * (3 * STAGE + 3 * HSTAGE + RING);
+};
+
+template <int TX, int CY>
+__global__ void __launch_bounds__(TX, 2)
+    k_stream_collide_rows(const float* __restrict__ src, float* __restrict__ dst, Layout L, FastModel m, int zchunk,
+                          CentreParts cp, int* __restrict__ d_err) {
+    using FL = FastLayout<TX, CY>;
+    constexpr int RW = FL::RW, HN = FL::HN;
+    extern __shared__ __align__(16) float sm[];
+    float* stage = sm;                          // [3][38][TX]
+    float* hstage = stage + 3 * FL::STAGE;      // [3][38][HN]
+    float* ring = hstage + 3 * FL::HSTAGE;      // [4][2][3][RW]
+    __shared__ double red[4 * ((TX + 31) / 32)];
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int x = threadIdx.x;
+    const int y = blockIdx.y;
+    const int rank = (int)cluster.block_rank();  // == y % CY for cluster dims (1, CY, 1)
+    const int Y0 = y - rank;
+    const int zc0 = blockIdx.z * zchunk;
+    const int zc1 = min(zc0 + zchunk, L.Lz);
+
+    // Outer-halo node handled by this thread (threads x < HN): the first half
+    // of them cover row Y0 - 1 (kept in rank 0's ring row -1), the second half
+    // row Y0 + CY (kept in rank CY-1's ring row +1), TX/CY columns per CTA.
+    const bool hthr = x < HN;
+    const int hside = x < HN / 2 ? 0 : 1;
+    const int hcol = rank * (HN / 2) + (x % (HN / 2));
+    const int hy = hside ? Y0 + CY : Y0 - 1;
+    const bool hin = hy >= 0 && hy < L.Ly;
+    float* hring = cluster.map_shared_rank(ring, hside ? CY - 1 : 0) + (hside ? 2 : 0) * RW + hcol + 1;
+
+    // Density rows the force reads: own row, and rows y -/+ 1 from the
+    // neighbouring CTAs (or from this CTA's outer-halo rows at the cluster edge).
+    const float* row0 = ring + 1 * RW + 1 + x;
+    const float* rowB = (rank > 0 ? cluster.map_shared_rank(ring, rank - 1) + 1 * RW : ring) + 1 + x;
+    const float* rowA = (rank < CY - 1 ? cluster.map_shared_rank(ring, rank + 1) + 1 * RW : ring + 2 * RW) + 1 + x;
+
+    // ring[slot][s][row][col] is at ((slot * 2 + s) * 3 + row + 1) * RW + col + 1
+    for (int e = x; e < FL::RING; e += TX) ring[e] = m.rho_b[(e / (3 * RW)) & 1];
+    cluster.sync();  // prefill before any remote halo write
+
+    const long long node0 = L.at(0, 0, x, y, 0);      // (s=0, i=0, x, y, z=0)
+    const long long hnode0 = L.at(0, 0, hcol, hin ? hy : 0, 0);
+
+    // Issue the cp.async copies of plane p into stage p % 3 (always one group).
+    auto issue = [&](int p) {
+        if (p >= 0 && p < L.Lz) {
+            float* st = stage + ((p + 3) % 3) * FL::STAGE + x;
+            const long long b = node0 + (long long)p * L.plane;
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < 19; ++i)
+                    cp_async4(st + (s * 19 + i) * TX,
+                              src + b + (long long)(s * 19 + i) * L.array -
+                                  ((long long)cz_(i) * L.plane + (long long)cy_(i) * L.pitch + cx_(i)));
+            if (hthr && hin) {
+                float* hs = hstage + ((p + 3) % 3) * FL::HSTAGE + x;
+                const long long hb = hnode0 + (long long)p * L.plane;
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int i = 0; i < 19; ++i)
+                        cp_async4(hs + (s * 19 + i) * HN,
+                                  src + hb + (long long)(s * 19 + i) * L.array -
+                                      ((long long)cz_(i) * L.plane + (long long)cy_(i) * L.pitch + cx_(i)));
+            }
+        }
+        cp_async_commit();
+    };
+    // Densities of plane p (copies landed) into ring slot p & 3.
+    auto densities = [&](int p) {
+        const int slot = p & 3;
+        const bool in = p >= 0 && p < L.Lz;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            float r = m.rho_b[s];
+            if (in) {
+                const float* st = stage + ((p + 3) % 3) * FL::STAGE + s * 19 * TX + x;
+                r = st[0];
+#pragma unroll
+                for (int i = 1; i < 19; i += 2) r += st[i * TX] + st[(i + 1) * TX];
+            }
+            ring[((slot * 2 + s) * 3 + 1) * RW + x + 1] = r;
+        }
+        if (hthr) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                float r = m.rho_b[s];
+                if (in && hin) {
+                    const float* hs = hstage + ((p + 3) % 3) * FL::HSTAGE + s * 19 * HN + x;
+                    r = hs[0];
+#pragma unroll
+                    for (int i = 1; i < 19; i += 2) r += hs[i * HN] + hs[(i + 1) * HN];
+                }
+                hring[(slot * 2 + s) * 3 * RW] = r;
+            }
+        }
+    };
+
+    float cm[4] = {0.f, 0.f, 0.f, 0.f};
+    const float px = (float)x - 0.5f * (float)(L.Lx - 1), py = (float)y - 0.5f * (float)(L.Ly - 1);
+
+    issue(zc0 - 1);
+    issue(zc0);
+    issue(zc0 + 1);
+    cp_async_wait1();
+    densities(zc0 - 1);
+    densities(zc0);
+
+    for (int z = zc0; z < zc1; ++z) {
+        if (z + 2 <= zc1) issue(z + 2);
+        else cp_async_commit();
+        cp_async_wait1();
+        densities(z + 1);
+        cluster.sync();
+
+        const int s0 = (z - 1) & 3, s1 = z & 3, s2 = (z + 1) & 3;
+        const float* st = stage + (z % 3) * FL::STAGE + x;
+        // neighbour density of component s at offset (dx, dy, dz)
+        auto nb = [&](int s, int dx, int dy, int dz) -> float {
+            const int slot = dz == 0 ? s1 : (dz > 0 ? s2 : s0);
+            const int o = (slot * 2 + s) * 3 * RW + dx;
+            return dy == 0 ? row0[o] : (dy > 0 ? rowA[o] : rowB[o]);
+        };
+        const float rho[2] = {row0[(s1 * 2 + 0) * 3 * RW], row0[(s1 * 2 + 1) * 3 * RW]};
+        // momentum (Eq. 6), opposite pairs differenced first
+        float j[2][3];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            float jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+            for (int i = 1; i < 19; i += 2) {
+                const float d = st[(s * 19 + i) * TX] - st[(s * 19 + i + 1) * TX];
+                if (cx_(i)) jx += (float)cx_(i) * d;
+                if (cy_(i)) jy += (float)cy_(i) * d;
+                if (cz_(i)) jz += (float)cz_(i) * d;
+            }
+            j[s][0] = jx; j[s][1] = jy; j[s][2] = jz;
+        }
+        // Shan-Chen force (Eq. 7) sums, neighbour pairs differenced first
+        float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+        for (int i = 1; i < 19; i += 2) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const float d = wgt<float>(i) * (nb(s, cx_(i), cy_(i), cz_(i)) - nb(s, -cx_(i), -cy_(i), -cz_(i)));
+                if (cx_(i)) acc[s][0] += (float)cx_(i) * d;
+                if (cy_(i)) acc[s][1] += (float)cy_(i) * d;
+                if (cz_(i)) acc[s][2] += (float)cz_(i) * d;
+            }
+        }
+        const float den = rho[0] * m.inv_tau[0] + rho[1] * m.inv_tau[1];
+        float up[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) up[a] = (j[0][a] * m.inv_tau[0] + j[1][a] * m.inv_tau[1]) / den;
+        if (!(isfinite(rho[0]) && isfinite(rho[1]))) atomicOr(d_err, 1);
+        {
+            const float phi = (rho[0] - rho[1]) / (rho[0] + rho[1]);
+            const float w = phi > 0.f ? phi : 0.f;
+            cm[0] += w;
+            cm[1] += w * px;
+            cm[2] += w * py;
+            cm[3] += w * ((float)z - 0.5f * (float)(L.Lz - 1));
+        }
+        const long long b = L.at(0, 0, x, y, z);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const float sh = -m.G * m.tau[s];  // tau_s F^s / rho_s per unit of the other sum
+            const float ux = up[0] + sh * acc[1 - s][0];
+            const float uy = up[1] + sh * acc[1 - s][1];
+            const float uz = up[2] + sh * acc[1 - s][2];
+            const float u2x = 1.5f * (ux * ux + uy * uy + uz * uz);
+            const float it = m.inv_tau[s];
+            const float r = rho[s];
+            {
+                const float f = st[(s * 19) * TX];
+                const float g = r * wgt<float>(0) * (1.f - u2x);
+                dst[b + (long long)(s * 19) * L.array] = f - (f - g) * it;
+            }
+#pragma unroll
+            for (int i = 1; i < 19; i += 2) {
+                const float cu = (float)cx_(i) * ux + (float)cy_(i) * uy + (float)cz_(i) * uz;
+                const float rw = r * wgt<float>(i);
+                const float even = rw * (1.f + 4.5f * cu * cu - u2x);
+                const float odd = rw * (3.f * cu);
+                const float fa = st[(s * 19 + i) * TX], fb = st[(s * 19 + i + 1) * TX];
+                const float ga = even + odd, gb = even - odd;
+                dst[b + (long long)(s * 19 + i) * L.array] = fa - (fa - ga) * it;
+                dst[b + (long long)(s * 19 + i + 1) * L.array] = fb - (fb - gb) * it;
+            }
+        }
+    }
+    // neighbours may still read this CTA's ring for their last plane
+    cluster.sync();
+
+    // centre-of-mass partials of the written state (fixed-order reduction)
+    const int lane = x & 31, warp = x >> 5;
+    constexpr int nwarps = (TX + 31) / 32;
+    double cmd[4] = {(double)cm[0], (double)cm[1], (double)cm[2], (double)cm[3]};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double a = cmd[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) red[4 * warp + q] = a;
+    }
+    __syncthreads();
+    __shared__ unsigned last;
+    const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            double a = lane < nwarps ? red[4 * lane + q] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) cp.p[4 * cta + q] = a;
+        }
+        if (lane == 0) {
+            __threadfence();
+            last = atomicAdd(cp.counter, 1u) == total - 1 ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+    if (last && warp == 0) {
+        __threadfence();
+        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        for (unsigned bb = lane; bb < total; bb += 32)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s4[q] += __ldcg(cp.p + 4LL * bb + q);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s4[q] += __shfl_down_sync(0xffffffffu, s4[q], o);
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cp.sum[q] = s4[q];
+            *cp.counter = 0u;
+        }
+    }
+}
+
+template <int TX, int CY>
+cudaError_t launch_rows(const float* src, float* dst, const Layout& L, const Model& m, int zchunk, int nchunks,
+                        CentreParts cp, int* d_err, cudaStream_t s) {
+    auto k = k_stream_collide_rows<TX, CY>;
+    const size_t smem = FastLayout<TX, CY>::bytes;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    FastModel fm;
+    for (int q = 0; q < 2; ++q) {
+        fm.inv_tau[q] = (float)(1.0 / m.tau[q]);
+        fm.tau[q] = (float)m.tau[q];
+        fm.rho_b[q] = (float)m.rho_b[q];
+    }
+    fm.G = (float)m.G;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1, L.Ly, nchunks);
+    cfg.blockDim = dim3(TX, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = CY;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, src, dst, L, fm, zchunk, cp, d_err);
+}
+
+template <int TX, int CY>
+int max_clusters() {
+    auto k = k_stream_collide_rows<TX, CY>;
+    const size_t smem = FastLayout<TX, CY>::bytes;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1, CY, 1);
+    cfg.blockDim = dim3(TX, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = CY;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+constexpr int kRowCluster = 8;
+
+}  // namespace
+
+bool rows_kernel_applies(const Layout& L, int prec, int periodic) {
+    if (prec != 1 || periodic) return false;
+    if (L.Lx != 32 && L.Lx != 64 && L.Lx != 128) return false;
+    return L.Ly % kRowCluster == 0 && L.Lz >= 2;
+}
+
+int rows_kernel_resident_ctas(const Layout& L) {
+    int n = 0;
+    if (L.Lx == 128) n = max_clusters<128, kRowCluster>();
+    else if (L.Lx == 64) n = max_clusters<64, kRowCluster>();
+    else if (L.Lx == 32) n = max_clusters<32, kRowCluster>();
+    return n * kRowCluster;
+}
+
+cudaError_t launch_stream_collide_rows(const void* src, void* dst, const Layout& L, const Model& m, int zchunk,
+                                       CentreParts cp, int* d_err, cudaStream_t s) {
+    const int nchunks = (L.Lz + zchunk - 1) / zchunk;
+    if (L.Lx == 128) return launch_rows<128, kRowCluster>((const float*)src, (float*)dst, L, m, zchunk, nchunks, cp, d_err, s);
+    if (L.Lx == 64) return launch_rows<64, kRowCluster>((const float*)src, (float*)dst, L, m, zchunk, nchunks, cp, d_err, s);
+    if (L.Lx == 32) return launch_rows<32, kRowCluster>((const float*)src, (float*)dst, L, m, zchunk, nchunks, cp, d_err, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lbmgb

@@ -62,6 +62,7 @@ struct Grad {
 
 // Launch shape of the stream-collide kernel.
 struct Shape {
+    int rows;       // 1: the row-tiled cluster kernel (lbm_fast.cu), 0: the generic tile kernel
     int tx, ty;     // tile of the x-y plane per CTA
     int zchunk;     // z planes marched per CTA
     dim3 grid;
@@ -70,7 +71,7 @@ struct Shape {
 };
 
 // ---- launchers (lbm_step.cu) ----
-Shape choose_shape(const Layout& L, int elem_bytes, int ty_req, int zchunk_req, int num_sms);
+Shape choose_shape(const Layout& L, int elem_bytes, int periodic, int ty_req, int zchunk_req, int num_sms);
 cudaError_t launch_init(int prec, void* f, const Layout& L, double R, double xi, double rho_hi, double rho_lo,
                         Grad A0, cudaStream_t s);
 cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Grad A, CentreParts cp, int* d_err,
@@ -79,6 +80,12 @@ cudaError_t launch_stream_collide(int prec, const void* src, void* dst, const La
                                   const Shape& sh, CentreParts cp, int* d_err, cudaStream_t s);
 // Centre-of-mass partials of the stored populations f (cp.n CTAs, grid-stride).
 cudaError_t launch_centre(int prec, const void* f, const Layout& L, CentreParts cp, cudaStream_t s);
+
+// ---- row-tiled cluster kernel (lbm_fast.cu): fp32, ghost boundary, Lx in {32, 64, 128}, Ly % 8 == 0 ----
+bool rows_kernel_applies(const Layout& L, int prec, int periodic);
+int rows_kernel_resident_ctas(const Layout& L);
+cudaError_t launch_stream_collide_rows(const void* src, void* dst, const Layout& L, const Model& m, int zchunk,
+                                       CentreParts cp, int* d_err, cudaStream_t s);
 
 // ---- launchers (lbm_reduce.cu) ----
 // Ten moments of w = max(phi, 0) and the deformation: result[0..9] moments,

@@ -31,51 +31,10 @@
 #include <cuda_runtime.h>
 
 #include "lbm_internal.h"
+#include "lbm_lattice.cuh"
 
 namespace lbmgb {
 namespace {
-
-// D3Q19 velocities in the order documented in lbm.h: direction 2k is the
-// opposite of direction 2k-1.  Every loop over directions is unrolled, so
-// these fold to immediates.
-__host__ __device__ __forceinline__ constexpr int cx_(int i) {
-    constexpr int t[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
-    return t[i];
-}
-__host__ __device__ __forceinline__ constexpr int cy_(int i) {
-    constexpr int t[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
-    return t[i];
-}
-__host__ __device__ __forceinline__ constexpr int cz_(int i) {
-    constexpr int t[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
-    return t[i];
-}
-
-template <typename C>
-__host__ __device__ __forceinline__ constexpr C wgt(int i) {
-    return i == 0 ? C(1) / C(3) : (i < 7 ? C(1) / C(18) : C(1) / C(36));
-}
-
-// Eq. 8 with u2x = 1.5 |u|^2 precomputed.
-template <typename C>
-__device__ __forceinline__ C feq(int i, C rho, C ux, C uy, C uz, C u2x) {
-    const C cu = C(cx_(i)) * ux + C(cy_(i)) * uy + C(cz_(i)) * uz;
-    return rho * wgt<C>(i) * (C(1) + C(3) * cu + C(4.5) * cu * cu - u2x);
-}
-
-__device__ __forceinline__ int wrap(int a, int n) {
-    a = a < 0 ? a + n : a;
-    return a >= n ? a - n : a;
-}
-
-// Sum of 19 values as f0 + sum over opposite pairs.
-template <typename C>
-__device__ __forceinline__ C sum19(const C (&f)[19]) {
-    C s = f[0];
-#pragma unroll
-    for (int i = 1; i < 19; i += 2) s += f[i] + f[i + 1];
-    return s;
-}
 
 // ----------------------------------------------------------------------------
 // Initial state.
@@ -104,7 +63,7 @@ __global__ void k_init(S* __restrict__ f, Layout L, double R, double xi, double 
 // x = -1 and x = Lx over y, z in [-1, L]; y = -1 and y = Ly over x in [0, Lx),
 // z in [-1, Lz]; z = -1 and z = Lz over x in [0, Lx), y in [0, Ly).  A ghost
 // population i is written only if it streams into the box (y + c_i inside).
-template <typename S>
+template <typename S, typename C>
 __global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, Model m, Grad A, CentreParts cp,
                                                int* __restrict__ d_err) {
     // frame origin: the droplet's centre of mass of the current state
@@ -143,12 +102,14 @@ __global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, Mode
     } else {
         return;
     }
-    const double px = x - 0.5 * (L.Lx - 1) - xc, py = y - 0.5 * (L.Ly - 1) - yc, pz = z - 0.5 * (L.Lz - 1) - zc;
-    const double ux = A.a[0] * px + A.a[1] * py + A.a[2] * pz;
-    const double uy = A.a[3] * px + A.a[4] * py + A.a[5] * pz;
-    const double uz = A.a[6] * px + A.a[7] * py + A.a[8] * pz;
-    const double usq = ux * ux + uy * uy + uz * uz;
-    const double u2x = 1.5 * usq;
+    // position relative to the frame origin, then the flow and Eq. 8 in the
+    // compute type of the populations (fp64 arithmetic is slow on this part)
+    const C px = (C)(x - 0.5 * (L.Lx - 1) - xc), py = (C)(y - 0.5 * (L.Ly - 1) - yc), pz = (C)(z - 0.5 * (L.Lz - 1) - zc);
+    const C ux = (C)A.a[0] * px + (C)A.a[1] * py + (C)A.a[2] * pz;
+    const C uy = (C)A.a[3] * px + (C)A.a[4] * py + (C)A.a[5] * pz;
+    const C uz = (C)A.a[6] * px + (C)A.a[7] * py + (C)A.a[8] * pz;
+    const C usq = ux * ux + uy * uy + uz * uz;
+    const C u2x = C(1.5) * usq;
     bool any = false;
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
@@ -156,9 +117,9 @@ __global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, Mode
         if (xi < 0 || xi >= L.Lx || yi < 0 || yi >= L.Ly || zi < 0 || zi >= L.Lz) continue;
         any = true;
 #pragma unroll
-        for (int s = 0; s < 2; ++s) f[L.at(s, i, x, y, z)] = (S)feq<double>(i, m.rho_b[s], ux, uy, uz, u2x);
+        for (int s = 0; s < 2; ++s) f[L.at(s, i, x, y, z)] = (S)feq<C>(i, (C)m.rho_b[s], ux, uy, uz, u2x);
     }
-    if (any && usq > m.mach2) atomicOr(d_err, 2);
+    if (any && (double)usq > m.mach2) atomicOr(d_err, 2);
 }
 
 // Fixed-order reduction of the per-CTA centre partials by the last CTA to
@@ -473,8 +434,26 @@ Layout make_layout(int Lx, int Ly, int Lz, int elem_bytes) {
     return L;
 }
 
-Shape choose_shape(const Layout& L, int elem_bytes, int ty_req, int zchunk_req, int num_sms) {
+Shape choose_shape(const Layout& L, int elem_bytes, int periodic, int ty_req, int zchunk_req, int num_sms) {
     Shape sh;
+    sh.rows = 0;
+    if (ty_req <= 0 && rows_kernel_applies(L, elem_bytes == 4 ? 1 : 0, periodic)) {
+        // one CTA per row, as many z chunks as fill the resident CTA slots once
+        const int resident = rows_kernel_resident_ctas(L);
+        if (resident > 0) {
+            int chunks = zchunk_req > 0 ? (L.Lz + zchunk_req - 1) / zchunk_req : resident / L.Ly;
+            if (chunks < 1) chunks = 1;
+            if (chunks > L.Lz) chunks = L.Lz;
+            sh.rows = 1;
+            sh.tx = L.Lx;
+            sh.ty = 1;
+            sh.zchunk = (L.Lz + chunks - 1) / chunks;
+            sh.grid = dim3(1, L.Ly, (L.Lz + sh.zchunk - 1) / sh.zchunk);
+            sh.threads = L.Lx;
+            sh.smem = 0;
+            return sh;
+        }
+    }
     const int maxt = elem_bytes == 8 ? kMaxThreadsF64 : kMaxThreadsF32;
     sh.tx = L.Lx <= maxt ? L.Lx : 128;
     if (sh.tx > maxt) sh.tx = maxt;
@@ -517,8 +496,8 @@ cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Gra
     const long long n = 2LL * (L.Ly + 2) * (L.Lz + 2) + 2LL * L.Lx * (L.Lz + 2) + 2LL * L.Lx * L.Ly;
     const int T = 256;
     const unsigned blocks = (unsigned)((n + T - 1) / T);
-    if (prec == 0) k_ghost<double><<<blocks, T, 0, s>>>((double*)f, L, m, A, cp, d_err);
-    else k_ghost<float><<<blocks, T, 0, s>>>((float*)f, L, m, A, cp, d_err);
+    if (prec == 0) k_ghost<double, double><<<blocks, T, 0, s>>>((double*)f, L, m, A, cp, d_err);
+    else k_ghost<float, float><<<blocks, T, 0, s>>>((float*)f, L, m, A, cp, d_err);
     return cudaGetLastError();
 }
 
@@ -530,6 +509,7 @@ cudaError_t launch_centre(int prec, const void* f, const Layout& L, CentreParts 
 
 cudaError_t launch_stream_collide(int prec, const void* src, void* dst, const Layout& L, const Model& m,
                                   const Shape& sh, CentreParts cp, int* d_err, cudaStream_t s) {
+    if (sh.rows) return launch_stream_collide_rows(src, dst, L, m, sh.zchunk, cp, d_err, s);
     if (prec == 0) return stream_collide_t<double, double, kMaxThreadsF64>(src, dst, L, m, sh, cp, d_err, s);
     return stream_collide_t<float, float, kMaxThreadsF32>(src, dst, L, m, sh, cp, d_err, s);
 }

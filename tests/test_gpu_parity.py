@@ -54,10 +54,14 @@ def c1_reference(oracle_mod):
     return dict(A=A, ra=ra, rb=rb, u=u, D=D, axes=axes, lam=lam, mass=o.checksums()[0])
 
 
-@pytest.mark.parametrize("precision,tol_field,tol_D", [("fp64", 1e-10, 1e-9), ("fp32", 1e-4, 1e-3)])
-def test_config1_parity_after_2000_steps(built, c1_reference, precision, tol_field, tol_D):
+@pytest.mark.parametrize("precision,tile_y,tol_field,tol_D",
+                         [("fp64", 0, 1e-10, 1e-9), ("fp32", 0, 1e-4, 1e-3), ("fp32", 8, 1e-4, 1e-3)])
+def test_config1_parity_after_2000_steps(built, c1_reference, precision, tile_y, tol_field, tol_D):
+    """fp32 runs both stream-collide kernels: the row-tiled cluster kernel
+    (automatic for a 32-wide box) and the generic tile kernel (tile_y = 8)."""
     w = workloads.C1_PARITY
-    g = DropletLBM((w.box,) * 3, w.R, w.visc, w.G, precision=precision, rho_hi=w.rho_hi, rho_lo=w.rho_lo, xi=w.xi)
+    g = DropletLBM((w.box,) * 3, w.R, w.visc, w.G, precision=precision, rho_hi=w.rho_hi, rho_lo=w.rho_lo, xi=w.xi,
+                   tile_y=tile_y)
     g.set_gradient(c1_reference["A"], 0)
     g.step(w.steps)
     ra, rb, u = g.fields()
@@ -108,9 +112,10 @@ def test_interpolated_gradient_knots(built, oracle_mod):
     assert rel_linf(g.populations(), o.populations()) <= 1e-12
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
-def test_full_size_single_step_128(built, oracle_mod, precision, tol):
-    """128^3 with the benchmark's launch shape: one step from an oracle state."""
+@pytest.mark.parametrize("precision,tile_y,tol", [("fp64", 0, 1e-12), ("fp32", 0, 1e-5), ("fp32", 4, 1e-5)])
+def test_full_size_single_step_128(built, oracle_mod, precision, tile_y, tol):
+    """128^3 with the benchmark's launch shape (fp32, automatic: the row-tiled
+    cluster kernel) and the generic tile kernel: one step from an oracle state."""
     w = workloads.C2_THROUGHPUT
     box = (w.box,) * 3
     hist = w.gradient_history(3)
@@ -119,7 +124,7 @@ def test_full_size_single_step_128(built, oracle_mod, precision, tol):
     o.step(hist[0])
     f0 = inputs.perturbed_populations(o.populations(), 1e-4, seed=5)
     o.set_populations(f0)
-    g = DropletLBM(box, w.R, w.visc, w.G, precision=precision, rho_hi=w.rho_hi, rho_lo=w.rho_lo)
+    g = DropletLBM(box, w.R, w.visc, w.G, precision=precision, rho_hi=w.rho_hi, rho_lo=w.rho_lo, tile_y=tile_y)
     g.set_populations(f0)
     g.set_gradient_table([0, 1, 2], hist)
     # the context's step counter is 0; the oracle steps with A(t=0) as well
@@ -131,7 +136,7 @@ def test_full_size_single_step_128(built, oracle_mod, precision, tol):
 def test_moments_and_deformation_match_oracle(built, oracle_mod):
     box = (40, 36, 33)
     o, g = _pair(oracle_mod, box, 8.0, (1.0, 1.0), 3.5, "fp64")
-    hist = inputs.ou_gradient_history(30, 10.0, 20.0, seed=9)
+    hist = inputs.ou_gradient_history(30, 10.0, 400.0, seed=9)
     o.init_droplet(8.0, 1.0, 1.0, workloads.RHO_LO, hist[0])
     o.run(30, np.arange(30), hist)
     g.set_populations(o.populations())
@@ -233,3 +238,20 @@ def test_box_frame_short_run(built, oracle_mod):
     o.run(30, [0.0], [A])
     g.step(30)
     assert rel_linf(g.populations(), o.populations()) <= 1e-12
+
+
+@pytest.mark.parametrize("box", [(64, 24, 20), (128, 16, 9), (32, 40, 3)])
+def test_row_cluster_kernel_shapes(built, oracle_mod, box):
+    """The row-tiled cluster kernel on other widths, cluster counts and short
+    z extents (ragged last z chunk), fp32, 12 steps from a perturbed state."""
+    tau = (1.0, 1.0)
+    o, g = _pair(oracle_mod, box, 1.5, tau, 3.5, "fp32", z_chunk=2)
+    hist = inputs.ou_gradient_history(12, 20.0, 600.0, seed=4)
+    o.init_droplet(1.5, 1.0, 1.0, workloads.RHO_LO, hist[0])
+    f0 = inputs.perturbed_populations(o.populations(), 1e-3, seed=8)
+    o.set_populations(f0)
+    g.set_populations(f0)
+    g.set_gradient_table(np.arange(12), hist)
+    o.run(12, np.arange(12), hist)
+    g.step(12)
+    assert rel_linf(g.populations(), o.populations()) <= 1e-5
