@@ -258,11 +258,12 @@ int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_partials, sizeof(double) * 10 * c->red_blocks);
     c->centre.n = (int)(c->shape.grid.x * c->shape.grid.y * c->shape.grid.z);
-    if (e == cudaSuccess) e = cudaMalloc(&c->centre.p, sizeof(double) * 4 * (c->centre.n + 1) + 16);
+    const size_t centre_bytes = sizeof(double) * (4 * (size_t)c->centre.n + 8) + 16;
+    if (e == cudaSuccess) e = cudaMalloc(&c->centre.p, centre_bytes);
     if (e == cudaSuccess) {
         c->centre.sum = c->centre.p + 4 * c->centre.n;
-        c->centre.counter = (unsigned*)(c->centre.sum + 4);
-        e = cudaMemsetAsync(c->centre.p, 0, sizeof(double) * 4 * (c->centre.n + 1) + 16, c->stream);
+        c->centre.counter = (unsigned*)(c->centre.sum + 8);
+        e = cudaMemsetAsync(c->centre.p, 0, centre_bytes, c->stream);
     }
     if (e == cudaSuccess) e = cudaMalloc(&c->d_result, sizeof(double) * 32);
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_result, sizeof(double) * 32);
@@ -463,7 +464,7 @@ int lbm_save(lbm_ctx* c, const char* path) {
     int st = lbm_get_populations(c, pop.data());
     if (st) return st;
     // the frame origin of the next step is part of the state
-    std::vector<double> cparts((size_t)4 * c->centre.n);
+    std::vector<double> cparts((size_t)4 * c->centre.n + 8);
     LBM_TRY(cudaMemcpy(cparts.data(), c->centre.p, sizeof(double) * cparts.size(), cudaMemcpyDeviceToHost));
     CkptHeader h;
     memset(&h, 0, sizeof(h));
@@ -518,7 +519,7 @@ int lbm_load(lbm_ctx* c, const char* path) {
         kt.resize((size_t)h.nknots);
         kA.resize((size_t)h.nknots * 9);
         pop.resize(E);
-        cparts.resize((size_t)h.ncentre * 4);
+        cparts.resize((size_t)h.ncentre * 4 + 8);
     } catch (...) {
         fclose(fp);
         return LBM_ENOMEM;

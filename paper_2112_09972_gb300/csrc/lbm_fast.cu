@@ -292,6 +292,9 @@ __global__ void __launch_bounds__(TX, 2)
         if (lane == 0) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) cp.sum[q] = s4[q];
+            // frame origin x_c = sum w x / sum w (box centre when there is no droplet)
+            const bool have = s4[0] > 0.0;
+            for (int q = 0; q < 3; ++q) cp.sum[4 + q] = have ? s4[1 + q] / s4[0] : 0.0;
             *cp.counter = 0u;
         }
     }

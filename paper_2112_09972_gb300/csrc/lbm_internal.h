@@ -51,7 +51,7 @@ struct Model {
 struct CentreParts {
     double* p;          // [n][4]
     int n;              // CTAs of the stream-collide launch
-    double* sum;        // [4]
+    double* sum;        // [8]: the four sums, then the frame origin x_c, y_c, z_c
     unsigned* counter;  // CTAs finished, 0 between launches
 };
 

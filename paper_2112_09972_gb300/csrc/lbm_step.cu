@@ -67,14 +67,11 @@ template <typename S, typename C>
 __global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, Model m, Grad A, CentreParts cp,
                                                int* __restrict__ d_err) {
     // frame origin: the droplet's centre of mass of the current state
-    double xc = 0.0, yc = 0.0, zc = 0.0;
+    C xc = C(0), yc = C(0), zc = C(0);
     if (m.droplet_frame) {
-        const double w0 = cp.sum[0];
-        if (w0 > 0.0) {
-            xc = cp.sum[1] / w0;
-            yc = cp.sum[2] / w0;
-            zc = cp.sum[3] / w0;
-        }
+        xc = (C)cp.sum[4];
+        yc = (C)cp.sum[5];
+        zc = (C)cp.sum[6];
     }
     const long long nX = (long long)(L.Ly + 2) * (L.Lz + 2);
     const long long nY = (long long)L.Lx * (L.Lz + 2);
@@ -104,7 +101,8 @@ __global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, Mode
     }
     // position relative to the frame origin, then the flow and Eq. 8 in the
     // compute type of the populations (fp64 arithmetic is slow on this part)
-    const C px = (C)(x - 0.5 * (L.Lx - 1) - xc), py = (C)(y - 0.5 * (L.Ly - 1) - yc), pz = (C)(z - 0.5 * (L.Lz - 1) - zc);
+    const C px = (C(x) - C(0.5) * C(L.Lx - 1)) - xc, py = (C(y) - C(0.5) * C(L.Ly - 1)) - yc,
+            pz = (C(z) - C(0.5) * C(L.Lz - 1)) - zc;
     const C ux = (C)A.a[0] * px + (C)A.a[1] * py + (C)A.a[2] * pz;
     const C uy = (C)A.a[3] * px + (C)A.a[4] * py + (C)A.a[5] * pz;
     const C uz = (C)A.a[6] * px + (C)A.a[7] * py + (C)A.a[8] * pz;
@@ -167,6 +165,9 @@ __device__ void centre_epilogue(double (&cm)[4], CentreParts cp, double* scratch
         if (lane == 0) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) cp.sum[q] = s4[q];
+            // frame origin x_c = sum w x / sum w (box centre when there is no droplet)
+            const bool have = s4[0] > 0.0;
+            for (int q = 0; q < 3; ++q) cp.sum[4 + q] = have ? s4[1 + q] / s4[0] : 0.0;
             *cp.counter = 0u;
         }
     }
