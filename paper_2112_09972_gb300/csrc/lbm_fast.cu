@@ -5,12 +5,12 @@
 // Work decomposition.  A CTA of TX threads owns one row y of the box and
 // marches a chunk of z planes; CY consecutive rows form a thread-block
 // cluster.  Per plane and thread (one node x):
-//   * the 38 populations pulled into the node (x - c_i) are copied from HBM
-//     into a three-stage shared-memory ring with cp.async, two planes ahead
-//     of the plane being collided, so the copies of plane z+2 are in flight
-//     while plane z is collided;
-//   * the node's post-streaming densities go into a four-slot ring of
-//     density planes in shared memory;
+//   * the 38 populations pulled into the node (x - c_i) are read and summed
+//     into the node's post-streaming densities, which go into a four-slot
+//     ring of density planes in shared memory; one plane later the same 38
+//     values are read again for the collision (that second read is served by
+//     L1/L2).  Holding no populations on chip keeps each CTA at a few KB of
+//     shared memory and few registers, so many CTAs per SM hide the latency;
 //   * the force (Eq. 7) reads the 18 neighbour densities: those of its own
 //     row from its own ring, those of rows y -/+ 1 from the rings of the
 //     neighbouring CTAs of the cluster through distributed shared memory.
@@ -18,7 +18,8 @@
 //     (ratio 2/CY); that work is split evenly over the CTAs of the cluster,
 //     which write the densities into the edge CTAs' rings remotely.
 // One cluster barrier per plane publishes the densities.  DRAM therefore sees
-// one read and one write of every population plus (2/CY) of a read from L2.
+// one read and one write of every population; L2 serves the second read and
+// the (2/CY) outer-halo reads.
 //
 // Sums over opposite velocity pairs are differenced first (c_{2k} = -c_{2k-1}),
 // and the equilibria of a pair share their even part.
@@ -34,13 +35,6 @@ namespace cg = cooperative_groups;
 namespace lbmgb {
 namespace {
 
-__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
 struct FastModel {
     float inv_tau[2], tau[2], G, rho_b[2];
 };
@@ -49,22 +43,23 @@ template <int TX, int CY>
 struct FastLayout {
     static constexpr int RW = TX + 2;              // ring row width (x halo columns -1, TX)
     static constexpr int HN = 2 * TX / CY;         // outer-halo nodes pulled per CTA
-    static constexpr int STAGE = 38 * TX;          // floats per population stage
-    static constexpr int HSTAGE = 38 * HN;         // floats per outer-halo stage
     static constexpr int RING = 4 * 2 * 3 * RW;    // [slot][component][row -1..1][col]
-    static constexpr size_t bytes = sizeof(float) * (3 * STAGE + 3 * HSTAGE + RING);
+    static constexpr size_t bytes = sizeof(float) * RING;
 };
 
-template <int TX, int CY>
-__global__ void __launch_bounds__(TX, 2)
+// Pulled population (s, i) of the node whose (s=0, i=0) element index is b.
+__device__ __forceinline__ float pulled(const float* __restrict__ src, const Layout& L, long long b, int s, int i) {
+    return __ldg(src + b + (long long)(s * 19 + i) * L.array -
+                 ((long long)cz_(i) * L.plane + (long long)cy_(i) * L.pitch + cx_(i)));
+}
+
+template <int TX, int CY, int MINB>
+__global__ void __launch_bounds__(TX, MINB)
     k_stream_collide_rows(const float* __restrict__ src, float* __restrict__ dst, Layout L, FastModel m, int zchunk,
                           CentreParts cp, int* __restrict__ d_err) {
     using FL = FastLayout<TX, CY>;
     constexpr int RW = FL::RW, HN = FL::HN;
-    extern __shared__ __align__(16) float sm[];
-    float* stage = sm;                          // [3][38][TX]
-    float* hstage = stage + 3 * FL::STAGE;      // [3][38][HN]
-    float* ring = hstage + 3 * FL::HSTAGE;      // [4][2][3][RW]
+    extern __shared__ __align__(16) float ring[];  // [4][2][3][RW]
     __shared__ double red[4 * ((TX + 31) / 32)];
 
     cg::cluster_group cluster = cg::this_cluster();
@@ -98,87 +93,64 @@ __global__ void __launch_bounds__(TX, 2)
     const long long node0 = L.at(0, 0, x, y, 0);      // (s=0, i=0, x, y, z=0)
     const long long hnode0 = L.at(0, 0, hcol, hin ? hy : 0, 0);
 
-    // Issue the cp.async copies of plane p into stage p % 3 (always one group).
-    auto issue = [&](int p) {
-        if (p >= 0 && p < L.Lz) {
-            float* st = stage + ((p + 3) % 3) * FL::STAGE + x;
-            const long long b = node0 + (long long)p * L.plane;
-#pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int i = 0; i < 19; ++i)
-                    cp_async4(st + (s * 19 + i) * TX,
-                              src + b + (long long)(s * 19 + i) * L.array -
-                                  ((long long)cz_(i) * L.plane + (long long)cy_(i) * L.pitch + cx_(i)));
-            if (hthr && hin) {
-                float* hs = hstage + ((p + 3) % 3) * FL::HSTAGE + x;
-                const long long hb = hnode0 + (long long)p * L.plane;
-#pragma unroll
-                for (int s = 0; s < 2; ++s)
-#pragma unroll
-                    for (int i = 0; i < 19; ++i)
-                        cp_async4(hs + (s * 19 + i) * HN,
-                                  src + hb + (long long)(s * 19 + i) * L.array -
-                                      ((long long)cz_(i) * L.plane + (long long)cy_(i) * L.pitch + cx_(i)));
-            }
-        }
-        cp_async_commit();
-    };
-    // Densities of plane p (copies landed) into ring slot p & 3.
+    // Post-streaming densities of plane p into ring slot p & 3 (own node and,
+    // for threads x < HN, one outer-halo node written into the edge CTA).
     auto densities = [&](int p) {
         const int slot = p & 3;
         const bool in = p >= 0 && p < L.Lz;
+        float ra = m.rho_b[0], rb = m.rho_b[1];
+        if (in) {
+            const long long b = node0 + (long long)p * L.plane;
+            ra = pulled(src, L, b, 0, 0);
+            rb = pulled(src, L, b, 1, 0);
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            float r = m.rho_b[s];
-            if (in) {
-                const float* st = stage + ((p + 3) % 3) * FL::STAGE + s * 19 * TX + x;
-                r = st[0];
-#pragma unroll
-                for (int i = 1; i < 19; i += 2) r += st[i * TX] + st[(i + 1) * TX];
+            for (int i = 1; i < 19; i += 2) {
+                ra += pulled(src, L, b, 0, i) + pulled(src, L, b, 0, i + 1);
+                rb += pulled(src, L, b, 1, i) + pulled(src, L, b, 1, i + 1);
             }
-            ring[((slot * 2 + s) * 3 + 1) * RW + x + 1] = r;
         }
+        ring[((slot * 2 + 0) * 3 + 1) * RW + x + 1] = ra;
+        ring[((slot * 2 + 1) * 3 + 1) * RW + x + 1] = rb;
         if (hthr) {
+            float ha = m.rho_b[0], hb = m.rho_b[1];
+            if (in && hin) {
+                const long long b = hnode0 + (long long)p * L.plane;
+                ha = pulled(src, L, b, 0, 0);
+                hb = pulled(src, L, b, 1, 0);
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                float r = m.rho_b[s];
-                if (in && hin) {
-                    const float* hs = hstage + ((p + 3) % 3) * FL::HSTAGE + s * 19 * HN + x;
-                    r = hs[0];
-#pragma unroll
-                    for (int i = 1; i < 19; i += 2) r += hs[i * HN] + hs[(i + 1) * HN];
+                for (int i = 1; i < 19; i += 2) {
+                    ha += pulled(src, L, b, 0, i) + pulled(src, L, b, 0, i + 1);
+                    hb += pulled(src, L, b, 1, i) + pulled(src, L, b, 1, i + 1);
                 }
-                hring[(slot * 2 + s) * 3 * RW] = r;
             }
+            hring[(slot * 2 + 0) * 3 * RW] = ha;
+            hring[(slot * 2 + 1) * 3 * RW] = hb;
         }
     };
 
     float cm[4] = {0.f, 0.f, 0.f, 0.f};
     const float px = (float)x - 0.5f * (float)(L.Lx - 1), py = (float)y - 0.5f * (float)(L.Ly - 1);
 
-    issue(zc0 - 1);
-    issue(zc0);
-    issue(zc0 + 1);
-    cp_async_wait1();
     densities(zc0 - 1);
     densities(zc0);
-
     for (int z = zc0; z < zc1; ++z) {
-        if (z + 2 <= zc1) issue(z + 2);
-        else cp_async_commit();
-        cp_async_wait1();
         densities(z + 1);
         cluster.sync();
 
         const int s0 = (z - 1) & 3, s1 = z & 3, s2 = (z + 1) & 3;
-        const float* st = stage + (z % 3) * FL::STAGE + x;
         // neighbour density of component s at offset (dx, dy, dz)
         auto nb = [&](int s, int dx, int dy, int dz) -> float {
             const int slot = dz == 0 ? s1 : (dz > 0 ? s2 : s0);
             const int o = (slot * 2 + s) * 3 * RW + dx;
             return dy == 0 ? row0[o] : (dy > 0 ? rowA[o] : rowB[o]);
         };
+        // the node's pulled populations again (second read, from L1/L2)
+        const long long bz = node0 + (long long)z * L.plane;
+        float f[2][19];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 19; ++i) f[s][i] = pulled(src, L, bz, s, i);
         const float rho[2] = {row0[(s1 * 2 + 0) * 3 * RW], row0[(s1 * 2 + 1) * 3 * RW]};
         // momentum (Eq. 6), opposite pairs differenced first
         float j[2][3];
@@ -187,7 +159,7 @@ __global__ void __launch_bounds__(TX, 2)
             float jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
             for (int i = 1; i < 19; i += 2) {
-                const float d = st[(s * 19 + i) * TX] - st[(s * 19 + i + 1) * TX];
+                const float d = f[s][i] - f[s][i + 1];
                 if (cx_(i)) jx += (float)cx_(i) * d;
                 if (cy_(i)) jy += (float)cy_(i) * d;
                 if (cz_(i)) jz += (float)cz_(i) * d;
@@ -230,9 +202,8 @@ __global__ void __launch_bounds__(TX, 2)
             const float it = m.inv_tau[s];
             const float r = rho[s];
             {
-                const float f = st[(s * 19) * TX];
                 const float g = r * wgt<float>(0) * (1.f - u2x);
-                dst[b + (long long)(s * 19) * L.array] = f - (f - g) * it;
+                dst[b + (long long)(s * 19) * L.array] = f[s][0] - (f[s][0] - g) * it;
             }
 #pragma unroll
             for (int i = 1; i < 19; i += 2) {
@@ -240,10 +211,9 @@ __global__ void __launch_bounds__(TX, 2)
                 const float rw = r * wgt<float>(i);
                 const float even = rw * (1.f + 4.5f * cu * cu - u2x);
                 const float odd = rw * (3.f * cu);
-                const float fa = st[(s * 19 + i) * TX], fb = st[(s * 19 + i + 1) * TX];
-                const float ga = even + odd, gb = even - odd;
-                dst[b + (long long)(s * 19 + i) * L.array] = fa - (fa - ga) * it;
-                dst[b + (long long)(s * 19 + i + 1) * L.array] = fb - (fb - gb) * it;
+                const float fa = f[s][i], fb = f[s][i + 1];
+                dst[b + (long long)(s * 19 + i) * L.array] = fa - (fa - (even + odd)) * it;
+                dst[b + (long long)(s * 19 + i + 1) * L.array] = fb - (fb - (even - odd)) * it;
             }
         }
     }
@@ -300,10 +270,12 @@ __global__ void __launch_bounds__(TX, 2)
     }
 }
 
+constexpr int kRowMinBlocks = 6;
+
 template <int TX, int CY>
 cudaError_t launch_rows(const float* src, float* dst, const Layout& L, const Model& m, int zchunk, int nchunks,
                         CentreParts cp, int* d_err, cudaStream_t s) {
-    auto k = k_stream_collide_rows<TX, CY>;
+    auto k = k_stream_collide_rows<TX, CY, kRowMinBlocks * 128 / TX>;
     const size_t smem = FastLayout<TX, CY>::bytes;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -331,7 +303,7 @@ cudaError_t launch_rows(const float* src, float* dst, const Layout& L, const Mod
 
 template <int TX, int CY>
 int max_clusters() {
-    auto k = k_stream_collide_rows<TX, CY>;
+    auto k = k_stream_collide_rows<TX, CY, kRowMinBlocks * 128 / TX>;
     const size_t smem = FastLayout<TX, CY>::bytes;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     cudaLaunchConfig_t cfg = {};

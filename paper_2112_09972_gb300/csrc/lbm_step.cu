@@ -17,12 +17,13 @@
 // it uses no tensor cores.  Each CTA owns a TX x TY tile of the x-y plane and
 // marches along z.  The force at plane z needs the post-streaming densities
 // of planes z-1, z, z+1 including a one-node halo around the tile; those live
-// in a four-slot ring of density planes in shared memory.  The tile's own
-// populations are pulled once per plane and held in registers across one
-// plane of the march (pulled at z+1, collided one iteration later), so DRAM
-// sees one read and one write of every population; only the halo rows are
-// pulled a second time, from L2, because the neighbouring tiles march the
-// same planes at about the same time.
+// in a four-slot ring of density planes in shared memory.  Each plane is
+// pulled twice: one plane ahead to sum its densities into the ring, and again
+// for the collision.  The second read, and the halo nodes' reads, are served
+// by L1/L2 (the neighbouring tiles march the same planes at about the same
+// time), so DRAM sees about one read and one write of every population while
+// no populations are held on chip across planes, which keeps registers and
+// shared memory low and occupancy high.
 //
 // Sums of populations with opposite velocities are formed as differences of
 // the pair first (c_{2k} = -c_{2k-1}); in fp32 this keeps the cancellation in
@@ -218,7 +219,7 @@ struct Puller {
 };
 
 template <typename S, typename C, bool PER, int MAXT>
-__global__ void __launch_bounds__(MAXT) k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, Layout L,
+__global__ void __launch_bounds__(MAXT, 1) k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, Layout L,
                                                           ModelC<C> m, int TX, int TY, int zchunk, CentreParts cp,
                                                           int* __restrict__ d_err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -259,40 +260,23 @@ __global__ void __launch_bounds__(MAXT) k_stream_collide(const S* __restrict__ s
         R(slot, 1, tx, ty) = rb;
         halo(z, slot);
     };
-    // Pull the tile's populations of plane z (z inside the box) into f and
-    // its densities (tile + halo) into the ring.
-    auto load_plane = [&](int z, int slot, C (&f)[2][19]) {
-        if (active) {
-            P.pull(x, y, z, f);
-            R(slot, 0, tx, ty) = sum19<C>(f[0]);
-            R(slot, 1, tx, ty) = sum19<C>(f[1]);
-        } else {
-            C ra, rb;
-            P.rho_at(x, y, z, m, ra, rb);
-            R(slot, 0, tx, ty) = ra;
-            R(slot, 1, tx, ty) = rb;
-        }
-        halo(z, slot);
-    };
-
     // droplet moments {sum w, sum w x, sum w y, sum w z} of the state written
     // here, w = max(phi, 0); they give the next step's frame origin.  Summed
     // over the thread's z column in the compute type, then reduced in double.
     C cm[4] = {C(0), C(0), C(0), C(0)};
     const C pxc = C(x) - C(0.5) * C(L.Lx - 1), pyc = C(y) - C(0.5) * C(L.Ly - 1);
 
-    C fc[2][19], fn[2][19];
     rho_plane(zc0 - 1, (zc0 - 1) & 3);
-    load_plane(zc0, zc0 & 3, fc);
-    __syncthreads();
+    rho_plane(zc0, zc0 & 3);
 
     for (int z = zc0; z < zc1; ++z) {
-        const int zn = z + 1;
-        if (zn < zc1) load_plane(zn, zn & 3, fn);
-        else rho_plane(zn, zn & 3);
+        rho_plane(z + 1, (z + 1) & 3);
         __syncthreads();
 
         if (active) {
+            // the node's pulled populations again (second read, from L1/L2)
+            C fc[2][19];
+            P.pull(x, y, z, fc);
             const int s0 = (z - 1) & 3, s1 = z & 3, s2 = (z + 1) & 3;
             const C rho[2] = {R(s1, 0, tx, ty), R(s1, 1, tx, ty)};
             // momentum of each component (Eq. 6), opposite pairs first
@@ -353,10 +337,6 @@ __global__ void __launch_bounds__(MAXT) k_stream_collide(const S* __restrict__ s
                 }
             }
         }
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int i = 0; i < 19; ++i) fc[s][i] = fn[s][i];
     }
     double cmd[4] = {(double)cm[0], (double)cm[1], (double)cm[2], (double)cm[3]};
     centre_epilogue(cmd, cp, reinterpret_cast<double*>(smem_raw));
