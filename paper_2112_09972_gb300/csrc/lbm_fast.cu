@@ -48,9 +48,23 @@ struct FastLayout {
 };
 
 // Pulled population (s, i) of the node whose (s=0, i=0) element index is b.
-__device__ __forceinline__ float pulled(const float* __restrict__ src, const Layout& L, long long b, int s, int i) {
-    return __ldg(src + b + (long long)(s * 19 + i) * L.array -
-                 ((long long)cz_(i) * L.plane + (long long)cy_(i) * L.pitch + cx_(i)));
+// The first read of a plane keeps its lines in L2 (evict_last policy) for the
+// second read one plane later, which marks them last-use.
+__device__ __forceinline__ const float* pulled_ptr(const float* src, const Layout& L, long long b, int s, int i) {
+    return src + b + (long long)(s * 19 + i) * L.array -
+           ((long long)cz_(i) * L.plane + (long long)cy_(i) * L.pitch + cx_(i));
+}
+__device__ __forceinline__ float ld_keep(const float* p, unsigned long long pol) {
+    float v;
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float pulled(const float* __restrict__ src, const Layout& L, long long b, int s, int i,
+                                        unsigned long long pol) {
+    return ld_keep(pulled_ptr(src, L, b, s, i), pol);
+}
+__device__ __forceinline__ float pulled_last(const float* __restrict__ src, const Layout& L, long long b, int s, int i) {
+    return __ldlu(pulled_ptr(src, L, b, s, i));
 }
 
 template <int TX, int CY, int MINB>
@@ -92,6 +106,8 @@ __global__ void __launch_bounds__(TX, MINB)
 
     const long long node0 = L.at(0, 0, x, y, 0);      // (s=0, i=0, x, y, z=0)
     const long long hnode0 = L.at(0, 0, hcol, hin ? hy : 0, 0);
+    unsigned long long keep;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
 
     // Post-streaming densities of plane p into ring slot p & 3 (own node and,
     // for threads x < HN, one outer-halo node written into the edge CTA).
@@ -101,12 +117,12 @@ __global__ void __launch_bounds__(TX, MINB)
         float ra = m.rho_b[0], rb = m.rho_b[1];
         if (in) {
             const long long b = node0 + (long long)p * L.plane;
-            ra = pulled(src, L, b, 0, 0);
-            rb = pulled(src, L, b, 1, 0);
+            ra = pulled(src, L, b, 0, 0, keep);
+            rb = pulled(src, L, b, 1, 0, keep);
 #pragma unroll
             for (int i = 1; i < 19; i += 2) {
-                ra += pulled(src, L, b, 0, i) + pulled(src, L, b, 0, i + 1);
-                rb += pulled(src, L, b, 1, i) + pulled(src, L, b, 1, i + 1);
+                ra += pulled(src, L, b, 0, i, keep) + pulled(src, L, b, 0, i + 1, keep);
+                rb += pulled(src, L, b, 1, i, keep) + pulled(src, L, b, 1, i + 1, keep);
             }
         }
         ring[((slot * 2 + 0) * 3 + 1) * RW + x + 1] = ra;
@@ -115,12 +131,12 @@ __global__ void __launch_bounds__(TX, MINB)
             float ha = m.rho_b[0], hb = m.rho_b[1];
             if (in && hin) {
                 const long long b = hnode0 + (long long)p * L.plane;
-                ha = pulled(src, L, b, 0, 0);
-                hb = pulled(src, L, b, 1, 0);
+                ha = pulled(src, L, b, 0, 0, keep);
+                hb = pulled(src, L, b, 1, 0, keep);
 #pragma unroll
                 for (int i = 1; i < 19; i += 2) {
-                    ha += pulled(src, L, b, 0, i) + pulled(src, L, b, 0, i + 1);
-                    hb += pulled(src, L, b, 1, i) + pulled(src, L, b, 1, i + 1);
+                    ha += pulled(src, L, b, 0, i, keep) + pulled(src, L, b, 0, i + 1, keep);
+                    hb += pulled(src, L, b, 1, i, keep) + pulled(src, L, b, 1, i + 1, keep);
                 }
             }
             hring[(slot * 2 + 0) * 3 * RW] = ha;
@@ -135,7 +151,16 @@ __global__ void __launch_bounds__(TX, MINB)
     densities(zc0);
     for (int z = zc0; z < zc1; ++z) {
         densities(z + 1);
-        cluster.sync();
+        // publish the densities (release), read this node's populations for
+        // the collision while the other CTAs catch up, then acquire theirs
+        asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+        const long long bz = node0 + (long long)z * L.plane;
+        float f[2][19];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 19; ++i) f[s][i] = pulled_last(src, L, bz, s, i);
+        asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 
         const int s0 = (z - 1) & 3, s1 = z & 3, s2 = (z + 1) & 3;
         // neighbour density of component s at offset (dx, dy, dz)
@@ -144,13 +169,6 @@ __global__ void __launch_bounds__(TX, MINB)
             const int o = (slot * 2 + s) * 3 * RW + dx;
             return dy == 0 ? row0[o] : (dy > 0 ? rowA[o] : rowB[o]);
         };
-        // the node's pulled populations again (second read, from L1/L2)
-        const long long bz = node0 + (long long)z * L.plane;
-        float f[2][19];
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int i = 0; i < 19; ++i) f[s][i] = pulled(src, L, bz, s, i);
         const float rho[2] = {row0[(s1 * 2 + 0) * 3 * RW], row0[(s1 * 2 + 1) * 3 * RW]};
         // momentum (Eq. 6), opposite pairs differenced first
         float j[2][3];
@@ -203,7 +221,7 @@ __global__ void __launch_bounds__(TX, MINB)
             const float r = rho[s];
             {
                 const float g = r * wgt<float>(0) * (1.f - u2x);
-                dst[b + (long long)(s * 19) * L.array] = f[s][0] - (f[s][0] - g) * it;
+                __stcs(dst + b + (long long)(s * 19) * L.array, f[s][0] - (f[s][0] - g) * it);
             }
 #pragma unroll
             for (int i = 1; i < 19; i += 2) {
@@ -212,8 +230,8 @@ __global__ void __launch_bounds__(TX, MINB)
                 const float even = rw * (1.f + 4.5f * cu * cu - u2x);
                 const float odd = rw * (3.f * cu);
                 const float fa = f[s][i], fb = f[s][i + 1];
-                dst[b + (long long)(s * 19 + i) * L.array] = fa - (fa - (even + odd)) * it;
-                dst[b + (long long)(s * 19 + i + 1) * L.array] = fb - (fb - (even - odd)) * it;
+                __stcs(dst + b + (long long)(s * 19 + i) * L.array, fa - (fa - (even + odd)) * it);
+                __stcs(dst + b + (long long)(s * 19 + i + 1) * L.array, fb - (fb - (even - odd)) * it);
             }
         }
     }

@@ -60,10 +60,11 @@ __global__ void k_init(S* __restrict__ f, Layout L, double R, double xi, double 
 }
 
 // ----------------------------------------------------------------------------
-// Ghost nodes.  The shell is enumerated face by face without overlap:
+// Ghost nodes.  The shell is covered face by face without overlap:
 // x = -1 and x = Lx over y, z in [-1, L]; y = -1 and y = Ly over x in [0, Lx),
 // z in [-1, Lz]; z = -1 and z = Lz over x in [0, Lx), y in [0, Ly).  A ghost
 // population i is written only if it streams into the box (y + c_i inside).
+// Corner nodes stream into no fluid node and write nothing.
 template <typename S, typename C>
 __global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, Model m, Grad A, CentreParts cp,
                                                int* __restrict__ d_err) {
@@ -74,31 +75,22 @@ __global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, Mode
         yc = (C)cp.sum[5];
         zc = (C)cp.sum[6];
     }
-    const long long nX = (long long)(L.Ly + 2) * (L.Lz + 2);
-    const long long nY = (long long)L.Lx * (L.Lz + 2);
-    const long long nZ = (long long)L.Lx * L.Ly;
-    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // grid: x = fast face coordinate (32-wide blocks), y = slow face
+    // coordinate, z = face (0/1: x = -1 / Lx over y, z in [-1, L]; 2/3: y = -1 / Ly
+    // over x in [0, Lx), z in [-1, Lz]; 4/5: z = -1 / Lz over x, y inside)
+    const int face = blockIdx.z;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y * blockDim.y + threadIdx.y;
     int x, y, z;
-    if (g < 2 * nX) {
-        const int side = (int)(g / nX);
-        const long long r = g - side * nX;
-        x = side ? L.Lx : -1;
-        y = (int)(r % (L.Ly + 2)) - 1;
-        z = (int)(r / (L.Ly + 2)) - 1;
-    } else if ((g -= 2 * nX) < 2 * nY) {
-        const int side = (int)(g / nY);
-        const long long r = g - side * nY;
-        y = side ? L.Ly : -1;
-        x = (int)(r % L.Lx);
-        z = (int)(r / L.Lx) - 1;
-    } else if ((g -= 2 * nY) < 2 * nZ) {
-        const int side = (int)(g / nZ);
-        const long long r = g - side * nZ;
-        z = side ? L.Lz : -1;
-        x = (int)(r % L.Lx);
-        y = (int)(r / L.Lx);
+    if (face < 2) {
+        if (a >= L.Ly + 2 || b >= L.Lz + 2) return;
+        x = face ? L.Lx : -1; y = a - 1; z = b - 1;
+    } else if (face < 4) {
+        if (a >= L.Lx || b >= L.Lz + 2) return;
+        y = face == 3 ? L.Ly : -1; x = a; z = b - 1;
     } else {
-        return;
+        if (a >= L.Lx || b >= L.Ly) return;
+        z = face == 5 ? L.Lz : -1; x = a; y = b;
     }
     // position relative to the frame origin, then the flow and Eq. 8 in the
     // compute type of the populations (fp64 arithmetic is slow on this part)
@@ -474,11 +466,12 @@ cudaError_t launch_init(int prec, void* f, const Layout& L, double R, double xi,
 
 cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Grad A, CentreParts cp, int* d_err,
                          cudaStream_t s) {
-    const long long n = 2LL * (L.Ly + 2) * (L.Lz + 2) + 2LL * L.Lx * (L.Lz + 2) + 2LL * L.Lx * L.Ly;
-    const int T = 256;
-    const unsigned blocks = (unsigned)((n + T - 1) / T);
-    if (prec == 0) k_ghost<double, double><<<blocks, T, 0, s>>>((double*)f, L, m, A, cp, d_err);
-    else k_ghost<float, float><<<blocks, T, 0, s>>>((float*)f, L, m, A, cp, d_err);
+    const int fast = (L.Lx > L.Ly + 2 ? L.Lx : L.Ly + 2);
+    const int slow = (L.Lz + 2 > L.Ly ? L.Lz + 2 : L.Ly);
+    const dim3 block(32, 8, 1);
+    const dim3 grid((fast + 31) / 32, (slow + 7) / 8, 6);
+    if (prec == 0) k_ghost<double, double><<<grid, block, 0, s>>>((double*)f, L, m, A, cp, d_err);
+    else k_ghost<float, float><<<grid, block, 0, s>>>((float*)f, L, m, A, cp, d_err);
     return cudaGetLastError();
 }
 
