@@ -204,6 +204,33 @@ int lbm_profile_read(lbm_ctx* ctx, int kernel, double* total_ms, int64_t* launch
  * per CTA, CTAs. */
 int lbm_launch_shape(lbm_ctx* ctx, int32_t* tile_y, int32_t* z_chunk, int32_t* ctas);
 
+/*
+ * Allocation-free droplet moments (an addition of this library; the paper has
+ * no counterpart).  For callers that cannot allocate device memory when they
+ * need the droplet's shape: code recording into a CUDA graph (no cudaMalloc
+ * inside a capture), loops that must not touch the allocator, hosts with a
+ * fixed memory budget.  Computes the same result as lbm_moments and
+ * lbm_deformation from populations the caller already holds on the device:
+ *   f          device pointer to float64 (precision LBM_FP64) or float32
+ *              (LBM_FP32) populations in the dense layout of
+ *              lbm_get_populations: [2][19][box[2]][box[1]][box[0]];
+ *   box        box extents (x, y, z), each >= 1, at most 2^31/38 nodes in all
+ *              (larger boxes return LBM_EINVAL);
+ *   out        device pointer to 26 doubles receiving, in order, the ten
+ *              moments of lbm_moments, D, the axes (as in lbm_deformation,
+ *              axes[3*a + k]), the three eigenvalues and the centre of mass;
+ *   cuda_stream the stream to run on (NULL: the legacy default stream).
+ * Asynchronous; no device or host memory is allocated and no synchronising
+ * call is made.  Scratch lives in one fixed 80 KB device array of the library
+ * (1024 blocks x 10 doubles), held by every GPU that loads the library until
+ * the process exits.  Its device address is looked up on the first call on
+ * each device (with that device current): make that first call before any
+ * stream capture starts.  All calls share the array, so calls whose kernels
+ * may run concurrently on the GPU (unordered streams) race and give wrong
+ * results; calls ordered on one stream are safe.
+ */
+int lbm_moments_static(const void* f, int32_t precision, const int32_t box[3], double* out, void* cuda_stream);
+
 /* Free the context and its device memory (NULL is allowed). */
 void lbm_destroy(lbm_ctx* ctx);
 

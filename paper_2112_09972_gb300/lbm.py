@@ -28,7 +28,7 @@ ABI_FUNCTIONS = [
     "lbm_opts_default", "lbm_create", "lbm_set_gradient", "lbm_set_gradient_table", "lbm_step", "lbm_sync",
     "lbm_deformation", "lbm_moments", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
     "lbm_checksums", "lbm_get_step", "lbm_save", "lbm_load", "lbm_profile_enable", "lbm_profile_read",
-    "lbm_launch_shape", "lbm_destroy", "lbm_strerror",
+    "lbm_launch_shape", "lbm_destroy", "lbm_strerror", "lbm_moments_static",
 ]
 
 
@@ -91,6 +91,7 @@ def load_library(path=LIB_PATH):
         "lbm_launch_shape": (ctypes.c_int, [vp, _I32P, _I32P, _I32P]),
         "lbm_destroy": (None, [vp]),
         "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "lbm_moments_static": (ctypes.c_int, [vp, ctypes.c_int32, _I32P, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -125,6 +126,21 @@ def current_torch_stream():
     if not torch.cuda.is_available():
         return None
     return torch.cuda.current_stream().cuda_stream
+
+
+def lbm_moments_static(f_dev_ptr, precision, box, out_dev_ptr, stream=None):
+    """Allocation-free droplet moments of device-resident populations.
+
+    For callers that cannot allocate device memory at that point (e.g. while a
+    stream is being captured into a CUDA graph).  ``f_dev_ptr`` and
+    ``out_dev_ptr`` are device addresses (ints) of the dense population array
+    and of 26 doubles; ``precision`` is "fp64" or "fp32".  See ``lbm.h``.
+    """
+    lib = load_library()
+    b = (ctypes.c_int32 * 3)(*[int(v) for v in box])
+    _check(lib.lbm_moments_static(ctypes.c_void_p(int(f_dev_ptr)), PRECISIONS[precision], b,
+                                  ctypes.c_void_p(int(out_dev_ptr)), None if stream is None else ctypes.c_void_p(stream)),
+           "lbm_moments_static")
 
 
 class DropletLBM:
