@@ -219,10 +219,10 @@ __global__ void __launch_bounds__(TX, MINB)
             const float u2x = 1.5f * (ux * ux + uy * uy + uz * uz);
             const float it = m.inv_tau[s];
             const float r = rho[s];
-            {
-                const float g = r * wgt<float>(0) * (1.f - u2x);
-                __stcs(dst + b + (long long)(s * 19) * L.array, f[s][0] - (f[s][0] - g) * it);
-            }
+            // moving populations; the rest population then closes the mass
+            // balance exactly (sum of outputs = rho), which keeps fp32
+            // rounding from drifting the interface
+            float others = 0.f;
 #pragma unroll
             for (int i = 1; i < 19; i += 2) {
                 const float cu = (float)cx_(i) * ux + (float)cy_(i) * uy + (float)cz_(i) * uz;
@@ -230,9 +230,13 @@ __global__ void __launch_bounds__(TX, MINB)
                 const float even = rw * (1.f + 4.5f * cu * cu - u2x);
                 const float odd = rw * (3.f * cu);
                 const float fa = f[s][i], fb = f[s][i + 1];
-                __stcs(dst + b + (long long)(s * 19 + i) * L.array, fa - (fa - (even + odd)) * it);
-                __stcs(dst + b + (long long)(s * 19 + i + 1) * L.array, fb - (fb - (even - odd)) * it);
+                const float oa = fa - (fa - (even + odd)) * it;
+                const float ob = fb - (fb - (even - odd)) * it;
+                __stcs(dst + b + (long long)(s * 19 + i) * L.array, oa);
+                __stcs(dst + b + (long long)(s * 19 + i + 1) * L.array, ob);
+                others += oa + ob;
             }
+            __stcs(dst + b + (long long)(s * 19) * L.array, r - others);
         }
     }
     // neighbours may still read this CTA's ring for their last plane

@@ -321,12 +321,19 @@ __global__ void __launch_bounds__(MAXT, 1) k_stream_collide(const S* __restrict_
                 const C uy = up[1] + sh * acc[1 - s][1];
                 const C uz = up[2] + sh * acc[1 - s][2];
                 const C u2x = C(1.5) * (ux * ux + uy * uy + uz * uz);
+                // moving populations; the rest population then closes the
+                // mass balance exactly (sum of outputs = rho), which keeps
+                // fp32 rounding from drifting the interface
+                C others = C(0);
 #pragma unroll
-                for (int i = 0; i < 19; ++i) {
+                for (int i = 1; i < 19; ++i) {
                     const C f = fc[s][i];
                     const C g = feq<C>(i, rho[s], ux, uy, uz, u2x);
-                    dst[base + (long long)(s * 19 + i) * L.array] = (S)(f - (f - g) * m.inv_tau[s]);
+                    const S o = (S)(f - (f - g) * m.inv_tau[s]);
+                    dst[base + (long long)(s * 19 + i) * L.array] = o;
+                    others += (C)o;
                 }
+                dst[base + (long long)(s * 19) * L.array] = (S)(rho[s] - others);
             }
         }
     }
