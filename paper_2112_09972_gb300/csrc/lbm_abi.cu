@@ -33,7 +33,7 @@ struct lbm_ctx {
     int cur;                // buffer holding the current post-collision populations
     bool initialised;       // populations hold a state (lazy init on first use)
     int64_t step;           // steps taken; step n uses A(t_n = n)
-    int* d_err;             // latched device error bits: 1 non-finite, 2 Mach
+    int* d_err;             // latched device error bits: 1 non-finite, 2 Mach, 4 wait timeout
     int* h_err;             // pinned mirror
     int latched;            // latched status returned by later calls
     // gradient knots (host); A(t_n) is evaluated here and passed by value
@@ -110,7 +110,8 @@ int check_latched(lbm_ctx* c) {
     // A Mach violation at the boundary is the usual cause of a later
     // non-finite density, so it is reported first.
     int bits = *c->h_err;
-    if (bits & 2) c->latched = LBM_EMACH;
+    if (bits & 4) c->latched = LBM_ETIMEOUT;
+    else if (bits & 2) c->latched = LBM_EMACH;
     else if (bits & 1) c->latched = LBM_ENONFINITE;
     return c->latched;
 }

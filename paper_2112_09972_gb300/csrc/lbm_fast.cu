@@ -11,15 +11,16 @@
 //     values are read again for the collision (that second read is served by
 //     L1/L2).  Holding no populations on chip keeps each CTA at a few KB of
 //     shared memory and few registers, so many CTAs per SM hide the latency;
-//   * the force (Eq. 7) reads the 18 neighbour densities: those of its own
-//     row from its own ring, those of rows y -/+ 1 from the rings of the
-//     neighbouring CTAs of the cluster through distributed shared memory.
-//     Only the two rows just outside the cluster are pulled a second time
-//     (ratio 2/CY); that work is split evenly over the CTAs of the cluster,
-//     which write the densities into the edge CTAs' rings remotely.
-// One cluster barrier per plane publishes the densities.  DRAM therefore sees
-// one read and one write of every population; L2 serves the second read and
-// the (2/CY) outer-halo reads.
+//   * each CTA pushes its row of densities into the rings of the CTAs that
+//     own rows y -/+ 1 with st.async, which counts the bytes on the
+//     receiving CTA's mbarrier for that plane; the force (Eq. 7) then reads
+//     all 18 neighbour densities from local shared memory after a bounded
+//     mbarrier wait.  Only the two rows just outside the cluster are pulled
+//     a second time (ratio 2/CY); that work is split evenly over the CTAs of
+//     the cluster, which push those densities into the edge CTAs' rings.
+// There is no cluster-wide barrier and no memory fence per plane: a CTA waits
+// only for the two rows it reads.  DRAM sees about one read and one write of
+// every population; L2 serves the second read and the outer-halo reads.
 //
 // Sums over opposite velocity pairs are differenced first (c_{2k} = -c_{2k-1}),
 // and the equilibria of a pair share their even part.
@@ -39,12 +40,54 @@ struct FastModel {
     float inv_tau[2], tau[2], G, rho_b[2];
 };
 
+// Shared-memory, cluster-address and mbarrier helpers (inline PTX).
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned cluster_addr(unsigned local, unsigned rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_init(unsigned mbar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned mbar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned mbar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+// Store two floats into (possibly another CTA's) shared memory and count
+// 8 bytes on that CTA's mbarrier when they land.
+__device__ __forceinline__ void st_async_f2(unsigned raddr, float a, float b, unsigned rmbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+                 "f"(a), "f"(b), "r"(rmbar)
+                 : "memory");
+}
+
+// Upper bound on mbarrier polls before a wait gives up (the kernel then sets
+// error bit 4, reported as LBM_ETIMEOUT, and carries on without blocking).
+constexpr unsigned kWaitPolls = 1u << 20;
+
 template <int TX, int CY>
 struct FastLayout {
-    static constexpr int RW = TX + 2;              // ring row width (x halo columns -1, TX)
-    static constexpr int HN = 2 * TX / CY;         // outer-halo nodes pulled per CTA
-    static constexpr int RING = 4 * 2 * 3 * RW;    // [slot][component][row -1..1][col]
-    static constexpr size_t bytes = sizeof(float) * RING;
+    static constexpr int RW = TX + 2;            // ring row width (x halo columns -1, TX)
+    static constexpr int HN = 2 * TX / CY;       // outer-halo nodes pulled per CTA
+    // Density ring slots.  Plane p lives in slot p mod S.  The rows beyond
+    // the cluster are written by every CTA of the cluster, and a CTA can run
+    // at most CY - 1 planes ahead of the edge CTA it writes to, so S = CY + 2
+    // slots keep a slot's next plane from landing before its last reader.
+    static constexpr int S = CY + 2;
+    static constexpr int RING = S * 3 * RW * 2;  // [slot][row -1..1][col][component]
+    static constexpr unsigned TX_BYTES = 2u * TX * 2u * 4u;  // rows -1 and +1, both components
+    static constexpr size_t bytes = sizeof(float) * RING + sizeof(unsigned long long) * S;
 };
 
 // Pulled population (s, i) of the node whose (s=0, i=0) element index is b.
@@ -72,8 +115,9 @@ __global__ void __launch_bounds__(TX, MINB)
     k_stream_collide_rows(const float* __restrict__ src, float* __restrict__ dst, Layout L, FastModel m, int zchunk,
                           CentreParts cp, int* __restrict__ d_err) {
     using FL = FastLayout<TX, CY>;
-    constexpr int RW = FL::RW, HN = FL::HN;
-    extern __shared__ __align__(16) float ring[];  // [4][2][3][RW]
+    constexpr int RW = FL::RW, HN = FL::HN, S = FL::S;
+    extern __shared__ __align__(16) float ring[];  // [S][3][RW][2], then S mbarriers
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(ring + FL::RING);
     __shared__ double red[4 * ((TX + 31) / 32)];
 
     cg::cluster_group cluster = cg::this_cluster();
@@ -92,27 +136,41 @@ __global__ void __launch_bounds__(TX, MINB)
     const int hcol = rank * (HN / 2) + (x % (HN / 2));
     const int hy = hside ? Y0 + CY : Y0 - 1;
     const bool hin = hy >= 0 && hy < L.Ly;
-    float* hring = cluster.map_shared_rank(ring, hside ? CY - 1 : 0) + (hside ? 2 : 0) * RW + hcol + 1;
 
-    // Density rows the force reads: own row, and rows y -/+ 1 from the
-    // neighbouring CTAs (or from this CTA's outer-halo rows at the cluster edge).
-    const float* row0 = ring + 1 * RW + 1 + x;
-    const float* rowB = (rank > 0 ? cluster.map_shared_rank(ring, rank - 1) + 1 * RW : ring) + 1 + x;
-    const float* rowA = (rank < CY - 1 ? cluster.map_shared_rank(ring, rank + 1) + 1 * RW : ring + 2 * RW) + 1 + x;
+    // ring index of (slot, row in -1..1, col in -1..TX), component 0
+    auto ridx = [&](int slot, int row, int col) { return ((slot * 3 + row + 1) * RW + col + 1) * 2; };
+    const unsigned ring_s = smem_u32(ring);
+    const unsigned mbar_s = smem_u32(mbar);
+    // Where this CTA's own row goes in the neighbours' rings, and where its
+    // outer-halo node goes in the edge CTA's ring (cluster addresses).
+    const unsigned below_ring = rank > 0 ? cluster_addr(ring_s, rank - 1) : 0u;  // their row +1
+    const unsigned below_mbar = rank > 0 ? cluster_addr(mbar_s, rank - 1) : 0u;
+    const unsigned above_ring = rank < CY - 1 ? cluster_addr(ring_s, rank + 1) : 0u;  // their row -1
+    const unsigned above_mbar = rank < CY - 1 ? cluster_addr(mbar_s, rank + 1) : 0u;
+    const unsigned halo_ring = cluster_addr(ring_s, hside ? CY - 1 : 0);
+    const unsigned halo_mbar = cluster_addr(mbar_s, hside ? CY - 1 : 0);
 
-    // ring[slot][s][row][col] is at ((slot * 2 + s) * 3 + row + 1) * RW + col + 1
-    for (int e = x; e < FL::RING; e += TX) ring[e] = m.rho_b[(e / (3 * RW)) & 1];
-    cluster.sync();  // prefill before any remote halo write
+    // ghost density in every slot (x halo columns keep it for good), barriers
+    for (int e = x; e < FL::RING; e += TX) ring[e] = m.rho_b[e & 1];
+    if (x == 0) {
+        for (int k = 0; k < S; ++k) mbar_init(mbar_s + 8u * k, 1u);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cluster.sync();  // barriers initialised before any remote store arrives
 
     const long long node0 = L.at(0, 0, x, y, 0);      // (s=0, i=0, x, y, z=0)
     const long long hnode0 = L.at(0, 0, hcol, hin ? hy : 0, 0);
     unsigned long long keep;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
 
-    // Post-streaming densities of plane p into ring slot p & 3 (own node and,
-    // for threads x < HN, one outer-halo node written into the edge CTA).
+    auto slot_of = [&](int p) { return (p - (zc0 - 1)) % S; };
+
+    // Post-streaming densities of plane p: the own node into row 0 of this
+    // CTA's ring and into the neighbours' rows -1 / +1; the outer-halo node
+    // (threads x < HN) into the edge CTA's row -1 / +1.  Ghost densities
+    // outside the box.  Every CTA then expects TX_BYTES on its slot barrier.
     auto densities = [&](int p) {
-        const int slot = p & 3;
+        const int slot = slot_of(p);
         const bool in = p >= 0 && p < L.Lz;
         float ra = m.rho_b[0], rb = m.rho_b[1];
         if (in) {
@@ -125,8 +183,10 @@ __global__ void __launch_bounds__(TX, MINB)
                 rb += pulled(src, L, b, 1, i, keep) + pulled(src, L, b, 1, i + 1, keep);
             }
         }
-        ring[((slot * 2 + 0) * 3 + 1) * RW + x + 1] = ra;
-        ring[((slot * 2 + 1) * 3 + 1) * RW + x + 1] = rb;
+        *reinterpret_cast<float2*>(ring + ridx(slot, 0, x)) = make_float2(ra, rb);
+        const unsigned mb = 8u * slot;
+        if (rank > 0) st_async_f2(below_ring + 4u * ridx(slot, 1, x), ra, rb, below_mbar + mb);
+        if (rank < CY - 1) st_async_f2(above_ring + 4u * ridx(slot, -1, x), ra, rb, above_mbar + mb);
         if (hthr) {
             float ha = m.rho_b[0], hb = m.rho_b[1];
             if (in && hin) {
@@ -139,9 +199,23 @@ __global__ void __launch_bounds__(TX, MINB)
                     hb += pulled(src, L, b, 1, i, keep) + pulled(src, L, b, 1, i + 1, keep);
                 }
             }
-            hring[(slot * 2 + 0) * 3 * RW] = ha;
-            hring[(slot * 2 + 1) * 3 * RW] = hb;
+            st_async_f2(halo_ring + 4u * ridx(slot, hside ? 1 : -1, hcol), ha, hb, halo_mbar + mb);
         }
+        if (x == 0) mbar_expect_tx(mbar_s + mb, FL::TX_BYTES);
+    };
+    // Wait (bounded) until the neighbour rows of plane p have landed.
+    unsigned phase = 0u;  // bit k: parity of slot k's next phase
+    auto wait_rows = [&](int p) {
+        const int slot = slot_of(p);
+        const unsigned par = (phase >> slot) & 1u;
+        unsigned polls = 0;
+        while (!mbar_try_wait(mbar_s + 8u * slot, par)) {
+            if (++polls == kWaitPolls) {
+                atomicOr(d_err, 4);
+                break;
+            }
+        }
+        phase ^= 1u << slot;
     };
 
     float cm[4] = {0.f, 0.f, 0.f, 0.f};
@@ -149,27 +223,28 @@ __global__ void __launch_bounds__(TX, MINB)
 
     densities(zc0 - 1);
     densities(zc0);
+    wait_rows(zc0 - 1);
+    wait_rows(zc0);
     for (int z = zc0; z < zc1; ++z) {
         densities(z + 1);
-        // publish the densities (release), read this node's populations for
-        // the collision while the other CTAs catch up, then acquire theirs
-        asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+        // this node's populations for the collision, read while the
+        // neighbour rows of plane z + 1 are in flight
         const long long bz = node0 + (long long)z * L.plane;
         float f[2][19];
 #pragma unroll
         for (int s = 0; s < 2; ++s)
 #pragma unroll
             for (int i = 0; i < 19; ++i) f[s][i] = pulled_last(src, L, bz, s, i);
-        asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+        __syncthreads();  // own row of plane z + 1 complete
+        wait_rows(z + 1);
 
-        const int s0 = (z - 1) & 3, s1 = z & 3, s2 = (z + 1) & 3;
+        const int s0 = slot_of(z - 1), s1 = slot_of(z), s2 = slot_of(z + 1);
         // neighbour density of component s at offset (dx, dy, dz)
         auto nb = [&](int s, int dx, int dy, int dz) -> float {
             const int slot = dz == 0 ? s1 : (dz > 0 ? s2 : s0);
-            const int o = (slot * 2 + s) * 3 * RW + dx;
-            return dy == 0 ? row0[o] : (dy > 0 ? rowA[o] : rowB[o]);
+            return ring[ridx(slot, dy, x + dx) + s];
         };
-        const float rho[2] = {row0[(s1 * 2 + 0) * 3 * RW], row0[(s1 * 2 + 1) * 3 * RW]};
+        const float rho[2] = {ring[ridx(s1, 0, x)], ring[ridx(s1, 0, x) + 1]};
         // momentum (Eq. 6), opposite pairs differenced first
         float j[2][3];
 #pragma unroll
@@ -238,8 +313,11 @@ __global__ void __launch_bounds__(TX, MINB)
             }
             __stcs(dst + b + (long long)(s * 19) * L.array, r - others);
         }
+        // Before a later plane reuses this plane's own-row slot, all threads
+        // must be done reading it: the __syncthreads of the next iterations
+        // (S > 3 planes apart) order that.
     }
-    // neighbours may still read this CTA's ring for their last plane
+    // no CTA leaves while another may still address its shared memory
     cluster.sync();
 
     // centre-of-mass partials of the written state (fixed-order reduction)
