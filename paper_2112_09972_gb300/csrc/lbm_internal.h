@@ -9,25 +9,28 @@
 
 namespace lbmgb {
 
-// Padded structure-of-arrays population layout in device memory.
+// Padded, plane-major structure-of-arrays population layout in device memory.
 //
-//   element (s, i, z, y, x) at  ((s*19 + i) * nz + (z + 1)) * ny + (y + 1)) * pitch + x0 + x
+//   element (s, i, z, y, x) at  (z + 1) * plane + (s*19 + i) * array + (y + 1) * pitch + x0 + x
 //
-// for fluid nodes x in [0, Lx), y in [0, Ly), z in [0, Lz).  One ghost layer
-// surrounds the box: x = -1 .. Lx, y = -1 .. Ly, z = -1 .. Lz all have
-// storage.  x0 puts the first fluid node of every row on a 32-byte boundary,
-// and pitch (a multiple of 32 bytes) keeps every row, plane and population
-// array on that boundary.
+// for fluid nodes x in [0, Lx), y in [0, Ly), z in [0, Lz), with
+// array = ny * pitch (one population's x-y plane) and plane = 38 * array.
+// All 38 populations of one z plane are contiguous, so a CTA marching along
+// z touches a few memory pages at a time rather than 38 arrays far apart.
+// One ghost layer surrounds the box: x = -1 .. Lx, y = -1 .. Ly, z = -1 .. Lz
+// all have storage.  x0 puts the first fluid node of every row on a 32-byte
+// boundary, and pitch (a multiple of 32 bytes) keeps every row on that
+// boundary.
 struct Layout {
     int Lx, Ly, Lz;
     int x0;           // elements before x = 0 in a row
     int pitch;        // elements per row
     int ny, nz;       // Ly + 2, Lz + 2
-    long long plane;  // ny * pitch
-    long long array;  // nz * plane: elements of one population array
-    long long total;  // 38 * array
+    long long plane;  // elements per z plane (all 38 populations)
+    long long array;  // elements of one population's x-y plane
+    long long total;  // nz * plane
     __host__ __device__ long long at(int s, int i, int x, int y, int z) const {
-        return ((long long)(s * 19 + i) * nz + (z + 1)) * plane + (long long)(y + 1) * pitch + x0 + x;
+        return (long long)(z + 1) * plane + (long long)(s * 19 + i) * array + (long long)(y + 1) * pitch + x0 + x;
     }
 };
 

@@ -408,9 +408,9 @@ Layout make_layout(int Lx, int Ly, int Lz, int elem_bytes) {
     L.pitch = ((L.x0 + Lx + 1 + align - 1) / align) * align;
     L.ny = Ly + 2;
     L.nz = Lz + 2;
-    L.plane = (long long)L.ny * L.pitch;
-    L.array = (long long)L.nz * L.plane;
-    L.total = 38LL * L.array;
+    L.array = (long long)L.ny * L.pitch;
+    L.plane = 38LL * L.array;
+    L.total = (long long)L.nz * L.plane;
     return L;
 }
 
@@ -418,10 +418,15 @@ Shape choose_shape(const Layout& L, int elem_bytes, int periodic, int ty_req, in
     Shape sh;
     sh.rows = 0;
     if (ty_req <= 0 && rows_kernel_applies(L, elem_bytes == 4 ? 1 : 0, periodic)) {
-        // one CTA per row, as many z chunks as fill the resident CTA slots once
+        // one CTA per row
         const int resident = rows_kernel_resident_ctas(L);
         if (resident > 0) {
-            int chunks = zchunk_req > 0 ? (L.Lz + zchunk_req - 1) / zchunk_req : resident / L.Ly;
+            // as many z chunks as fill the resident CTA slots once, but at
+            // least ~32 planes per chunk: each chunk re-reads two planes
+            int chunks = resident / L.Ly;
+            const int by_depth = (L.Lz + 31) / 32;
+            if (chunks > by_depth) chunks = by_depth;
+            if (zchunk_req > 0) chunks = (L.Lz + zchunk_req - 1) / zchunk_req;
             if (chunks < 1) chunks = 1;
             if (chunks > L.Lz) chunks = L.Lz;
             sh.rows = 1;
