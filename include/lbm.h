@@ -231,6 +231,66 @@ int lbm_launch_shape(lbm_ctx* ctx, int32_t* tile_y, int32_t* z_chunk, int32_t* c
  */
 int lbm_moments_static(const void* f, int32_t precision, const int32_t box[3], double* out, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched ensemble: many independent droplet boxes (for deformation
+ * statistics over many tracer trajectories, Sec. 6), each a full copy of the
+ * single-box method above with its own size, radius and per-step gradient
+ * history, advanced together: one ghost launch and one persistent
+ * stream-collide launch per step, replayed from a captured CUDA graph.  fp32
+ * populations, ghost boundary, the frame of opts->frame.
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch; /* opaque */
+
+/*
+ * Create an ensemble of nbox boxes: boxes[3k .. 3k+2] = (Lx, Ly, Lz) of box k
+ * (each 4 .. 1024), R[k] its droplet radius (2 R <= min extent - 2).
+ * visc, G as for lbm_create.  opts must ask for LBM_FP32 and the ghost
+ * boundary and must give rho_lo > 0 (the ghost density of the droplet
+ * component); rho_hi <= 0 means 1.  opts->z_chunk (0: 16) sets the initial
+ * z planes per work item.  Each box starts, on first use, at the equilibrium
+ * tanh droplet in the flow of its gradient at step 0.
+ */
+int lbm_batch_create(lbm_batch** out, int32_t nbox, const int32_t* boxes, const double* R, const double visc[2],
+                     double G, const lbm_opts* opts);
+
+/*
+ * Per-step gradients of every box: A[(t * nbox + k) * 9 .. + 8] drives box k at
+ * step t, t = 0 .. nsteps-1 (row-major, traceless, see lbm_set_gradient);
+ * steps beyond the table use its last row.  Stored on the device in float32.
+ */
+int lbm_batch_set_gradients(lbm_batch* batch, int64_t nsteps, const double* A);
+
+/* Advance every box n steps (asynchronous; pairs of steps replay a CUDA graph). */
+int lbm_batch_step(lbm_batch* batch, int64_t n);
+
+/* Wait for the ensemble's stream and report any latched device error. */
+int lbm_batch_sync(lbm_batch* batch);
+
+/*
+ * D of every box (as lbm_deformation): D[k]; axes[9k ..] and centre[3k ..]
+ * may be NULL.  Synchronises.
+ */
+int lbm_batch_deformation(lbm_batch* batch, double* D, double* axes, double* centre);
+
+/* Populations of one box to / from the host (float64, lbm_get_populations layout). */
+int lbm_batch_get_populations(lbm_batch* batch, int32_t box, double* f);
+int lbm_batch_set_populations(lbm_batch* batch, int32_t box, const double* f);
+
+/*
+ * Time trial_steps steps for each candidate work-list shape (z planes per
+ * item in {8, 16, 32, 64}, CTAs per SM in {all that fit, 2, 4}) and keep the
+ * fastest.  Only before the first step: the trials run from the initial
+ * state, which is restored afterwards (LBM_EINVAL once stepping started).
+ * The chosen values are returned in *zchunk and *ctas_per_sm (0 = all that fit).
+ */
+int lbm_batch_autotune(lbm_batch* batch, int32_t trial_steps, int32_t* zchunk, int32_t* ctas_per_sm);
+
+/* Work-list shape in use: z planes per item, persistent CTAs, work items. */
+int lbm_batch_shape(lbm_batch* batch, int32_t* zchunk, int32_t* ctas, int32_t* items);
+
+/* Free the ensemble (NULL is allowed). */
+void lbm_batch_destroy(lbm_batch* batch);
+
 /* Free the context and its device memory (NULL is allowed). */
 void lbm_destroy(lbm_ctx* ctx);
 

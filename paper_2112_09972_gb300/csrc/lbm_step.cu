@@ -33,6 +33,7 @@
 
 #include "lbm_internal.h"
 #include "lbm_lattice.cuh"
+#include "lbm_tile.cuh"
 
 namespace lbmgb {
 namespace {
@@ -60,13 +61,10 @@ __global__ void k_init(S* __restrict__ f, Layout L, double R, double xi, double 
 }
 
 // ----------------------------------------------------------------------------
-// Ghost nodes.  The shell is covered face by face without overlap:
-// x = -1 and x = Lx over y, z in [-1, L]; y = -1 and y = Ly over x in [0, Lx),
-// z in [-1, Lz]; z = -1 and z = Lz over x in [0, Lx), y in [0, Ly).  A ghost
-// population i is written only if it streams into the box (y + c_i inside).
-// Corner nodes stream into no fluid node and write nothing.
+// Ghost nodes (see shell_node for the face enumeration).  Corner nodes stream
+// into no fluid node and write nothing.
 template <typename S, typename C>
-__global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, Model m, Grad A, CentreParts cp,
+__global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, Model m, Grad G, CentreParts cp,
                                                int* __restrict__ d_err) {
     // frame origin: the droplet's centre of mass of the current state
     C xc = C(0), yc = C(0), zc = C(0);
@@ -75,269 +73,28 @@ __global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, Mode
         yc = (C)cp.sum[5];
         zc = (C)cp.sum[6];
     }
-    // grid: x = fast face coordinate (32-wide blocks), y = slow face
-    // coordinate, z = face (0/1: x = -1 / Lx over y, z in [-1, L]; 2/3: y = -1 / Ly
-    // over x in [0, Lx), z in [-1, Lz]; 4/5: z = -1 / Lz over x, y inside)
-    const int face = blockIdx.z;
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    const int b = blockIdx.y * blockDim.y + threadIdx.y;
     int x, y, z;
-    if (face < 2) {
-        if (a >= L.Ly + 2 || b >= L.Lz + 2) return;
-        x = face ? L.Lx : -1; y = a - 1; z = b - 1;
-    } else if (face < 4) {
-        if (a >= L.Lx || b >= L.Lz + 2) return;
-        y = face == 3 ? L.Ly : -1; x = a; z = b - 1;
-    } else {
-        if (a >= L.Lx || b >= L.Ly) return;
-        z = face == 5 ? L.Lz : -1; x = a; y = b;
-    }
-    // position relative to the frame origin, then the flow and Eq. 8 in the
-    // compute type of the populations (fp64 arithmetic is slow on this part)
-    const C px = (C(x) - C(0.5) * C(L.Lx - 1)) - xc, py = (C(y) - C(0.5) * C(L.Ly - 1)) - yc,
-            pz = (C(z) - C(0.5) * C(L.Lz - 1)) - zc;
-    const C ux = (C)A.a[0] * px + (C)A.a[1] * py + (C)A.a[2] * pz;
-    const C uy = (C)A.a[3] * px + (C)A.a[4] * py + (C)A.a[5] * pz;
-    const C uz = (C)A.a[6] * px + (C)A.a[7] * py + (C)A.a[8] * pz;
-    const C usq = ux * ux + uy * uy + uz * uz;
-    const C u2x = C(1.5) * usq;
-    bool any = false;
+    if (!shell_node(L, blockIdx.z, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y, x,
+                    y, z))
+        return;
+    C A[9];
 #pragma unroll
-    for (int i = 1; i < 19; ++i) {
-        const int xi = x + cx_(i), yi = y + cy_(i), zi = z + cz_(i);
-        if (xi < 0 || xi >= L.Lx || yi < 0 || yi >= L.Ly || zi < 0 || zi >= L.Lz) continue;
-        any = true;
-#pragma unroll
-        for (int s = 0; s < 2; ++s) f[L.at(s, i, x, y, z)] = (S)feq<C>(i, (C)m.rho_b[s], ux, uy, uz, u2x);
-    }
-    if (any && (double)usq > m.mach2) atomicOr(d_err, 2);
+    for (int j = 0; j < 9; ++j) A[j] = (C)G.a[j];
+    ghost_node<S, C>(f, L, m, A, xc, yc, zc, x, y, z, d_err);
 }
-
-// Fixed-order reduction of the per-CTA centre partials by the last CTA to
-// finish (threadfence-reduction pattern); every thread of the CTA calls it.
-// `scratch` holds 4 doubles per warp of shared memory.
-__device__ void centre_epilogue(double (&cm)[4], CentreParts cp, double* scratch) {
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = (blockDim.x + 31) >> 5;
-    const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    const unsigned total = gridDim.x * gridDim.y * gridDim.z;
-    __shared__ unsigned last;
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        double a = cm[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) scratch[4 * warp + q] = a;
-    }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            double a = lane < nwarps ? scratch[4 * lane + q] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-            if (lane == 0) cp.p[4 * cta + q] = a;
-        }
-        if (lane == 0) {
-            __threadfence();
-            last = atomicAdd(cp.counter, 1u) == total - 1 ? 1u : 0u;
-        }
-    }
-    __syncthreads();
-    if (last && warp == 0) {
-        __threadfence();
-        double s4[4] = {0.0, 0.0, 0.0, 0.0};
-        for (unsigned b = lane; b < total; b += 32)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) s4[q] += __ldcg(cp.p + 4LL * b + q);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s4[q] += __shfl_down_sync(0xffffffffu, s4[q], o);
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) cp.sum[q] = s4[q];
-            // frame origin x_c = sum w x / sum w (box centre when there is no droplet)
-            const bool have = s4[0] > 0.0;
-            for (int q = 0; q < 3; ++q) cp.sum[4 + q] = have ? s4[1 + q] / s4[0] : 0.0;
-            *cp.counter = 0u;
-        }
-    }
-}
-
-// ----------------------------------------------------------------------------
-// Fused pull-stream + Shan-Chen force + collision.
-template <typename C>
-struct ModelC {
-    C inv_tau[2], tau[2], G, rho_b[2];
-};
-
-template <typename S, typename C, bool PER>
-struct Puller {
-    const S* __restrict__ src;
-    Layout L;
-
-    // Element index of population (s, i) pulled into fluid node (x, y, z).
-    __device__ __forceinline__ long long idx(int s, int i, int x, int y, int z) const {
-        if (PER) {
-            return L.at(s, i, wrap(x - cx_(i), L.Lx), wrap(y - cy_(i), L.Ly), wrap(z - cz_(i), L.Lz));
-        }
-        return L.at(s, i, x, y, z) - ((long long)cz_(i) * L.plane + (long long)cy_(i) * L.pitch + cx_(i));
-    }
-
-    // Pull all 38 populations of fluid node (x, y, z).
-    __device__ __forceinline__ void pull(int x, int y, int z, C (&f)[2][19]) const {
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int i = 0; i < 19; ++i) f[s][i] = (C)__ldg(src + idx(s, i, x, y, z));
-    }
-
-    // Post-streaming densities at (x, y, z), any position: outside the box
-    // the ghost density (or the periodic image).
-    __device__ __forceinline__ void rho_at(int x, int y, int z, const ModelC<C>& m, C& ra, C& rb) const {
-        if (PER) {
-            x = wrap(x, L.Lx); y = wrap(y, L.Ly); z = wrap(z, L.Lz);
-        } else if (x < 0 || x >= L.Lx || y < 0 || y >= L.Ly || z < 0 || z >= L.Lz) {
-            ra = m.rho_b[0]; rb = m.rho_b[1];
-            return;
-        }
-        C f[2][19];
-        pull(x, y, z, f);
-        ra = sum19<C>(f[0]);
-        rb = sum19<C>(f[1]);
-    }
-};
 
 template <typename S, typename C, bool PER, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, Layout L,
                                                           ModelC<C> m, int TX, int TY, int zchunk, CentreParts cp,
                                                           int* __restrict__ d_err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* ring = reinterpret_cast<C*>(smem_raw);
-    const int RW = TX + 2, RS = RW * (TY + 2);
-    const int NT = TX * TY;
-    const int H = 2 * RW + 2 * TY;  // halo nodes per plane
-    const int t = threadIdx.x;
-    const int tx = t % TX, ty = t / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int x = x0 + tx, y = y0 + ty;
-    const bool active = x < L.Lx && y < L.Ly;
     const int zc0 = blockIdx.z * zchunk;
     const int zc1 = min(zc0 + zchunk, L.Lz);
-    Puller<S, C, PER> P{src, L};
-
-    auto R = [&](int slot, int s, int hx, int hy) -> C& { return ring[(slot * 2 + s) * RS + (hy + 1) * RW + (hx + 1)]; };
-
-    // Densities of the halo ring of plane z into ring slot `slot`.
-    auto halo = [&](int z, int slot) {
-        for (int h = t; h < H; h += NT) {
-            int hx, hy;
-            if (h < RW) { hx = h - 1; hy = -1; }
-            else if (h < 2 * RW) { hx = h - RW - 1; hy = TY; }
-            else if (h < 2 * RW + TY) { hx = -1; hy = h - 2 * RW; }
-            else { hx = TX; hy = h - 2 * RW - TY; }
-            C ra, rb;
-            P.rho_at(x0 + hx, y0 + hy, z, m, ra, rb);
-            R(slot, 0, hx, hy) = ra;
-            R(slot, 1, hx, hy) = rb;
-        }
-    };
-    // Densities only (tile + halo) of plane z.
-    auto rho_plane = [&](int z, int slot) {
-        C ra, rb;
-        P.rho_at(x, y, z, m, ra, rb);
-        R(slot, 0, tx, ty) = ra;
-        R(slot, 1, tx, ty) = rb;
-        halo(z, slot);
-    };
-    // droplet moments {sum w, sum w x, sum w y, sum w z} of the state written
-    // here, w = max(phi, 0); they give the next step's frame origin.  Summed
-    // over the thread's z column in the compute type, then reduced in double.
     C cm[4] = {C(0), C(0), C(0), C(0)};
-    const C pxc = C(x) - C(0.5) * C(L.Lx - 1), pyc = C(y) - C(0.5) * C(L.Ly - 1);
-
-    rho_plane(zc0 - 1, (zc0 - 1) & 3);
-    rho_plane(zc0, zc0 & 3);
-
-    for (int z = zc0; z < zc1; ++z) {
-        rho_plane(z + 1, (z + 1) & 3);
-        __syncthreads();
-
-        if (active) {
-            // the node's pulled populations again (second read, from L1/L2)
-            C fc[2][19];
-            P.pull(x, y, z, fc);
-            const int s0 = (z - 1) & 3, s1 = z & 3, s2 = (z + 1) & 3;
-            const C rho[2] = {R(s1, 0, tx, ty), R(s1, 1, tx, ty)};
-            // momentum of each component (Eq. 6), opposite pairs first
-            C j[2][3];
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                C jx = C(0), jy = C(0), jz = C(0);
-#pragma unroll
-                for (int i = 1; i < 19; i += 2) {
-                    const C d = fc[s][i] - fc[s][i + 1];
-                    if (cx_(i)) jx += C(cx_(i)) * d;
-                    if (cy_(i)) jy += C(cy_(i)) * d;
-                    if (cz_(i)) jz += C(cz_(i)) * d;
-                }
-                j[s][0] = jx; j[s][1] = jy; j[s][2] = jz;
-            }
-            // Shan-Chen force (Eq. 7): F^s = -G rho_s sum_i w_i rho_s'(x + c_i) c_i,
-            // with the neighbour pair x + c_i, x - c_i differenced first
-            C acc[2][3] = {{C(0), C(0), C(0)}, {C(0), C(0), C(0)}};
-#pragma unroll
-            for (int i = 1; i < 19; i += 2) {
-                const int sp = cz_(i) == 0 ? s1 : (cz_(i) > 0 ? s2 : s0);
-                const int sm = cz_(i) == 0 ? s1 : (cz_(i) > 0 ? s0 : s2);
-                const C da = wgt<C>(i) * (R(sp, 0, tx + cx_(i), ty + cy_(i)) - R(sm, 0, tx - cx_(i), ty - cy_(i)));
-                const C db = wgt<C>(i) * (R(sp, 1, tx + cx_(i), ty + cy_(i)) - R(sm, 1, tx - cx_(i), ty - cy_(i)));
-                if (cx_(i)) { acc[0][0] += C(cx_(i)) * da; acc[1][0] += C(cx_(i)) * db; }
-                if (cy_(i)) { acc[0][1] += C(cy_(i)) * da; acc[1][1] += C(cy_(i)) * db; }
-                if (cz_(i)) { acc[0][2] += C(cz_(i)) * da; acc[1][2] += C(cz_(i)) * db; }
-            }
-            // common velocity u' and per-component shifted velocity
-            const C den = rho[0] * m.inv_tau[0] + rho[1] * m.inv_tau[1];
-            C up[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) up[a] = (j[0][a] * m.inv_tau[0] + j[1][a] * m.inv_tau[1]) / den;
-            if (!(isfinite(rho[0]) && isfinite(rho[1]))) atomicOr(d_err, 1);
-            {
-                const C phi = (rho[0] - rho[1]) / (rho[0] + rho[1]);
-                const C wphi = phi > C(0) ? phi : C(0);
-                cm[0] += wphi;
-                cm[1] += wphi * pxc;
-                cm[2] += wphi * pyc;
-                cm[3] += wphi * (C(z) - C(0.5) * C(L.Lz - 1));
-            }
-            const long long base = L.at(0, 0, x, y, z);
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                // tau_s F^s / rho_s = -G tau_s * (the other component's sum)
-                const C sh = -m.G * m.tau[s];
-                const C ux = up[0] + sh * acc[1 - s][0];
-                const C uy = up[1] + sh * acc[1 - s][1];
-                const C uz = up[2] + sh * acc[1 - s][2];
-                const C u2x = C(1.5) * (ux * ux + uy * uy + uz * uz);
-                // moving populations; the rest population then closes the
-                // mass balance exactly (sum of outputs = rho), which keeps
-                // fp32 rounding from drifting the interface
-                C others = C(0);
-#pragma unroll
-                for (int i = 1; i < 19; ++i) {
-                    const C f = fc[s][i];
-                    const C g = feq<C>(i, rho[s], ux, uy, uz, u2x);
-                    const S o = (S)(f - (f - g) * m.inv_tau[s]);
-                    dst[base + (long long)(s * 19 + i) * L.array] = o;
-                    others += (C)o;
-                }
-                dst[base + (long long)(s * 19) * L.array] = (S)(rho[s] - others);
-            }
-        }
-    }
+    tile_march<S, C, PER>(src, dst, L, m, TX, TY, blockIdx.x * TX, blockIdx.y * TY, zc0, zc1,
+                          reinterpret_cast<C*>(smem_raw), d_err, cm);
     double cmd[4] = {(double)cm[0], (double)cm[1], (double)cm[2], (double)cm[3]};
+    __syncthreads();  // the ring is reused as reduction scratch
     centre_epilogue(cmd, cp, reinterpret_cast<double*>(smem_raw));
 }
 

@@ -29,6 +29,9 @@ ABI_FUNCTIONS = [
     "lbm_deformation", "lbm_moments", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
     "lbm_checksums", "lbm_get_step", "lbm_save", "lbm_load", "lbm_profile_enable", "lbm_profile_read",
     "lbm_launch_shape", "lbm_destroy", "lbm_strerror", "lbm_moments_static",
+    "lbm_batch_create", "lbm_batch_set_gradients", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_deformation",
+    "lbm_batch_get_populations", "lbm_batch_set_populations", "lbm_batch_autotune", "lbm_batch_shape",
+    "lbm_batch_destroy",
 ]
 
 
@@ -92,6 +95,17 @@ def load_library(path=LIB_PATH):
         "lbm_destroy": (None, [vp]),
         "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "lbm_moments_static": (ctypes.c_int, [vp, ctypes.c_int32, _I32P, vp, vp]),
+        "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int32, _I32P, _DP, _DP, ctypes.c_double,
+                                            ctypes.POINTER(lbm_opts)]),
+        "lbm_batch_set_gradients": (ctypes.c_int, [vp, ctypes.c_int64, _DP]),
+        "lbm_batch_step": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "lbm_batch_sync": (ctypes.c_int, [vp]),
+        "lbm_batch_deformation": (ctypes.c_int, [vp, _DP, _DP, _DP]),
+        "lbm_batch_get_populations": (ctypes.c_int, [vp, ctypes.c_int32, _DP]),
+        "lbm_batch_set_populations": (ctypes.c_int, [vp, ctypes.c_int32, _DP]),
+        "lbm_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int32, _I32P, _I32P]),
+        "lbm_batch_shape": (ctypes.c_int, [vp, _I32P, _I32P, _I32P]),
+        "lbm_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -271,3 +285,91 @@ class DropletLBM:
         _check(self._lib.lbm_launch_shape(self._h, ctypes.byref(ty), ctypes.byref(zc), ctypes.byref(ctas)),
                "lbm_launch_shape")
         return ty.value, zc.value, ctas.value
+
+
+class BatchLBM:
+    """An ensemble of independent droplet boxes behind the C ABI (fp32).
+
+    ``boxes`` is a sequence of (Lx, Ly, Lz); ``R`` the droplet radius of each
+    box; ``rho_lo`` the ghost density of the droplet component (required).
+    """
+
+    def __init__(self, boxes, R, visc, G, rho_lo, rho_hi=0.0, xi=0.0, mach_limit=0.0, stream=None, device=-1,
+                 z_chunk=0, frame="droplet"):
+        lib = load_library()
+        self._lib = lib
+        self.boxes = [tuple(int(v) for v in b) for b in boxes]
+        self.nbox = len(self.boxes)
+        o = lbm_opts()
+        lib.lbm_opts_default(ctypes.byref(o))
+        o.precision = LBM_FP32
+        o.bc = LBM_BC_GHOST_LINEAR
+        o.rho_hi, o.rho_lo, o.xi, o.mach_limit = float(rho_hi), float(rho_lo), float(xi), float(mach_limit)
+        if stream is None:
+            stream = current_torch_stream()
+        o.cuda_stream = stream
+        o.device = int(device)
+        o.z_chunk = int(z_chunk)
+        o.frame = FRAMES[frame]
+        flat = (ctypes.c_int32 * (3 * self.nbox))(*[v for b in self.boxes for v in b])
+        r = np.ascontiguousarray(np.asarray(R, dtype=np.float64).reshape(self.nbox))
+        v = (ctypes.c_double * 2)(float(visc[0]), float(visc[1]))
+        h = ctypes.c_void_p()
+        _check(lib.lbm_batch_create(ctypes.byref(h), self.nbox, flat, _dptr(r), v, float(G), ctypes.byref(o)),
+               "lbm_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape_of(self, k):
+        Lx, Ly, Lz = self.boxes[k]
+        return (2, 19, Lz, Ly, Lx)
+
+    def set_gradients(self, A):
+        """A[t, k, 9]: gradient of box k at step t."""
+        A = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
+        assert A.ndim == 3 and A.shape[1] == self.nbox and A.shape[2] == 9
+        _check(self._lib.lbm_batch_set_gradients(self._h, int(A.shape[0]), _dptr(A)), "lbm_batch_set_gradients")
+
+    def step(self, n=1):
+        _check(self._lib.lbm_batch_step(self._h, int(n)), "lbm_batch_step")
+
+    def sync(self):
+        _check(self._lib.lbm_batch_sync(self._h), "lbm_batch_sync")
+
+    def deformation(self):
+        D = np.zeros(self.nbox)
+        axes = np.zeros(9 * self.nbox)
+        c = np.zeros(3 * self.nbox)
+        _check(self._lib.lbm_batch_deformation(self._h, _dptr(D), _dptr(axes), _dptr(c)), "lbm_batch_deformation")
+        return D, axes.reshape(self.nbox, 3, 3), c.reshape(self.nbox, 3)
+
+    def populations(self, k):
+        f = np.zeros(self.shape_of(k))
+        _check(self._lib.lbm_batch_get_populations(self._h, int(k), _dptr(f)), "lbm_batch_get_populations")
+        return f
+
+    def set_populations(self, k, f):
+        f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(self.shape_of(k)))
+        _check(self._lib.lbm_batch_set_populations(self._h, int(k), _dptr(f)), "lbm_batch_set_populations")
+
+    def autotune(self, trial_steps=4):
+        zc, per = ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.lbm_batch_autotune(self._h, int(trial_steps), ctypes.byref(zc), ctypes.byref(per)),
+               "lbm_batch_autotune")
+        return zc.value, per.value
+
+    def shape(self):
+        zc, ctas, items = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.lbm_batch_shape(self._h, ctypes.byref(zc), ctypes.byref(ctas), ctypes.byref(items)),
+               "lbm_batch_shape")
+        return zc.value, ctas.value, items.value
