@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--z-chunk", type=int, default=0)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-ensemble", action="store_true")
+    p.add_argument("--ensemble-steps", type=int, default=200)
     return p.parse_args()
 
 
@@ -173,6 +175,71 @@ def cpu_baseline(w, hist, steps=None):
             "sample": f"{done} steps of the full {w.box}^3 box (FP64, all host cores), {el:.1f} s"}
 
 
+def ensemble_bench(steps, stream, dev):
+    """Droplet trajectories per second: the 512-box ensemble in one persistent
+    launch per step (graph replay, autotuned) against the plain single-box
+    path running the same boxes one after another, and the D difference
+    between the two after `steps` steps."""
+    import numpy as np
+    import torch
+
+    from paper_2112_09972_gb300 import workloads
+    from paper_2112_09972_gb300.lbm import BatchLBM, DropletLBM
+
+    e = workloads.C3_ENSEMBLE
+    edges = e.box_edges()
+    boxes = [(int(L),) * 3 for L in edges]
+    R = [L / 5.0 for L in edges]
+    warm = 20
+    hist = e.histories(steps + warm + 4)
+    t0 = time.perf_counter()
+    bt = BatchLBM(boxes, R, e.visc, e.G, rho_lo=e.rho_lo, stream=stream.cuda_stream, device=dev)
+    bt.set_gradients(hist)
+    zc, per = bt.autotune(trial_steps=4)
+    setup_s = time.perf_counter() - t0
+    bt.step(warm)
+    bt.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    bt.step(steps)
+    ev1.record(stream)
+    bt.sync()
+    t_batch = ev0.elapsed_time(ev1) / 1e3 / steps  # seconds per ensemble step
+    D_batch, _, _ = bt.deformation()
+    zc_used, ctas, items = bt.shape()
+    bt.close()
+    # plain path: one box of each edge, timed per step, weighted by the ensemble's mix
+    per_edge, D_err = {}, []
+    for L in sorted(set(int(v) for v in edges)):
+        k = int(np.flatnonzero(edges == L)[0])
+        g = DropletLBM((L,) * 3, L / 5.0, e.visc, e.G, precision="fp32", rho_lo=e.rho_lo,
+                       stream=stream.cuda_stream, device=dev)
+        g.set_gradient_table(np.arange(hist.shape[0]), hist[:, k])
+        g.step(warm)
+        g.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.step(steps)
+        b.record(stream)
+        g.sync()
+        per_edge[L] = a.elapsed_time(b) / 1e3 / steps
+        D_plain = g.deformation()[0]
+        D_err.append(abs(D_batch[k] - D_plain) / max(abs(D_plain), 1e-12))
+        g.close()
+    t_plain = sum(per_edge[int(L)] for L in edges)  # the boxes one after another
+    nodes = int(sum(int(L) ** 3 for L in edges))
+    return {
+        "workload": e.name, "boxes": e.nbox, "steps_per_trajectory": e.steps, "timed_steps": steps,
+        "batched_droplets_per_s": round(1.0 / (t_batch * e.steps), 4),
+        "plain_droplets_per_s": round(1.0 / (t_plain * e.steps) * 1.0, 4),
+        "speedup": round(t_plain / t_batch, 2),
+        "batched_mlups": round(nodes / t_batch / 1e6, 1),
+        "max_rel_D_difference_batched_vs_plain": float(max(D_err)),
+        "autotuned": {"z_chunk": zc_used, "ctas_per_sm": per, "ctas": ctas, "items": items},
+        "setup_s": round(setup_s, 2),
+    }
+
+
 def run_reference(args, w):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -287,6 +354,9 @@ def main():
                "h2d_bytes_per_step": round(h2d / K, 1), "d2h_bytes_per_step": round(d2h / K, 3)}
         g2.close()
 
+    ens = None
+    if not args.no_ensemble and world == 1:
+        ens = ensemble_bench(args.ensemble_steps, stream, dev)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -326,6 +396,7 @@ def main():
         "clocks": clk,
         "e2e": e2e,
         "cpu_baseline": cb,
+        "ensemble": ens,
         "D_last": samples[-1] if samples else None,
     }
     print(json.dumps(line))

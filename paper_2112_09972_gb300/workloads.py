@@ -96,3 +96,42 @@ C2_THROUGHPUT = Workload("droplet128_R16_ou", box=128, R=16.0, steps=20000, prec
                          driving="ou_eq15", seed=12346, T_corr=2000.0, u_lbm=0.1)
 
 WORKLOADS = {w.name: w for w in (C1_PARITY, C2_THROUGHPUT)}
+
+
+@dataclass
+class Ensemble:
+    """Independent droplet boxes of uneven sizes, each with its own gradient history."""
+
+    name: str
+    nbox: int
+    edges: tuple
+    steps: int
+    seed: int
+    tau: float = 1.0
+    G: float = G_COUPLING
+    rho_hi: float = RHO_HI
+    rho_lo: float = RHO_LO
+    T_corr: float = 2000.0
+    u_lbm: float = 0.1
+
+    def box_edges(self):
+        rng = np.random.Generator(np.random.Philox(key=[int(self.seed), 3]))
+        return rng.choice(np.asarray(self.edges), size=self.nbox)
+
+    @property
+    def visc(self):
+        return (nu_of_tau(self.tau), nu_of_tau(self.tau))
+
+    def histories(self, n_steps):
+        """A[t, k, 9]: OU history of box k (its own Philox stream), Eq. 15-rescaled to its edge."""
+        edges = self.box_edges()
+        out = np.empty((n_steps, self.nbox, 9))
+        for k in range(self.nbox):
+            h = inputs.ou_gradient_history(n_steps, self.T_corr, 1.0, self.seed, box_id=k)
+            out[:, k] = inputs.rescale_to_lattice(h, self.u_lbm, int(edges[k]))
+        return out
+
+
+# 512 boxes with edges drawn from {40, 48, 56, 64}, R = edge/5, fp32,
+# 10000 steps each.
+C3_ENSEMBLE = Ensemble("ensemble512_edges40-64", nbox=512, edges=(40, 48, 56, 64), steps=10000, seed=12347)
