@@ -191,11 +191,12 @@ int lbm_save(lbm_ctx* ctx, const char* path);
 int lbm_load(lbm_ctx* ctx, const char* path);
 
 /*
- * Kernel timing: while enabled, every launch of the stream-collide kernel
- * (kernel 0) and the ghost kernel (kernel 1) is bracketed by CUDA events on
- * the context's stream.  lbm_profile_read synchronises and returns the summed
- * device time in milliseconds and the number of launches since the last
- * enable.
+ * Kernel timing: lbm_profile_enable(ctx, k) with k > 0 brackets the launches
+ * of every k-th step (step counter divisible by k) of the stream-collide
+ * kernel (kernel 0) and of the ghost kernel (kernel 1) with CUDA events on
+ * the context's stream; k = 0 turns it off.  lbm_profile_read synchronises
+ * and returns the summed device time in milliseconds and the number of timed
+ * launches since the last enable.
  */
 int lbm_profile_enable(lbm_ctx* ctx, int enable);
 int lbm_profile_read(lbm_ctx* ctx, int kernel, double* total_ms, int64_t* launches);

@@ -45,8 +45,8 @@ struct lbm_ctx {
     int red_blocks;
     double* d_result;  // 32 doubles
     double* h_result;  // pinned
-    // profiling
-    bool prof;
+    // profiling: events around the launches of every prof-th step (0: off)
+    int prof;
     std::vector<cudaEvent_t> ev[2];
     int64_t prof_n[2];
 };
@@ -328,29 +328,31 @@ int lbm_step(lbm_ctx* c, int64_t n) {
     for (int64_t k = 0; k < n; ++k) {
         void* src = c->f[c->cur];
         void* dst = c->f[1 - c->cur];
-        if (!c->model.periodic) {
-            const Grad A = gradient_at(c, (double)c->step);
+        const bool timed = c->prof > 0 && (c->step % c->prof) == 0;
+        const Grad A = gradient_at(c, (double)c->step);
+        // the row-tiled kernel computes its ghost equilibria itself
+        if (!c->model.periodic && !c->shape.rows) {
             cudaEvent_t a = nullptr, b = nullptr;
-            if (c->prof) {
+            if (timed) {
                 cudaEventCreate(&a);
                 cudaEventCreate(&b);
                 cudaEventRecord(a, c->stream);
             }
             LBM_TRY(launch_ghost(c->prec, src, c->L, c->model, A, c->centre, c->d_err, c->stream));
-            if (c->prof) {
+            if (timed) {
                 cudaEventRecord(b, c->stream);
                 c->ev[1].push_back(a);
                 c->ev[1].push_back(b);
             }
         }
         cudaEvent_t a = nullptr, b = nullptr;
-        if (c->prof) {
+        if (timed) {
             cudaEventCreate(&a);
             cudaEventCreate(&b);
             cudaEventRecord(a, c->stream);
         }
-        LBM_TRY(launch_stream_collide(c->prec, src, dst, c->L, c->model, c->shape, c->centre, c->d_err, c->stream));
-        if (c->prof) {
+        LBM_TRY(launch_stream_collide(c->prec, src, dst, c->L, c->model, c->shape, A, c->centre, c->d_err, c->stream));
+        if (timed) {
             cudaEventRecord(b, c->stream);
             c->ev[0].push_back(a);
             c->ev[0].push_back(b);
@@ -568,7 +570,7 @@ int lbm_profile_enable(lbm_ctx* c, int enable) {
         c->ev[k].clear();
         c->prof_n[k] = 0;
     }
-    c->prof = enable != 0;
+    c->prof = enable > 0 ? enable : 0;
     return LBM_OK;
 }
 

@@ -79,16 +79,18 @@ cudaError_t launch_init(int prec, void* f, const Layout& L, double R, double xi,
                         Grad A0, cudaStream_t s);
 cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Grad A, CentreParts cp, int* d_err,
                          cudaStream_t s);
+// A: the boundary gradient of this step, used by kernels that compute the
+// ghost equilibria themselves (Shape::rows); the others read the ghost shell.
 cudaError_t launch_stream_collide(int prec, const void* src, void* dst, const Layout& L, const Model& m,
-                                  const Shape& sh, CentreParts cp, int* d_err, cudaStream_t s);
+                                  const Shape& sh, const Grad& A, CentreParts cp, int* d_err, cudaStream_t s);
 // Centre-of-mass partials of the stored populations f (cp.n CTAs, grid-stride).
 cudaError_t launch_centre(int prec, const void* f, const Layout& L, CentreParts cp, cudaStream_t s);
 
 // ---- row-tiled cluster kernel (lbm_fast.cu): fp32, ghost boundary, Lx in {32, 64, 128}, Ly % 8 == 0 ----
 bool rows_kernel_applies(const Layout& L, int prec, int periodic);
 int rows_kernel_resident_ctas(const Layout& L);
-cudaError_t launch_stream_collide_rows(const void* src, void* dst, const Layout& L, const Model& m, int zchunk,
-                                       CentreParts cp, int* d_err, cudaStream_t s);
+cudaError_t launch_stream_collide_rows(const void* src, void* dst, const Layout& L, const Model& m, const Grad& A,
+                                       int zchunk, CentreParts cp, int* d_err, cudaStream_t s);
 
 // ---- launchers (lbm_reduce.cu) ----
 // Ten moments of w = max(phi, 0) and the deformation: result[0..9] moments,

@@ -251,8 +251,8 @@ cudaError_t launch_centre(int prec, const void* f, const Layout& L, CentreParts 
 }
 
 cudaError_t launch_stream_collide(int prec, const void* src, void* dst, const Layout& L, const Model& m,
-                                  const Shape& sh, CentreParts cp, int* d_err, cudaStream_t s) {
-    if (sh.rows) return launch_stream_collide_rows(src, dst, L, m, sh.zchunk, cp, d_err, s);
+                                  const Shape& sh, const Grad& A, CentreParts cp, int* d_err, cudaStream_t s) {
+    if (sh.rows) return launch_stream_collide_rows(src, dst, L, m, A, sh.zchunk, cp, d_err, s);
     if (prec == 0) return stream_collide_t<double, double, kMaxThreadsF64>(src, dst, L, m, sh, cp, d_err, s);
     return stream_collide_t<float, float, kMaxThreadsF32>(src, dst, L, m, sh, cp, d_err, s);
 }

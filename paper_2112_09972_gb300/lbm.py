@@ -271,8 +271,9 @@ class DropletLBM:
     def load(self, path):
         _check(self._lib.lbm_load(self._h, str(path).encode()), "lbm_load")
 
-    def profile(self, enable=True):
-        _check(self._lib.lbm_profile_enable(self._h, int(bool(enable))), "lbm_profile_enable")
+    def profile(self, every=1):
+        """Time the launches of every `every`-th step (0 or False: off)."""
+        _check(self._lib.lbm_profile_enable(self._h, int(every)), "lbm_profile_enable")
 
     def profile_read(self, kernel=0):
         ms = ctypes.c_double()
