@@ -330,8 +330,7 @@ int lbm_step(lbm_ctx* c, int64_t n) {
         void* dst = c->f[1 - c->cur];
         const bool timed = c->prof > 0 && (c->step % c->prof) == 0;
         const Grad A = gradient_at(c, (double)c->step);
-        // the row-tiled kernel computes its ghost equilibria itself
-        if (!c->model.periodic && !c->shape.rows) {
+        if (!c->model.periodic) {
             cudaEvent_t a = nullptr, b = nullptr;
             if (timed) {
                 cudaEventCreate(&a);

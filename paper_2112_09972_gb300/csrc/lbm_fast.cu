@@ -19,10 +19,7 @@
 //     a second time (ratio 2/CY); that work is split evenly over the CTAs of
 //     the cluster, which push those densities into the edge CTAs' rings.
 // There is no cluster-wide barrier and no memory fence per plane: a CTA waits
-// only for the two rows it reads.  The ghost-node rebuild of Eqs. 8 and 14 is
-// fused in: a node on the box face computes the ghost equilibrium of each
-// source outside the box where it would load it, so this path reads and
-// writes no ghost shell at all.  DRAM sees about one read and one write of
+// only for the two rows it reads.  DRAM sees about one read and one write of
 // every population; L2 serves the second read and the outer-halo reads.
 //
 // Sums over opposite velocity pairs are differenced first (c_{2k} = -c_{2k-1}),
@@ -41,9 +38,6 @@ namespace {
 
 struct FastModel {
     float inv_tau[2], tau[2], G, rho_b[2];
-    float A[9];     // boundary gradient of this step
-    float mach2;    // guard on |u_ghost|^2
-    int droplet_frame;
 };
 
 // Shared-memory, cluster-address and mbarrier helpers (inline PTX).
@@ -116,48 +110,6 @@ __device__ __forceinline__ float pulled_last(const float* __restrict__ src, cons
     return __ldlu(pulled_ptr(src, L, b, s, i));
 }
 
-// Ghost equilibrium of population (s, i) at the out-of-box node (xs, ys, zs):
-// Eq. 8 at the ghost density with the flow A (p - x_c) of Eq. 14 (the
-// ghost-node rebuild, computed where it is pulled instead of stored).
-__device__ __forceinline__ float ghost_value(const Layout& L, const FastModel& m, const float (&xc)[3], int s, int i,
-                                             int xs, int ys, int zs, int* __restrict__ d_err) {
-    const float px = ((float)xs - 0.5f * (float)(L.Lx - 1)) - xc[0];
-    const float py = ((float)ys - 0.5f * (float)(L.Ly - 1)) - xc[1];
-    const float pz = ((float)zs - 0.5f * (float)(L.Lz - 1)) - xc[2];
-    const float ux = m.A[0] * px + m.A[1] * py + m.A[2] * pz;
-    const float uy = m.A[3] * px + m.A[4] * py + m.A[5] * pz;
-    const float uz = m.A[6] * px + m.A[7] * py + m.A[8] * pz;
-    const float usq = ux * ux + uy * uy + uz * uz;
-    if (usq > m.mach2) atomicOr(d_err, 2);
-    return feq<float>(i, m.rho_b[s], ux, uy, uz, 1.5f * usq);
-}
-
-// The 38 populations pulled into node (x, y, z) (element index b of its
-// (s=0, i=0) slot): loads, except that a node on the box face takes the ghost
-// equilibrium for every source outside the box.  `last` selects the last-use
-// load of the second read; otherwise the evict_last policy `pol` is used.
-__device__ __forceinline__ void pull_node(const float* __restrict__ src, const Layout& L, const FastModel& m,
-                                          const float (&xc)[3], long long b, int x, int y, int z, bool last,
-                                          unsigned long long pol, float (&q)[2][19], int* __restrict__ d_err) {
-    const bool face = x == 0 || x == L.Lx - 1 || y == 0 || y == L.Ly - 1 || z == 0 || z == L.Lz - 1;
-    if (!face) {
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int i = 0; i < 19; ++i) q[s][i] = last ? pulled_last(src, L, b, s, i) : pulled(src, L, b, s, i, pol);
-        return;
-    }
-#pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        const int xs = x - cx_(i), ys = y - cy_(i), zs = z - cz_(i);
-        const bool out = xs < 0 || xs >= L.Lx || ys < 0 || ys >= L.Ly || zs < 0 || zs >= L.Lz;
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-            q[s][i] = out ? ghost_value(L, m, xc, s, i, xs, ys, zs, d_err)
-                          : (last ? pulled_last(src, L, b, s, i) : pulled(src, L, b, s, i, pol));
-    }
-}
-
 template <int TX, int CY, int MINB>
 __global__ void __launch_bounds__(TX, MINB)
     k_stream_collide_rows(const float* __restrict__ src, float* __restrict__ dst, Layout L, FastModel m, int zchunk,
@@ -208,11 +160,6 @@ __global__ void __launch_bounds__(TX, MINB)
 
     const long long node0 = L.at(0, 0, x, y, 0);      // (s=0, i=0, x, y, z=0)
     const long long hnode0 = L.at(0, 0, hcol, hin ? hy : 0, 0);
-    // frame origin of the ghost flow: the droplet's centre of mass of the
-    // state being read (written by the previous step's last CTA)
-    float xc[3] = {0.f, 0.f, 0.f};
-    if (m.droplet_frame)
-        for (int q = 0; q < 3; ++q) xc[q] = (float)cp.sum[4 + q];
     unsigned long long keep;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
 
@@ -227,10 +174,14 @@ __global__ void __launch_bounds__(TX, MINB)
         const bool in = p >= 0 && p < L.Lz;
         float ra = m.rho_b[0], rb = m.rho_b[1];
         if (in) {
-            float q[2][19];
-            pull_node(src, L, m, xc, node0 + (long long)p * L.plane, x, y, p, false, keep, q, d_err);
-            ra = sum19<float>(q[0]);
-            rb = sum19<float>(q[1]);
+            const long long b = node0 + (long long)p * L.plane;
+            ra = pulled(src, L, b, 0, 0, keep);
+            rb = pulled(src, L, b, 1, 0, keep);
+#pragma unroll
+            for (int i = 1; i < 19; i += 2) {
+                ra += pulled(src, L, b, 0, i, keep) + pulled(src, L, b, 0, i + 1, keep);
+                rb += pulled(src, L, b, 1, i, keep) + pulled(src, L, b, 1, i + 1, keep);
+            }
         }
         *reinterpret_cast<float2*>(ring + ridx(slot, 0, x)) = make_float2(ra, rb);
         const unsigned mb = 8u * slot;
@@ -239,10 +190,14 @@ __global__ void __launch_bounds__(TX, MINB)
         if (hthr) {
             float ha = m.rho_b[0], hb = m.rho_b[1];
             if (in && hin) {
-                float q[2][19];
-                pull_node(src, L, m, xc, hnode0 + (long long)p * L.plane, hcol, hy, p, false, keep, q, d_err);
-                ha = sum19<float>(q[0]);
-                hb = sum19<float>(q[1]);
+                const long long b = hnode0 + (long long)p * L.plane;
+                ha = pulled(src, L, b, 0, 0, keep);
+                hb = pulled(src, L, b, 1, 0, keep);
+#pragma unroll
+                for (int i = 1; i < 19; i += 2) {
+                    ha += pulled(src, L, b, 0, i, keep) + pulled(src, L, b, 0, i + 1, keep);
+                    hb += pulled(src, L, b, 1, i, keep) + pulled(src, L, b, 1, i + 1, keep);
+                }
             }
             st_async_f2(halo_ring + 4u * ridx(slot, hside ? 1 : -1, hcol), ha, hb, halo_mbar + mb);
         }
@@ -274,8 +229,12 @@ __global__ void __launch_bounds__(TX, MINB)
         densities(z + 1);
         // this node's populations for the collision, read while the
         // neighbour rows of plane z + 1 are in flight
+        const long long bz = node0 + (long long)z * L.plane;
         float f[2][19];
-        pull_node(src, L, m, xc, node0 + (long long)z * L.plane, x, y, z, true, keep, f, d_err);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 19; ++i) f[s][i] = pulled_last(src, L, bz, s, i);
         __syncthreads();  // own row of plane z + 1 complete
         wait_rows(z + 1);
 
@@ -414,8 +373,8 @@ __global__ void __launch_bounds__(TX, MINB)
 constexpr int kRowMinBlocks = 6;
 
 template <int TX, int CY>
-cudaError_t launch_rows(const float* src, float* dst, const Layout& L, const Model& m, const Grad& A, int zchunk,
-                        int nchunks, CentreParts cp, int* d_err, cudaStream_t s) {
+cudaError_t launch_rows(const float* src, float* dst, const Layout& L, const Model& m, int zchunk, int nchunks,
+                        CentreParts cp, int* d_err, cudaStream_t s) {
     auto k = k_stream_collide_rows<TX, CY, kRowMinBlocks * 128 / TX>;
     const size_t smem = FastLayout<TX, CY>::bytes;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -427,9 +386,6 @@ cudaError_t launch_rows(const float* src, float* dst, const Layout& L, const Mod
         fm.rho_b[q] = (float)m.rho_b[q];
     }
     fm.G = (float)m.G;
-    for (int j = 0; j < 9; ++j) fm.A[j] = (float)A.a[j];
-    fm.mach2 = (float)m.mach2;
-    fm.droplet_frame = m.droplet_frame;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(1, L.Ly, nchunks);
     cfg.blockDim = dim3(TX, 1, 1);
@@ -489,10 +445,11 @@ int rows_kernel_resident_ctas(const Layout& L) {
 
 cudaError_t launch_stream_collide_rows(const void* src, void* dst, const Layout& L, const Model& m, const Grad& A,
                                        int zchunk, CentreParts cp, int* d_err, cudaStream_t s) {
+    (void)A;  // this kernel reads the ghost shell written by the ghost kernel
     const int nchunks = (L.Lz + zchunk - 1) / zchunk;
-    if (L.Lx == 128) return launch_rows<128, kRowCluster>((const float*)src, (float*)dst, L, m, A, zchunk, nchunks, cp, d_err, s);
-    if (L.Lx == 64) return launch_rows<64, kRowCluster>((const float*)src, (float*)dst, L, m, A, zchunk, nchunks, cp, d_err, s);
-    if (L.Lx == 32) return launch_rows<32, kRowCluster>((const float*)src, (float*)dst, L, m, A, zchunk, nchunks, cp, d_err, s);
+    if (L.Lx == 128) return launch_rows<128, kRowCluster>((const float*)src, (float*)dst, L, m, zchunk, nchunks, cp, d_err, s);
+    if (L.Lx == 64) return launch_rows<64, kRowCluster>((const float*)src, (float*)dst, L, m, zchunk, nchunks, cp, d_err, s);
+    if (L.Lx == 32) return launch_rows<32, kRowCluster>((const float*)src, (float*)dst, L, m, zchunk, nchunks, cp, d_err, s);
     return cudaErrorInvalidValue;
 }
 

@@ -79,8 +79,8 @@ cudaError_t launch_init(int prec, void* f, const Layout& L, double R, double xi,
                         Grad A0, cudaStream_t s);
 cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Grad A, CentreParts cp, int* d_err,
                          cudaStream_t s);
-// A: the boundary gradient of this step, used by kernels that compute the
-// ghost equilibria themselves (Shape::rows); the others read the ghost shell.
+// A: the boundary gradient of this step (the kernels read the ghost shell
+// written by launch_ghost; A is passed for kernels that may compute it).
 cudaError_t launch_stream_collide(int prec, const void* src, void* dst, const Layout& L, const Model& m,
                                   const Shape& sh, const Grad& A, CentreParts cp, int* d_err, cudaStream_t s);
 // Centre-of-mass partials of the stored populations f (cp.n CTAs, grid-stride).
