@@ -37,6 +37,10 @@ def _load():
         lib.orc_equilibrium.argtypes = [ctypes.c_int, ctypes.c_double, _DP]
         lib.orc_set_threads.restype = ctypes.c_int
         lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_storage.restype = ctypes.c_int
+        lib.orc_set_storage.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        lib.orc_round.restype = ctypes.c_double
+        lib.orc_round.argtypes = [ctypes.c_int, ctypes.c_double]
         _lib = lib
     return _lib
 
@@ -44,6 +48,16 @@ def _load():
 def _ptr(a: np.ndarray):
     assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
     return a.ctypes.data_as(_DP)
+
+
+STORAGE = {"exact": 0, "fp16dev": 1, "bf16dev": 2}
+ROUND_FORMATS = {"float32": 0, "binary16": 1, "bfloat16": 2}
+
+
+def round_to(fmt: str, x: float) -> float:
+    """x rounded to nearest-even in ``fmt`` ("float32", "binary16", "bfloat16"):
+    the rounding of the oracle's storage model."""
+    return float(_load().orc_round(ROUND_FORMATS[fmt], float(x)))
 
 
 def set_threads(n: int) -> int:
@@ -97,9 +111,16 @@ class OracleLBM:
     remains fixed ... linear in the distance from the droplet's centre of
     mass"), recomputed from the stored populations before every step;
     ``frame="box"`` measures it from the box centre.
+
+    ``storage`` selects the storage model of ``lbm_oracle.cpp``: "exact"
+    (full precision, the paper's method), or "fp16dev" / "bf16dev": after
+    every state change the populations are replaced by the values 16-bit
+    deviation storage holds (float32 densities, deviations from w_i rho* of
+    the destination node rounded to binary16 / bfloat16, float32 rest
+    population closing each node's mass).
     """
 
-    def __init__(self, box, tau, G, rho_b, periodic=False, frame="droplet"):
+    def __init__(self, box, tau, G, rho_b, periodic=False, frame="droplet", storage="exact"):
         self.box = tuple(int(v) for v in box)
         self.nodes = self.box[0] * self.box[1] * self.box[2]
         self.tau = (float(tau[0]), float(tau[1]))
@@ -113,6 +134,9 @@ class OracleLBM:
         self._h = self._lib.orc_create(
             self.box[0], self.box[1], self.box[2], int(self.periodic),
             self.tau[0], self.tau[1], self.G, self.rho_b[0], self.rho_b[1])
+        self.storage = storage
+        if self._lib.orc_set_storage(self._h, STORAGE[storage]) != 0:
+            raise ValueError(storage)
         self.step_count = 0
 
     def __del__(self):

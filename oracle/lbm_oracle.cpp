@@ -22,6 +22,16 @@
 //   (vi)  BGK relaxation g* = g - (g - g^eq(rho_s, u_s)) / tau_s with
 //         nu = (tau - 1/2)/3 (Eqs. 9, 10).
 //
+// Optional storage model (orc_set_storage): after every state change the
+// populations are replaced by the values that 16-bit deviation storage can
+// hold, so the same oracle states what that storage form of the method
+// computes.  A population streaming from x to x + c_i is kept as the
+// deviation d_i = f*_i - w_i rho*(x + c_i), rounded to binary16 or bfloat16,
+// with rho* the float32 density of the node it streams to (the ghost density
+// outside the box); the rest population holds the remainder of the node's
+// float32 density, rounded to float32.  This is an addition of the library,
+// not of the paper: the paper stores populations at full precision.
+//
 // Build: g++ -O2 -ffp-contract=off -fopenmp -shared -fPIC (see build.py).
 // Loops over nodes run in parallel over z planes; every node's result is
 // independent of the thread count.  The moment and checksum sums are serial
@@ -57,9 +67,26 @@ double equilibrium(int i, double rho, const double u[3]) {
     return rho * weight(i) * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
 }
 
+// x rounded to nearest-even in a binary format with p significant bits and
+// smallest normal exponent emin (gradual underflow below it); the values
+// rounded here are far below every format's largest finite number.
+double round_to_format(double x, int p, int emin) {
+    if (x == 0.0 || !std::isfinite(x)) return x;
+    int e;
+    std::frexp(x, &e);  // |x| = m 2^e, 1/2 <= m < 1: leading bit 2^(e-1)
+    int lead = e - 1;
+    if (lead < emin) lead = emin;
+    const double q = std::ldexp(1.0, lead - (p - 1));  // spacing of the format near x
+    return std::nearbyint(x / q) * q;                   // default mode: ties to even
+}
+double to_float32(double x) { return round_to_format(x, 24, -126); }
+double to_binary16(double x) { return round_to_format(x, 11, -14); }
+double to_bfloat16(double x) { return round_to_format(x, 8, -126); }
+
 struct Oracle {
     int L[3];
     bool periodic;
+    int storage = 0;  // 0 full precision, 1 binary16 deviations, 2 bfloat16 deviations
     double tau[2];
     double G;
     double rho_b[2];
@@ -92,6 +119,45 @@ struct Oracle {
         }
         return rho[(int64_t)s * nodes() + node(x, y, z)];
     }
+
+    // The storage model: replace fpost by what 16-bit deviation storage holds.
+    void apply_storage() {
+        if (storage == 0) return;
+        const int64_t N = nodes();
+        // float32 densities of the stored state (the rest of the state refers to them)
+        std::vector<double> rs((size_t)(2 * N));
+        for (int s = 0; s < 2; ++s)
+            for (int64_t n = 0; n < N; ++n) {
+                double r = 0.0;
+                for (int i = 0; i < 19; ++i) r += fpost[pidx(s, i, n)];
+                rs[(size_t)(s * N + n)] = to_float32(r);
+            }
+        auto dest = [&](int s, int x, int y, int z) {
+            if (periodic) {
+                x = wrap(x, L[0]); y = wrap(y, L[1]); z = wrap(z, L[2]);
+            } else if (!inside(x, y, z)) {
+                return to_float32(rho_b[s]);
+            }
+            return rs[(size_t)(s * N + node(x, y, z))];
+        };
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < L[2]; ++z)
+            for (int y = 0; y < L[1]; ++y)
+                for (int x = 0; x < L[0]; ++x) {
+                    const int64_t n = node(x, y, z);
+                    for (int s = 0; s < 2; ++s) {
+                        double moving = 0.0;
+                        for (int i = 1; i < 19; ++i) {
+                            const double ref = weight(i) * dest(s, x + CX[i], y + CY[i], z + CZ[i]);
+                            const double d = fpost[pidx(s, i, n)] - ref;
+                            const double dq = storage == 1 ? to_binary16(d) : to_bfloat16(d);
+                            fpost[pidx(s, i, n)] = ref + dq;
+                            moving += ref + dq;
+                        }
+                        fpost[pidx(s, 0, n)] = to_float32(rs[(size_t)(s * N + n)] - moving);
+                    }
+                }
+    }
 };
 
 }  // namespace
@@ -117,6 +183,26 @@ void orc_destroy(void* h) { delete (Oracle*)h; }
 void orc_set_populations(void* h, const double* f) {
     Oracle* o = (Oracle*)h;
     std::memcpy(o->fpost.data(), f, o->fpost.size() * sizeof(double));
+    o->apply_storage();
+}
+
+// Storage model: 0 full precision (the default), 1 binary16 deviations,
+// 2 bfloat16 deviations.  Applies to the current state at once.  Returns 0,
+// or -1 for an unknown mode.
+int orc_set_storage(void* h, int mode) {
+    Oracle* o = (Oracle*)h;
+    if (mode < 0 || mode > 2) return -1;
+    o->storage = mode;
+    o->apply_storage();
+    return 0;
+}
+
+// The rounding of the storage model, exported for its tests:
+// format 0 float32, 1 binary16, 2 bfloat16.
+double orc_round(int format, double x) {
+    if (format == 0) return to_float32(x);
+    if (format == 1) return to_binary16(x);
+    return to_bfloat16(x);
 }
 
 void orc_get_populations(void* h, double* f) {
@@ -146,6 +232,7 @@ void orc_init_droplet(void* h, double R, double xi, double rho_hi, double rho_lo
                 for (int s = 0; s < 2; ++s)
                     for (int i = 0; i < 19; ++i) o->fpost[o->pidx(s, i, n)] = equilibrium(i, rho_s[s], u);
             }
+    o->apply_storage();
 }
 
 // One time step with the boundary gradient A (row-major, A[3*a+b] = d_b u_a).
@@ -260,6 +347,7 @@ void orc_step(void* h, const double* A, const double* centre, double* flux_in, d
                     }
                 }
             }
+    o->apply_storage();
 }
 
 // Density and velocity of the stored (post-collision) populations (Eq. 6):
