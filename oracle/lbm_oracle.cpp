@@ -29,8 +29,10 @@
 // deviation d_i = f*_i - w_i rho*(x + c_i), rounded to binary16 or bfloat16,
 // with rho* the float32 density of the node it streams to (the ghost density
 // outside the box); the rest population holds the remainder of the node's
-// float32 density, rounded to float32.  This is an addition of the library,
-// not of the paper: the paper stores populations at full precision.
+// float32 density, rounded to float32.  Ghost populations are held the same
+// way, relative to the density of the fluid node they stream into.  This is
+// an addition of the library, not of the paper: the paper stores populations
+// at full precision.
 //
 // Build: g++ -O2 -ffp-contract=off -fopenmp -shared -fPIC (see build.py).
 // Loops over nodes run in parallel over z planes; every node's result is
@@ -247,6 +249,19 @@ void orc_step(void* h, const double* A, const double* centre, double* flux_in, d
     const int Lx = o->L[0], Ly = o->L[1], Lz = o->L[2];
     const int64_t N = o->nodes();
 
+    // Storage model: ghost populations are held in the same format as the
+    // state, as deviations from w_i rho* of the fluid node they stream into.
+    std::vector<double> rs;
+    if (o->storage) {
+        rs.resize((size_t)(2 * N));
+        for (int s = 0; s < 2; ++s)
+            for (int64_t n = 0; n < N; ++n) {
+                double r = 0.0;
+                for (int i = 0; i < 19; ++i) r += o->fpost[o->pidx(s, i, n)];
+                rs[(size_t)(s * N + n)] = to_float32(r);
+            }
+    }
+
     // (i)+(ii) pull streaming, with ghost equilibria outside the box.
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < Lz; ++z)
@@ -270,6 +285,11 @@ void orc_step(void* h, const double* A, const double* centre, double* flux_in, d
                             for (int a = 0; a < 3; ++a)
                                 u[a] = A[3 * a + 0] * p[0] + A[3 * a + 1] * p[1] + A[3 * a + 2] * p[2];
                             val = equilibrium(i, o->rho_b[s], u);
+                            if (o->storage) {
+                                const double ref = weight(i) * rs[(size_t)(s * N + n)];
+                                const double d = val - ref;
+                                val = ref + (o->storage == 1 ? to_binary16(d) : to_bfloat16(d));
+                            }
                         }
                         o->fstream[o->pidx(s, i, n)] = val;
                     }

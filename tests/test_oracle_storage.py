@@ -15,7 +15,11 @@ not come from the oracle:
   and each node's populations sum to its float32 density;
 * dynamics: in the periodic test mode the model conserves each component's
   mass to float32 rounding, and one step departs from the full-precision
-  oracle by no more than the format's rounding of the deviations.
+  oracle by no more than the format's rounding of the deviations;
+* the rest state (uniform ghost densities exact in float32, A = 0) stays a
+  fixed point with ghost nodes: bit for bit with binary16 deviations (all
+  zero, ghost ones included), and to float32 rounding with bfloat16, whose
+  range holds the float32 residues of the rest population.
 """
 
 import numpy as np
@@ -130,3 +134,27 @@ def test_storage_dynamics(oracle_mod, storage, ulp):
         dv.step()
     m1 = dv.checksums()[0]
     assert np.all(np.abs(m1 - m0) <= 1e-6 * m0)
+
+
+@pytest.mark.parametrize("storage", ["fp16dev", "bf16dev"])
+def test_rest_state_fixed_point_with_ghosts(oracle_mod, storage):
+    box = (7, 6, 5)
+    # ghost densities exact in float32, so the float64 ghost equilibria and
+    # the float32 densities of the state agree exactly
+    rho_b = (2.0 ** -9, 1.0)
+    o = oracle_mod.OracleLBM(box, (1.0, 1.3), 3.5, rho_b, storage=storage)
+    _, w = oracle_mod.lattice()
+    f = np.empty(o.shape)
+    for s in range(2):
+        f[s] = rho_b[s] * w[:, None, None, None]
+    o.set_populations(f)
+    g0 = o.populations()
+    assert np.max(np.abs(g0 - f)) <= 1e-7  # float32 densities
+    for _ in range(5):
+        o.step(np.zeros(9))
+    if storage == "fp16dev":
+        assert np.array_equal(o.populations(), g0)
+    else:
+        # bfloat16 holds residues at the float32 rounding of the rest
+        # population (an ulp of 1/3 is 3e-8)
+        assert np.max(np.abs(o.populations() - g0)) <= 1e-7
