@@ -38,6 +38,9 @@ sys.path.insert(0, ROOT)
 SAMPLE_EVERY = 200  # gradient sampling time of the paper (Sec. 4): D is read every 200 steps
 PROFILE_EVERY = 8  # kernel durations are sampled with CUDA events on every 8th step of the timed region
 BYTES_PER_LUP_FP32 = 2 * 19 * 4 * 2  # read + write of 38 fp32 populations
+# 16-bit deviation storage: per node a float4 {rho*_A, rho*_B, f*_0A, f*_0B}
+# and 36 16-bit deviations, read and written once
+BYTES_PER_LUP_DEV16 = 2 * (16 + 36 * 2)
 
 
 def parse():
@@ -52,6 +55,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-ensemble", action="store_true")
     p.add_argument("--ensemble-steps", type=int, default=200)
+    p.add_argument("--no-precision", action="store_true")
+    p.add_argument("--precision-steps", type=int, default=400)
     return p.parse_args()
 
 
@@ -241,6 +246,64 @@ def ensemble_bench(steps, stream, dev):
     }
 
 
+def precision_bench(steps, stream, dev):
+    """The 256^3, R = 32 precision case: float32 storage against 16-bit
+    deviation storage (binary16, bfloat16) with float32 collision.  Each form
+    runs `steps` timed steps from its own initial state under the same
+    gradient history; reports MLUPS, the stream-collide kernel's bandwidth
+    against its algorithmic bytes, and D and the float64 mass checksum of
+    each form against the float32 run."""
+    import numpy as np
+    import torch
+
+    from paper_2112_09972_gb300 import workloads
+    from paper_2112_09972_gb300.lbm import DropletLBM
+
+    w = workloads.C4_PRECISION
+    box = (w.box,) * 3
+    warm = 20
+    hist = w.gradient_history(steps + warm + 2)
+    peak, peak_kind = measured_peaks()
+    out = {"workload": w.name, "box": w.box, "R": w.R, "timed_steps": steps, "forms": {}}
+    ref = None
+    for prec, bpl in (("fp32", BYTES_PER_LUP_FP32), ("fp16dev", BYTES_PER_LUP_DEV16), ("bf16dev", BYTES_PER_LUP_DEV16)):
+        g = DropletLBM(box, w.R, w.visc, w.G, precision=prec, rho_hi=w.rho_hi, rho_lo=w.rho_lo,
+                       stream=stream.cuda_stream, device=dev)
+        g.set_gradient_table(np.arange(hist.shape[0]), hist)
+        g.step(warm)
+        g.sync()
+        g.profile(PROFILE_EVERY)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.step(steps)
+        b.record(stream)
+        g.sync()
+        ms = a.elapsed_time(b)
+        k_ms, k_n = g.profile_read(0)
+        g.profile(0)
+        D = g.deformation()[0]
+        mass, _ = g.checksums()
+        k_s = k_ms / 1e3 / max(k_n, 1)
+        achieved = bpl * w.nodes / k_s / 1e9
+        e = {"mlups": round(w.nodes * steps / (ms / 1e3) / 1e6, 1),
+             "bytes_per_lup": bpl,
+             "kernel_avg_us": round(k_s * 1e6, 2),
+             "achieved_gbs": round(achieved, 1),
+             "frac": round(achieved / peak, 4),
+             "D": D, "mass": [float(v) for v in mass]}
+        if ref is None:
+            ref = e
+        else:
+            e["rel_D_difference_vs_fp32"] = abs(D - ref["D"]) / max(abs(ref["D"]), 1e-12)
+            e["rel_mass_difference_vs_fp32"] = float(np.max(np.abs(mass - np.array(ref["mass"])) / np.array(ref["mass"])))
+            e["speedup_vs_fp32"] = round(e["mlups"] / ref["mlups"], 3)
+        out["forms"][prec] = e
+        g.close()
+    out["peak"] = peak
+    out["peak_kind"] = peak_kind
+    return out
+
+
 def run_reference(args, w):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -358,6 +421,9 @@ def main():
     ens = None
     if not args.no_ensemble and world == 1:
         ens = ensemble_bench(args.ensemble_steps, stream, dev)
+    prec = None
+    if not args.no_precision and world == 1:
+        prec = precision_bench(args.precision_steps, stream, dev)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -399,6 +465,7 @@ def main():
         "e2e": e2e,
         "cpu_baseline": cb,
         "ensemble": ens,
+        "precision": prec,
         "D_last": samples[-1] if samples else None,
     }
     print(json.dumps(line))

@@ -61,8 +61,21 @@ typedef enum {
 } lbm_status;
 
 typedef enum {
-    LBM_FP64 = 0, /* populations stored and collided in float64 */
-    LBM_FP32 = 1  /* populations stored and collided in float32 */
+    LBM_FP64 = 0,     /* populations stored and collided in float64 */
+    LBM_FP32 = 1,     /* populations stored and collided in float32 */
+    /* 16-bit deviation storage, float32 collision.  Per node and component
+       the post-collision density rho* and the rest population f*_0 are kept
+       in float32; each moving population f*_i (i = 1..18) is kept as the
+       16-bit deviation d_i = f*_i - w_i rho(x + c_i) from the equilibrium
+       weight of the density of the node it streams to (the writer holds that
+       density on chip for the force of Eq. 7, and the reader rebuilds the
+       pulled value from its own rho*).  The rest population closes the mass
+       of the node exactly, so mass is conserved to float32 rounding.  88
+       bytes per node and copy (float64: 608, float32: 304).  Boxes with
+       box[0] in {32, 64, 128, 256} and box[1] a multiple of 8, ghost
+       boundary; other shapes use the generic kernel. */
+    LBM_FP16_DEV = 2, /* deviations in IEEE binary16 */
+    LBM_BF16_DEV = 3  /* deviations in bfloat16 */
 } lbm_precision;
 
 typedef enum {
@@ -110,7 +123,8 @@ void lbm_opts_default(lbm_opts* opts);
  * flow u = A(0) x of the gradient table (zero until lbm_set_gradient).  The
  * ghost densities are rho_b^A = rho_lo and rho_b^B = rho_hi (density ratio 1,
  * Sec. 3).  Device memory: two population buffers of
- * 38 (box[2]+2)(box[1]+2) pitch elements, pitch >= box[0] + 2.
+ * 38 (box[2]+2)(box[1]+2) pitch elements (float64 / float32), pitch >=
+ * box[0] + 2, or 88 (box[2]+2)(box[1]+2) pitch bytes (16-bit deviations).
  * On success *out receives the context; on failure *out is NULL.
  */
 int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[2], double G,
@@ -170,7 +184,11 @@ int lbm_moments(lbm_ctx* ctx, double m[10]);
  */
 int lbm_get_fields(lbm_ctx* ctx, double* rho_A, double* rho_B, double* u);
 
-/* Copy all populations to / from the host (float64, layout above). */
+/* Copy all populations to / from the host (float64, layout above).  With
+ * 16-bit deviation storage the values read back are w_i rho*(x + c_i) + d_i
+ * (the ghost density where x + c_i lies outside the box), and values written
+ * are converted to that form: rho* is their float32 sum, each d_i is rounded
+ * to 16 bits and the rest population closes the node's mass. */
 int lbm_get_populations(lbm_ctx* ctx, double* f);
 int lbm_set_populations(lbm_ctx* ctx, const double* f);
 
@@ -182,7 +200,8 @@ int lbm_get_step(lbm_ctx* ctx, int64_t* step);
 
 /*
  * Checkpoint: lbm_save writes the parameters, the step counter, the gradient
- * table and the populations (float64) with a 64-bit FNV-1a checksum;
+ * table and the populations (float64; the raw device buffer for 16-bit
+ * deviation storage) with a 64-bit FNV-1a checksum;
  * lbm_load restores them into a context created with the same box, precision
  * and boundary mode (LBM_EINVAL otherwise, LBM_EIO for a missing, short or
  * corrupt file).  A resumed run is bit-identical to an uninterrupted one.

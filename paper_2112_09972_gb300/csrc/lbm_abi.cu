@@ -22,8 +22,8 @@ struct lbm_ctx {
     int box[3];
     double R, xi, rho_hi, rho_lo;
     Model model;
-    int prec;       // 0 = fp64, 1 = fp32
-    int elem;       // bytes per stored population
+    int prec;       // lbm_precision: 0 fp64, 1 fp32, 2 / 3 16-bit deviations (fp16 / bf16)
+    int elem;       // bytes per layout element (8, 4, or the 2-byte unit of deviation storage)
     Layout L;
     Shape shape;
     int device, num_sms;
@@ -156,6 +156,14 @@ uint64_t fnv1a(const void* p, size_t n, uint64_t h = 1469598103934665603ULL) {
     return h;
 }
 
+// Doubles of the population block of a checkpoint: the float64 populations,
+// or the raw device buffer for deviation storage (whose float64 round trip
+// would not be bit-exact).
+size_t ckpt_pop_words(const lbm_ctx* c) {
+    if (is_dev(c->prec)) return ((size_t)c->L.total * c->elem + 7) / 8;
+    return 38ull * c->box[0] * c->box[1] * c->box[2];
+}
+
 struct CkptHeader {
     char magic[8];
     int32_t version, box[3], prec, bc;
@@ -203,7 +211,9 @@ int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[
     lbm_opts o;
     lbm_opts_default(&o);
     if (opts) o = *opts;
-    if (o.precision != LBM_FP64 && o.precision != LBM_FP32) return LBM_EINVAL;
+    if (o.precision != LBM_FP64 && o.precision != LBM_FP32 && o.precision != LBM_FP16_DEV &&
+        o.precision != LBM_BF16_DEV)
+        return LBM_EINVAL;
     if (o.bc != LBM_BC_GHOST_LINEAR && o.bc != LBM_BC_PERIODIC_TEST) return LBM_EINVAL;
     if (o.frame != LBM_FRAME_DROPLET && o.frame != LBM_FRAME_BOX) return LBM_EINVAL;
     for (int a = 0; a < 3; ++a)
@@ -240,10 +250,10 @@ int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[
     c->model.periodic = o.bc == LBM_BC_PERIODIC_TEST;
     c->model.mach2 = mach * mach / 3.0;
     c->model.droplet_frame = o.frame == LBM_FRAME_DROPLET;
-    c->prec = o.precision == LBM_FP64 ? 0 : 1;
-    c->elem = c->prec == 0 ? 8 : 4;
-    c->L = make_layout(box[0], box[1], box[2], c->elem);
-    c->shape = choose_shape(c->L, c->elem, o.bc == LBM_BC_PERIODIC_TEST, o.tile_y, o.z_chunk, c->num_sms);
+    c->prec = o.precision;
+    c->elem = elem_bytes_of(c->prec);
+    c->L = make_layout(box[0], box[1], box[2], c->prec);
+    c->shape = choose_shape(c->L, c->prec, o.bc == LBM_BC_PERIODIC_TEST, o.tile_y, o.z_chunk, c->num_sms);
     c->cur = 0;
     c->stream = (cudaStream_t)o.cuda_stream;
     c->own_stream = false;
@@ -399,7 +409,7 @@ int lbm_get_fields(lbm_ctx* c, double* rho_A, double* rho_B, double* u) {
     const size_t N = (size_t)c->box[0] * c->box[1] * c->box[2];
     double* d = nullptr;
     LBM_TRY(cudaMallocAsync(&d, sizeof(double) * 5 * N, c->stream));
-    cudaError_t e = launch_fields(c->prec, c->f[c->cur], c->L, d, d + N, d + 2 * N, c->stream);
+    cudaError_t e = launch_fields(c->prec, c->f[c->cur], c->L, c->model, d, d + N, d + 2 * N, c->stream);
     if (e == cudaSuccess && rho_A) e = cudaMemcpyAsync(rho_A, d, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && rho_B) e = cudaMemcpyAsync(rho_B, d + N, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, d + 2 * N, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->stream);
@@ -415,7 +425,7 @@ int lbm_get_populations(lbm_ctx* c, double* f) {
     const size_t E = 38ull * c->box[0] * c->box[1] * c->box[2];
     double* d = nullptr;
     LBM_TRY(cudaMallocAsync(&d, sizeof(double) * E, c->stream));
-    cudaError_t e = launch_pack(c->prec, c->f[c->cur], c->L, d, c->stream);
+    cudaError_t e = launch_pack(c->prec, c->f[c->cur], c->L, c->model, d, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, sizeof(double) * E, cudaMemcpyDeviceToHost, c->stream);
     cudaFreeAsync(d, c->stream);
     if (e != cudaSuccess) return cuda_status(e);
@@ -429,9 +439,12 @@ int lbm_set_populations(lbm_ctx* c, const double* f) {
     int st = set_device(c);
     if (st) return st;
     double* d = nullptr;
-    LBM_TRY(cudaMallocAsync(&d, sizeof(double) * E, c->stream));
+    // deviation storage needs the float32 densities of all nodes first
+    const size_t scratch = is_dev(c->prec) ? 2 * E / 38 : 0;
+    LBM_TRY(cudaMallocAsync(&d, sizeof(double) * E + sizeof(float) * scratch, c->stream));
     cudaError_t e = cudaMemcpyAsync(d, f, sizeof(double) * E, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = launch_unpack(c->prec, c->f[c->cur], c->L, d, c->stream);
+    if (e == cudaSuccess)
+        e = launch_unpack(c->prec, c->f[c->cur], c->L, c->model, d, scratch ? (float*)(d + E) : nullptr, c->stream);
     if (e == cudaSuccess) e = launch_centre(c->prec, c->f[c->cur], c->L, c->centre, c->stream);
     cudaFreeAsync(d, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -444,7 +457,8 @@ int lbm_checksums(lbm_ctx* c, double mass[2], double mom[3]) {
     if (!c) return LBM_EINVAL;
     int st = set_device(c);
     if (st || (st = lazy_init(c))) return st;
-    LBM_TRY(launch_checksums(c->prec, c->f[c->cur], c->L, c->d_partials, c->red_blocks, c->d_result, c->stream));
+    LBM_TRY(launch_checksums(c->prec, c->f[c->cur], c->L, c->model, c->d_partials, c->red_blocks, c->d_result,
+                             c->stream));
     LBM_TRY(cudaMemcpyAsync(c->h_result, c->d_result, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->stream));
     if ((st = sync_and_check(c))) return st;
     if (mass) memcpy(mass, c->h_result, sizeof(double) * 2);
@@ -460,11 +474,18 @@ int lbm_get_step(lbm_ctx* c, int64_t* step) {
 
 int lbm_save(lbm_ctx* c, const char* path) {
     if (!c || !path) return LBM_EINVAL;
-    const size_t E = 38ull * c->box[0] * c->box[1] * c->box[2];
+    const size_t E = ckpt_pop_words(c);
     std::vector<double> pop;
-    try { pop.resize(E); } catch (...) { return LBM_ENOMEM; }
-    int st = lbm_get_populations(c, pop.data());
-    if (st) return st;
+    try { pop.resize(E, 0.0); } catch (...) { return LBM_ENOMEM; }
+    int st;
+    if (is_dev(c->prec)) {
+        if ((st = set_device(c)) || (st = lazy_init(c))) return st;
+        LBM_TRY(cudaMemcpyAsync(pop.data(), c->f[c->cur], (size_t)c->L.total * c->elem, cudaMemcpyDeviceToHost,
+                                c->stream));
+        if ((st = sync_and_check(c))) return st;
+    } else if ((st = lbm_get_populations(c, pop.data()))) {
+        return st;
+    }
     // the frame origin of the next step is part of the state
     std::vector<double> cparts((size_t)4 * c->centre.n + 8);
     LBM_TRY(cudaMemcpy(cparts.data(), c->centre.p, sizeof(double) * cparts.size(), cudaMemcpyDeviceToHost));
@@ -509,7 +530,7 @@ int lbm_load(lbm_ctx* c, const char* path) {
         fclose(fp);
         return LBM_EIO;
     }
-    const size_t E = 38ull * c->box[0] * c->box[1] * c->box[2];
+    const size_t E = ckpt_pop_words(c);
     if (h.box[0] != c->box[0] || h.box[1] != c->box[1] || h.box[2] != c->box[2] || h.prec != c->prec ||
         h.bc != c->model.periodic || h.npop != (int64_t)E || h.nknots < 0 || h.nknots > (1LL << 32) ||
         h.ncentre < 0 || h.ncentre > (1LL << 30)) {
@@ -549,7 +570,14 @@ int lbm_load(lbm_ctx* c, const char* path) {
     c->model.rho_b[0] = h.rho_b[0]; c->model.rho_b[1] = h.rho_b[1];
     c->kt.swap(kt);
     c->kA.swap(kA);
-    if ((st = lbm_set_populations(c, pop.data()))) return st;
+    if (is_dev(c->prec)) {
+        LBM_TRY(cudaMemcpyAsync(c->f[c->cur], pop.data(), (size_t)c->L.total * c->elem, cudaMemcpyHostToDevice,
+                                c->stream));
+        LBM_TRY(launch_centre(c->prec, c->f[c->cur], c->L, c->centre, c->stream));
+        c->initialised = true;
+    } else if ((st = lbm_set_populations(c, pop.data()))) {
+        return st;
+    }
     // restore the saved frame origin partials when the launch shape matches
     // (otherwise the ones just recomputed from the populations stay)
     if (h.ncentre == c->centre.n)

@@ -382,7 +382,7 @@ int lbm_batch_create(lbm_batch** out, int32_t nbox, const int32_t* boxes, const 
     b->boxes.resize(nbox);
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < nbox && e == cudaSuccess; ++k) {
-        b->boxes[k].L = make_layout(boxes[3 * k], boxes[3 * k + 1], boxes[3 * k + 2], 4);
+        b->boxes[k].L = make_layout(boxes[3 * k], boxes[3 * k + 1], boxes[3 * k + 2], kFP32);
         const size_t bytes = (size_t)b->boxes[k].L.total * sizeof(float);
         for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
             e = cudaMalloc(&b->boxes[k].f[q], bytes);
@@ -649,7 +649,7 @@ int lbm_batch_get_populations(lbm_batch* b, int32_t box, double* f) {
     const size_t E = 38ull * L.Lx * L.Ly * L.Lz;
     double* d = nullptr;
     BATCH_TRY(cudaMallocAsync(&d, sizeof(double) * E, b->stream));
-    cudaError_t e = launch_pack(1, b->boxes[box].f[b->parity], L, d, b->stream);
+    cudaError_t e = launch_pack(kFP32, b->boxes[box].f[b->parity], L, b->model, d, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, sizeof(double) * E, cudaMemcpyDeviceToHost, b->stream);
     cudaFreeAsync(d, b->stream);
     if (e != cudaSuccess) return cuda_status(e);
@@ -668,7 +668,7 @@ int lbm_batch_set_populations(lbm_batch* b, int32_t box, const double* f) {
     double* d = nullptr;
     BATCH_TRY(cudaMallocAsync(&d, sizeof(double) * E, b->stream));
     cudaError_t e = cudaMemcpyAsync(d, f, sizeof(double) * E, cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = launch_unpack(1, b->boxes[box].f[b->parity], L, d, b->stream);
+    if (e == cudaSuccess) e = launch_unpack(kFP32, b->boxes[box].f[b->parity], L, b->model, d, nullptr, b->stream);
     cudaFreeAsync(d, b->stream);
     // refresh every box's frame origin from the stored populations
     if (e == cudaSuccess) {

@@ -1,6 +1,8 @@
 // Row-tiled, cluster-pipelined variant of the fused pull-stream + Shan-Chen
 // force + collision step (Sec. 2, Eqs. 6-10 of Milan et al., arXiv:2112.09972)
-// for boxes whose x extent is one CTA row (Lx = TX in {32, 64, 128}), fp32.
+// for boxes whose x extent is one CTA row (Lx = TX in {32, 64, 128, 256}),
+// with float32 populations or 16-bit deviation storage (lbm_dev.cuh) and
+// float32 arithmetic.
 //
 // Work decomposition.  A CTA of TX threads owns one row y of the box and
 // marches a chunk of z planes; CY consecutive rows form a thread-block
@@ -28,6 +30,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include "lbm_dev.cuh"
 #include "lbm_internal.h"
 #include "lbm_lattice.cuh"
 
@@ -110,10 +113,105 @@ __device__ __forceinline__ float pulled_last(const float* __restrict__ src, cons
     return __ldlu(pulled_ptr(src, L, b, s, i));
 }
 
-template <int TX, int CY, int MINB>
+// 16-bit deviation storage: the word of the deviation pair {A, B} of
+// direction i pulled into the node whose first word (i = 1) has index b, and
+// the node's own float4 block {rho*_A, rho*_B, f*_0A, f*_0B}.
+__device__ __forceinline__ const unsigned* dev_ptr(const unsigned* src, const Layout& L, long long b, int i) {
+    return src + b + (long long)(i - 1) * L.array -
+           ((long long)cz_(i) * (L.plane >> 1) + (long long)cy_(i) * L.pitch + cx_(i));
+}
+__device__ __forceinline__ unsigned ld_keep_u32(const unsigned* p, unsigned long long pol) {
+    unsigned v;
+    asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float4 ld_keep_f4(const float4* p, unsigned long long pol) {
+    float4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
+// Storage-specific reads and writes of the row kernel.  A node is named by
+// its plane-0 indices (NodeIx); plane p adds p planes.
+struct NodeIx {
+    long long a;  // float32: element of (s=0, i=0); deviations: float4 block index
+    long long b;  // deviations: 2-byte index of deviation (s=0, i=1)
+};
+
+template <typename S>
+struct RowIO;
+
+template <>
+struct RowIO<float> {
+    static __device__ __forceinline__ NodeIx node(const Layout& L, int x, int y) { return {L.at(0, 0, x, y, 0), 0}; }
+    // post-streaming densities of the node at plane p (first read, kept in L2)
+    static __device__ __forceinline__ void densities(const float* __restrict__ src, const Layout& L, NodeIx n, int p,
+                                                     unsigned long long keep, float& ra, float& rb) {
+        const long long b = n.a + (long long)p * L.plane;
+        ra = pulled(src, L, b, 0, 0, keep);
+        rb = pulled(src, L, b, 1, 0, keep);
+#pragma unroll
+        for (int i = 1; i < 19; i += 2) {
+            ra += pulled(src, L, b, 0, i, keep) + pulled(src, L, b, 0, i + 1, keep);
+            rb += pulled(src, L, b, 1, i, keep) + pulled(src, L, b, 1, i + 1, keep);
+        }
+    }
+    // the node's 38 pulled populations at plane p (second read, last use)
+    static __device__ __forceinline__ void populations(const float* __restrict__ src, const Layout& L, NodeIx n, int p,
+                                                       float (&f)[2][19]) {
+        const long long b = n.a + (long long)p * L.plane;
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 19; ++i) f[s][i] = pulled_last(src, L, b, s, i);
+    }
+};
+
+template <typename T>
+struct RowIO<Dev<T>> {
+    static __device__ __forceinline__ NodeIx node(const Layout& L, int x, int y) {
+        return {L.dev_node(x, y, 0), L.dev_word(1, x, y, 0)};
+    }
+    static __device__ __forceinline__ void densities(const Dev<T>* __restrict__ src, const Layout& L, NodeIx n, int p,
+                                                     unsigned long long keep, float& ra, float& rb) {
+        const float4 o = ld_keep_f4(reinterpret_cast<const float4*>(src) + n.a + (long long)p * (L.plane >> 3), keep);
+        const unsigned* d = reinterpret_cast<const unsigned*>(src);
+        const long long b = n.b + (long long)p * (L.plane >> 1);
+        // sum_i (w_i rho* + d_i) + f*_0 = f*_0 + (1 - w_0) rho* + sum_i d_i
+        float da = 0.f, db = 0.f;
+#pragma unroll
+        for (int i = 1; i < 19; i += 2) {
+            const float2 u = dev_unpack2<T>(ld_keep_u32(dev_ptr(d, L, b, i), keep));
+            const float2 v = dev_unpack2<T>(ld_keep_u32(dev_ptr(d, L, b, i + 1), keep));
+            da += u.x + v.x;
+            db += u.y + v.y;
+        }
+        ra = o.z + (1.f - wgt<float>(0)) * o.x + da;
+        rb = o.w + (1.f - wgt<float>(0)) * o.y + db;
+    }
+    static __device__ __forceinline__ void populations(const Dev<T>* __restrict__ src, const Layout& L, NodeIx n, int p,
+                                                       float (&f)[2][19]) {
+        const float4 o = __ldlu(reinterpret_cast<const float4*>(src) + n.a + (long long)p * (L.plane >> 3));
+        const unsigned* d = reinterpret_cast<const unsigned*>(src);
+        const long long b = n.b + (long long)p * (L.plane >> 1);
+        f[0][0] = o.z;
+        f[1][0] = o.w;
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            const float2 v = dev_unpack2<T>(__ldlu(dev_ptr(d, L, b, i)));
+            f[0][i] = wgt<float>(i) * o.x + v.x;
+            f[1][i] = wgt<float>(i) * o.y + v.y;
+        }
+    }
+};
+
+template <int TX, int CY, int MINB, typename ST>
 __global__ void __launch_bounds__(TX, MINB)
-    k_stream_collide_rows(const float* __restrict__ src, float* __restrict__ dst, Layout L, FastModel m, int zchunk,
+    k_stream_collide_rows(const ST* __restrict__ src, ST* __restrict__ dst, Layout L, FastModel m, int zchunk,
                           CentreParts cp, int* __restrict__ d_err) {
+    using IO = RowIO<ST>;
     using FL = FastLayout<TX, CY>;
     constexpr int RW = FL::RW, HN = FL::HN, S = FL::S;
     extern __shared__ __align__(16) float ring[];  // [S][3][RW][2], then S mbarriers
@@ -158,8 +256,8 @@ __global__ void __launch_bounds__(TX, MINB)
     }
     cluster.sync();  // barriers initialised before any remote store arrives
 
-    const long long node0 = L.at(0, 0, x, y, 0);      // (s=0, i=0, x, y, z=0)
-    const long long hnode0 = L.at(0, 0, hcol, hin ? hy : 0, 0);
+    const NodeIx node0 = IO::node(L, x, y);
+    const NodeIx hnode0 = IO::node(L, hcol, hin ? hy : 0);
     unsigned long long keep;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
 
@@ -173,32 +271,14 @@ __global__ void __launch_bounds__(TX, MINB)
         const int slot = slot_of(p);
         const bool in = p >= 0 && p < L.Lz;
         float ra = m.rho_b[0], rb = m.rho_b[1];
-        if (in) {
-            const long long b = node0 + (long long)p * L.plane;
-            ra = pulled(src, L, b, 0, 0, keep);
-            rb = pulled(src, L, b, 1, 0, keep);
-#pragma unroll
-            for (int i = 1; i < 19; i += 2) {
-                ra += pulled(src, L, b, 0, i, keep) + pulled(src, L, b, 0, i + 1, keep);
-                rb += pulled(src, L, b, 1, i, keep) + pulled(src, L, b, 1, i + 1, keep);
-            }
-        }
+        if (in) IO::densities(src, L, node0, p, keep, ra, rb);
         *reinterpret_cast<float2*>(ring + ridx(slot, 0, x)) = make_float2(ra, rb);
         const unsigned mb = 8u * slot;
         if (rank > 0) st_async_f2(below_ring + 4u * ridx(slot, 1, x), ra, rb, below_mbar + mb);
         if (rank < CY - 1) st_async_f2(above_ring + 4u * ridx(slot, -1, x), ra, rb, above_mbar + mb);
         if (hthr) {
             float ha = m.rho_b[0], hb = m.rho_b[1];
-            if (in && hin) {
-                const long long b = hnode0 + (long long)p * L.plane;
-                ha = pulled(src, L, b, 0, 0, keep);
-                hb = pulled(src, L, b, 1, 0, keep);
-#pragma unroll
-                for (int i = 1; i < 19; i += 2) {
-                    ha += pulled(src, L, b, 0, i, keep) + pulled(src, L, b, 0, i + 1, keep);
-                    hb += pulled(src, L, b, 1, i, keep) + pulled(src, L, b, 1, i + 1, keep);
-                }
-            }
+            if (in && hin) IO::densities(src, L, hnode0, p, keep, ha, hb);
             st_async_f2(halo_ring + 4u * ridx(slot, hside ? 1 : -1, hcol), ha, hb, halo_mbar + mb);
         }
         if (x == 0) mbar_expect_tx(mbar_s + mb, FL::TX_BYTES);
@@ -229,12 +309,8 @@ __global__ void __launch_bounds__(TX, MINB)
         densities(z + 1);
         // this node's populations for the collision, read while the
         // neighbour rows of plane z + 1 are in flight
-        const long long bz = node0 + (long long)z * L.plane;
         float f[2][19];
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int i = 0; i < 19; ++i) f[s][i] = pulled_last(src, L, bz, s, i);
+        IO::populations(src, L, node0, z, f);
         __syncthreads();  // own row of plane z + 1 complete
         wait_rows(z + 1);
 
@@ -284,34 +360,80 @@ __global__ void __launch_bounds__(TX, MINB)
             cm[2] += w * py;
             cm[3] += w * ((float)z - 0.5f * (float)(L.Lz - 1));
         }
-        const long long b = L.at(0, 0, x, y, z);
+        if constexpr (is_dev_t<ST>::value) {
+            // 16-bit deviations from w_i times the density of the node each
+            // population streams to (this CTA's density planes), the pair of
+            // components of one direction in one word
+            using T = decltype(dev_tag(ST{}));
+            float ux[2], uy[2], uz[2], u2x[2];
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const float sh = -m.G * m.tau[s];  // tau_s F^s / rho_s per unit of the other sum
-            const float ux = up[0] + sh * acc[1 - s][0];
-            const float uy = up[1] + sh * acc[1 - s][1];
-            const float uz = up[2] + sh * acc[1 - s][2];
-            const float u2x = 1.5f * (ux * ux + uy * uy + uz * uz);
-            const float it = m.inv_tau[s];
-            const float r = rho[s];
-            // moving populations; the rest population then closes the mass
-            // balance exactly (sum of outputs = rho), which keeps fp32
-            // rounding from drifting the interface
-            float others = 0.f;
+            for (int s = 0; s < 2; ++s) {
+                const float sh = -m.G * m.tau[s];  // tau_s F^s / rho_s per unit of the other sum
+                ux[s] = up[0] + sh * acc[1 - s][0];
+                uy[s] = up[1] + sh * acc[1 - s][1];
+                uz[s] = up[2] + sh * acc[1 - s][2];
+                u2x[s] = 1.5f * (ux[s] * ux[s] + uy[s] * uy[s] + uz[s] * uz[s]);
+            }
+            unsigned* d = reinterpret_cast<unsigned*>(dst);
+            const long long db = L.dev_word(1, x, y, z);
+            float others[2] = {0.f, 0.f};
 #pragma unroll
             for (int i = 1; i < 19; i += 2) {
-                const float cu = (float)cx_(i) * ux + (float)cy_(i) * uy + (float)cz_(i) * uz;
-                const float rw = r * wgt<float>(i);
-                const float even = rw * (1.f + 4.5f * cu * cu - u2x);
-                const float odd = rw * (3.f * cu);
-                const float fa = f[s][i], fb = f[s][i + 1];
-                const float oa = fa - (fa - (even + odd)) * it;
-                const float ob = fb - (fb - (even - odd)) * it;
-                __stcs(dst + b + (long long)(s * 19 + i) * L.array, oa);
-                __stcs(dst + b + (long long)(s * 19 + i + 1) * L.array, ob);
-                others += oa + ob;
+                float da[2], dbv[2], refa[2], refb[2];
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const float cu = (float)cx_(i) * ux[s] + (float)cy_(i) * uy[s] + (float)cz_(i) * uz[s];
+                    const float rw = rho[s] * wgt<float>(i);
+                    const float even = rw * (1.f + 4.5f * cu * cu - u2x[s]);
+                    const float odd = rw * (3.f * cu);
+                    const float fa = f[s][i], fb = f[s][i + 1];
+                    const float oa = fa - (fa - (even + odd)) * m.inv_tau[s];
+                    const float ob = fb - (fb - (even - odd)) * m.inv_tau[s];
+                    refa[s] = wgt<float>(i) * nb(s, cx_(i), cy_(i), cz_(i));
+                    refb[s] = wgt<float>(i) * nb(s, -cx_(i), -cy_(i), -cz_(i));
+                    da[s] = oa - refa[s];
+                    dbv[s] = ob - refb[s];
+                }
+                const unsigned wa = dev_pack2<T>(da[0], da[1]), wb = dev_pack2<T>(dbv[0], dbv[1]);
+                __stcs(d + db + (long long)(i - 1) * L.array, wa);
+                __stcs(d + db + (long long)i * L.array, wb);
+                // the values the readers will rebuild, for the mass balance
+                const float2 qa = dev_unpack2<T>(wa), qb = dev_unpack2<T>(wb);
+                others[0] += (refa[0] + qa.x) + (refb[0] + qb.x);
+                others[1] += (refa[1] + qa.y) + (refb[1] + qb.y);
             }
-            __stcs(dst + b + (long long)(s * 19) * L.array, r - others);
+            __stcs(reinterpret_cast<float4*>(dst) + L.dev_node(x, y, z),
+                   make_float4(rho[0], rho[1], rho[0] - others[0], rho[1] - others[1]));
+        } else {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const float sh = -m.G * m.tau[s];  // tau_s F^s / rho_s per unit of the other sum
+                const float ux = up[0] + sh * acc[1 - s][0];
+                const float uy = up[1] + sh * acc[1 - s][1];
+                const float uz = up[2] + sh * acc[1 - s][2];
+                const float u2x = 1.5f * (ux * ux + uy * uy + uz * uz);
+                const float it = m.inv_tau[s];
+                const float r = rho[s];
+                // moving populations; the rest population then closes the mass
+                // balance exactly (sum of outputs = rho), which keeps fp32
+                // rounding from drifting the interface
+                const long long b = L.at(s, 0, x, y, z);
+                float others = 0.f;
+#pragma unroll
+                for (int i = 1; i < 19; i += 2) {
+                    const float cu = (float)cx_(i) * ux + (float)cy_(i) * uy + (float)cz_(i) * uz;
+                    const float rw = r * wgt<float>(i);
+                    const float even = rw * (1.f + 4.5f * cu * cu - u2x);
+                    const float odd = rw * (3.f * cu);
+                    const float fa = f[s][i], fb = f[s][i + 1];
+                    const float oa = fa - (fa - (even + odd)) * it;
+                    const float ob = fb - (fb - (even - odd)) * it;
+                    __stcs(dst + b + (long long)i * L.array, oa);
+                    __stcs(dst + b + (long long)(i + 1) * L.array, ob);
+                    others += oa + ob;
+                }
+                __stcs(dst + b, r - others);
+            }
         }
         // Before a later plane reuses this plane's own-row slot, all threads
         // must be done reading it: the __syncthreads of the next iterations
@@ -372,10 +494,16 @@ __global__ void __launch_bounds__(TX, MINB)
 
 constexpr int kRowMinBlocks = 6;
 
-template <int TX, int CY>
-cudaError_t launch_rows(const float* src, float* dst, const Layout& L, const Model& m, int zchunk, int nchunks,
+// Resident CTAs per SM asked of the compiler: 6 x 128 threads.
+template <int TX>
+constexpr int row_min_blocks() {
+    return kRowMinBlocks * 128 / TX;
+}
+
+template <int TX, int CY, typename S>
+cudaError_t launch_rows(const void* src, void* dst, const Layout& L, const Model& m, int zchunk, int nchunks,
                         CentreParts cp, int* d_err, cudaStream_t s) {
-    auto k = k_stream_collide_rows<TX, CY, kRowMinBlocks * 128 / TX>;
+    auto k = k_stream_collide_rows<TX, CY, row_min_blocks<TX>(), S>;
     const size_t smem = FastLayout<TX, CY>::bytes;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -398,12 +526,12 @@ cudaError_t launch_rows(const float* src, float* dst, const Layout& L, const Mod
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, src, dst, L, fm, zchunk, cp, d_err);
+    return cudaLaunchKernelEx(&cfg, k, (const S*)src, (S*)dst, L, fm, zchunk, cp, d_err);
 }
 
-template <int TX, int CY>
+template <int TX, int CY, typename S>
 int max_clusters() {
-    auto k = k_stream_collide_rows<TX, CY, kRowMinBlocks * 128 / TX>;
+    auto k = k_stream_collide_rows<TX, CY, row_min_blocks<TX>(), S>;
     const size_t smem = FastLayout<TX, CY>::bytes;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     cudaLaunchConfig_t cfg = {};
@@ -427,30 +555,56 @@ int max_clusters() {
 
 constexpr int kRowCluster = 8;
 
+template <int TX, typename S>
+cudaError_t rows_for(bool query, const void* src, void* dst, const Layout& L, const Model& m, int zchunk,
+                     CentreParts cp, int* d_err, cudaStream_t s, int* resident) {
+    if (query) {
+        *resident = max_clusters<TX, kRowCluster, S>() * kRowCluster;
+        return cudaSuccess;
+    }
+    const int nchunks = (L.Lz + zchunk - 1) / zchunk;
+    return launch_rows<TX, kRowCluster, S>(src, dst, L, m, zchunk, nchunks, cp, d_err, s);
+}
+
+// Dispatch on the row width and the storage type.
+cudaError_t rows_dispatch(int prec, bool query, const void* src, void* dst, const Layout& L, const Model& m,
+                          int zchunk, CentreParts cp, int* d_err, cudaStream_t s, int* resident) {
+#define LBM_ROWS_TX(TXV)                                                                                   \
+    if (L.Lx == TXV) {                                                                                     \
+        if (prec == kFP32) return rows_for<TXV, float>(query, src, dst, L, m, zchunk, cp, d_err, s, resident); \
+        if (prec == kFP16Dev)                                                                              \
+            return rows_for<TXV, Dev<__half>>(query, src, dst, L, m, zchunk, cp, d_err, s, resident);      \
+        if (prec == kBF16Dev)                                                                              \
+            return rows_for<TXV, Dev<__nv_bfloat16>>(query, src, dst, L, m, zchunk, cp, d_err, s, resident); \
+    }
+    LBM_ROWS_TX(32)
+    LBM_ROWS_TX(64)
+    LBM_ROWS_TX(128)
+    LBM_ROWS_TX(256)
+#undef LBM_ROWS_TX
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
 bool rows_kernel_applies(const Layout& L, int prec, int periodic) {
-    if (prec != 1 || periodic) return false;
-    if (L.Lx != 32 && L.Lx != 64 && L.Lx != 128) return false;
+    if ((prec != kFP32 && !is_dev(prec)) || periodic) return false;
+    if (L.Lx != 32 && L.Lx != 64 && L.Lx != 128 && L.Lx != 256) return false;
     return L.Ly % kRowCluster == 0 && L.Lz >= 2;
 }
 
-int rows_kernel_resident_ctas(const Layout& L) {
+int rows_kernel_resident_ctas(const Layout& L, int prec) {
     int n = 0;
-    if (L.Lx == 128) n = max_clusters<128, kRowCluster>();
-    else if (L.Lx == 64) n = max_clusters<64, kRowCluster>();
-    else if (L.Lx == 32) n = max_clusters<32, kRowCluster>();
-    return n * kRowCluster;
+    Model m = {};
+    CentreParts cp = {};
+    if (rows_dispatch(prec, true, nullptr, nullptr, L, m, 1, cp, nullptr, 0, &n) != cudaSuccess) return 0;
+    return n;
 }
 
-cudaError_t launch_stream_collide_rows(const void* src, void* dst, const Layout& L, const Model& m, const Grad& A,
-                                       int zchunk, CentreParts cp, int* d_err, cudaStream_t s) {
+cudaError_t launch_stream_collide_rows(int prec, const void* src, void* dst, const Layout& L, const Model& m,
+                                       const Grad& A, int zchunk, CentreParts cp, int* d_err, cudaStream_t s) {
     (void)A;  // this kernel reads the ghost shell written by the ghost kernel
-    const int nchunks = (L.Lz + zchunk - 1) / zchunk;
-    if (L.Lx == 128) return launch_rows<128, kRowCluster>((const float*)src, (float*)dst, L, m, zchunk, nchunks, cp, d_err, s);
-    if (L.Lx == 64) return launch_rows<64, kRowCluster>((const float*)src, (float*)dst, L, m, zchunk, nchunks, cp, d_err, s);
-    if (L.Lx == 32) return launch_rows<32, kRowCluster>((const float*)src, (float*)dst, L, m, zchunk, nchunks, cp, d_err, s);
-    return cudaErrorInvalidValue;
+    return rows_dispatch(prec, false, src, dst, L, m, zchunk, cp, d_err, s, nullptr);
 }
 
 }  // namespace lbmgb

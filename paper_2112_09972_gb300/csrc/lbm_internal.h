@@ -21,6 +21,12 @@ namespace lbmgb {
 // all have storage.  x0 puts the first fluid node of every row on a 32-byte
 // boundary, and pitch (a multiple of 32 bytes) keeps every row on that
 // boundary.
+//
+// 16-bit deviation storage uses the same geometry in 2-byte units with
+// plane = 44 * array: per z plane first a float4 block of `array` nodes
+// {rho*_A, rho*_B, f*_0A, f*_0B} (8 units per node), then for each direction
+// i = 1..18 an array of 32-bit words, one per node, holding the deviations
+// of both components {A, B} (see dev_node / dev_word / dev_at).
 struct Layout {
     int Lx, Ly, Lz;
     int x0;           // elements before x = 0 in a row
@@ -32,9 +38,28 @@ struct Layout {
     __host__ __device__ long long at(int s, int i, int x, int y, int z) const {
         return (long long)(z + 1) * plane + (long long)(s * 19 + i) * array + (long long)(y + 1) * pitch + x0 + x;
     }
+    // 16-bit deviation storage: float4 index of node (x, y, z)'s block
+    __host__ __device__ long long dev_node(int x, int y, int z) const {
+        return (long long)(z + 1) * (plane >> 3) + (long long)(y + 1) * pitch + x0 + x;
+    }
+    // 16-bit deviation storage: 32-bit word index of the deviation pair
+    // {A, B} of direction i >= 1 of node (x, y, z)
+    __host__ __device__ long long dev_word(int i, int x, int y, int z) const {
+        return (long long)(z + 1) * (plane >> 1) + (long long)(3 + i) * array + (long long)(y + 1) * pitch + x0 + x;
+    }
+    // 16-bit deviation storage: 2-byte index of deviation (s, i >= 1) of node (x, y, z)
+    __host__ __device__ long long dev_at(int s, int i, int x, int y, int z) const {
+        return 2 * dev_word(i, x, y, z) + s;
+    }
 };
 
-Layout make_layout(int Lx, int Ly, int Lz, int elem_bytes);
+// Precision codes of the kernels (the values of lbm_precision).
+enum { kFP64 = 0, kFP32 = 1, kFP16Dev = 2, kBF16Dev = 3 };
+inline bool is_dev(int prec) { return prec == kFP16Dev || prec == kBF16Dev; }
+// Bytes of one layout element: 8, 4 or 2 (the 16-bit unit of deviation storage).
+inline int elem_bytes_of(int prec) { return prec == kFP64 ? 8 : (prec == kFP32 ? 4 : 2); }
+
+Layout make_layout(int Lx, int Ly, int Lz, int prec);
 
 // Scalars of the model that every kernel needs.
 struct Model {
@@ -74,7 +99,7 @@ struct Shape {
 };
 
 // ---- launchers (lbm_step.cu) ----
-Shape choose_shape(const Layout& L, int elem_bytes, int periodic, int ty_req, int zchunk_req, int num_sms);
+Shape choose_shape(const Layout& L, int prec, int periodic, int ty_req, int zchunk_req, int num_sms);
 cudaError_t launch_init(int prec, void* f, const Layout& L, double R, double xi, double rho_hi, double rho_lo,
                         Grad A0, cudaStream_t s);
 cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Grad A, CentreParts cp, int* d_err,
@@ -86,11 +111,12 @@ cudaError_t launch_stream_collide(int prec, const void* src, void* dst, const La
 // Centre-of-mass partials of the stored populations f (cp.n CTAs, grid-stride).
 cudaError_t launch_centre(int prec, const void* f, const Layout& L, CentreParts cp, cudaStream_t s);
 
-// ---- row-tiled cluster kernel (lbm_fast.cu): fp32, ghost boundary, Lx in {32, 64, 128}, Ly % 8 == 0 ----
+// ---- row-tiled cluster kernel (lbm_fast.cu): fp32 or 16-bit deviations, ghost boundary,
+//      Lx in {32, 64, 128, 256}, Ly % 8 == 0 ----
 bool rows_kernel_applies(const Layout& L, int prec, int periodic);
-int rows_kernel_resident_ctas(const Layout& L);
-cudaError_t launch_stream_collide_rows(const void* src, void* dst, const Layout& L, const Model& m, const Grad& A,
-                                       int zchunk, CentreParts cp, int* d_err, cudaStream_t s);
+int rows_kernel_resident_ctas(const Layout& L, int prec);
+cudaError_t launch_stream_collide_rows(int prec, const void* src, void* dst, const Layout& L, const Model& m,
+                                       const Grad& A, int zchunk, CentreParts cp, int* d_err, cudaStream_t s);
 
 // ---- launchers (lbm_reduce.cu) ----
 // Ten moments of w = max(phi, 0) and the deformation: result[0..9] moments,
@@ -99,11 +125,15 @@ cudaError_t launch_stream_collide_rows(const void* src, void* dst, const Layout&
 int moments_blocks(const Layout& L, int num_sms);
 cudaError_t launch_moments(int prec, const void* f, const Layout& L, double* partials, int nblocks,
                            double* result, cudaStream_t s);
-cudaError_t launch_fields(int prec, const void* f, const Layout& L, double* rho_a, double* rho_b, double* u,
+// m: the ghost densities and boundary mode, which 16-bit deviation storage
+// needs to rebuild the populations that leave the box.
+cudaError_t launch_fields(int prec, const void* f, const Layout& L, const Model& m, double* rho_a, double* rho_b,
+                          double* u, cudaStream_t s);
+cudaError_t launch_checksums(int prec, const void* f, const Layout& L, const Model& m, double* partials,
+                             int nblocks, double* result5, cudaStream_t s);
+cudaError_t launch_pack(int prec, const void* f, const Layout& L, const Model& m, double* out, cudaStream_t s);
+// scratch: 2 N floats (16-bit deviation storage only; may be NULL otherwise)
+cudaError_t launch_unpack(int prec, void* f, const Layout& L, const Model& m, const double* in, float* scratch,
                           cudaStream_t s);
-cudaError_t launch_checksums(int prec, const void* f, const Layout& L, double* partials, int nblocks,
-                             double* result5, cudaStream_t s);
-cudaError_t launch_pack(int prec, const void* f, const Layout& L, double* out, cudaStream_t s);
-cudaError_t launch_unpack(int prec, void* f, const Layout& L, const double* in, cudaStream_t s);
 
 }  // namespace lbmgb

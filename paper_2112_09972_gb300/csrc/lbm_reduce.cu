@@ -10,14 +10,18 @@
 //   k_fields    -- rho_A, rho_B and u of the stored populations (Eq. 6);
 //   k_checksums -- float64 mass of each component and total momentum;
 //   k_pack / k_unpack -- float64 host layout <-> padded device layout.
+// Each reads float64, float32 or 16-bit deviation storage (lbm_dev.cuh); the
+// latter rebuilds the populations it needs from rho* and the deviations.
 //
 // Reductions are deterministic: a fixed grid, a fixed in-block tree and a
 // fixed-order final pass.
 
 #include <cuda_runtime.h>
 
+#include "lbm_dev.cuh"
 #include "lbm_eigen.cuh"
 #include "lbm_internal.h"
+#include "lbm_lattice.cuh"
 
 namespace lbmgb {
 namespace {
@@ -36,6 +40,72 @@ __host__ __device__ __forceinline__ constexpr int qz(int i) {
 }
 
 constexpr int kRedThreads = 256;
+
+// What 16-bit deviation storage needs to rebuild populations that leave the box.
+struct DevRef {
+    float rho_b[2];
+    int periodic;
+};
+
+DevRef dev_ref(const Model& m) {
+    DevRef r;
+    r.rho_b[0] = (float)m.rho_b[0];
+    r.rho_b[1] = (float)m.rho_b[1];
+    r.periodic = m.periodic;
+    return r;
+}
+
+// Post-collision population (s, i) of fluid node (x, y, z).  Deviation
+// storage: i = 0 is the stored rest population, i >= 1 is rebuilt as
+// w_i rho*(x + c_i) + d_i in float32, the arithmetic of the stream-collide
+// kernels (rho_b where x + c_i lies outside the box).
+template <typename S>
+__device__ __forceinline__ double population(const S* __restrict__ f, const Layout& L, const DevRef& r, int s, int i,
+                                             int x, int y, int z) {
+    if constexpr (is_dev_t<S>::value) {
+        using T = decltype(dev_tag(S{}));
+        const float4* nb = reinterpret_cast<const float4*>(f);
+        if (i == 0) {
+            const float4 o = nb[L.dev_node(x, y, z)];
+            return (double)(s ? o.w : o.z);
+        }
+        int xd = x + qx(i), yd = y + qy(i), zd = z + qz(i);
+        float rd = r.rho_b[s];
+        if (r.periodic) {
+            xd = (xd + L.Lx) % L.Lx; yd = (yd + L.Ly) % L.Ly; zd = (zd + L.Lz) % L.Lz;
+        }
+        if (xd >= 0 && xd < L.Lx && yd >= 0 && yd < L.Ly && zd >= 0 && zd < L.Lz) {
+            const float4 o = nb[L.dev_node(xd, yd, zd)];
+            rd = s ? o.y : o.x;
+        }
+        const unsigned short b = reinterpret_cast<const unsigned short*>(f)[L.dev_at(s, i, x, y, z)];
+        return (double)(wgt<float>(i) * rd + dev_to_f<T>(b));
+    } else {
+        (void)r;
+        return (double)f[L.at(s, i, x, y, z)];
+    }
+}
+
+// Component densities of fluid node (x, y, z): the sum of its populations,
+// or rho* of deviation storage (the same value up to float32 rounding).
+template <typename S>
+__device__ __forceinline__ void node_rho(const S* __restrict__ f, const Layout& L, int x, int y, int z, double& ra,
+                                         double& rb) {
+    if constexpr (is_dev_t<S>::value) {
+        const float4 o = reinterpret_cast<const float4*>(f)[L.dev_node(x, y, z)];
+        ra = o.x;
+        rb = o.y;
+    } else {
+        const long long b = L.at(0, 0, x, y, z);
+        ra = 0.0;
+        rb = 0.0;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            ra += (double)f[b + (long long)i * L.array];
+            rb += (double)f[b + (long long)(19 + i) * L.array];
+        }
+    }
+}
 
 // Block-wide sum of K doubles per thread; thread 0 writes them to out[0..K).
 template <int K>
@@ -73,13 +143,8 @@ __global__ void __launch_bounds__(kRedThreads) k_moments(const S* __restrict__ f
     const double cx = 0.5 * (L.Lx - 1), cy = 0.5 * (L.Ly - 1), cz = 0.5 * (L.Lz - 1);
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
-        const long long b = L.at(0, 0, x, y, z);
-        double ra = 0.0, rb = 0.0;
-#pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            ra += (double)f[b + (long long)i * L.array];
-            rb += (double)f[b + (long long)(19 + i) * L.array];
-        }
+        double ra, rb;
+        node_rho(f, L, x, y, z, ra, rb);
         const double phi = (ra - rb) / (ra + rb);
         const double w = phi > 0.0 ? phi : 0.0;
         const double px = x - cx, py = y - cy, pz = z - cz;
@@ -108,19 +173,18 @@ __global__ void k_moments_final(const double* __restrict__ partials, int nblocks
 }
 
 template <typename S>
-__global__ void k_fields(const S* __restrict__ f, Layout L, double* __restrict__ ra_out, double* __restrict__ rb_out,
-                         double* __restrict__ u_out) {
+__global__ void k_fields(const S* __restrict__ f, Layout L, DevRef dr, double* __restrict__ ra_out,
+                         double* __restrict__ rb_out, double* __restrict__ u_out) {
     const long long N = (long long)L.Lx * L.Ly * L.Lz;
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
-    const long long b = L.at(0, 0, x, y, z);
     double r[2] = {0.0, 0.0}, j[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            const double v = (double)f[b + (long long)(s * 19 + i) * L.array];
+            const double v = population(f, L, dr, s, i, x, y, z);
             r[s] += v;
             j[0] += qx(i) * v; j[1] += qy(i) * v; j[2] += qz(i) * v;
         }
@@ -135,17 +199,17 @@ __global__ void k_fields(const S* __restrict__ f, Layout L, double* __restrict__
 }
 
 template <typename S>
-__global__ void __launch_bounds__(kRedThreads) k_checksums(const S* __restrict__ f, Layout L, double* __restrict__ partials) {
+__global__ void __launch_bounds__(kRedThreads) k_checksums(const S* __restrict__ f, Layout L, DevRef dr,
+                                                           double* __restrict__ partials) {
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     const long long N = (long long)L.Lx * L.Ly * L.Lz;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
-        const long long b = L.at(0, 0, x, y, z);
 #pragma unroll
         for (int s = 0; s < 2; ++s)
 #pragma unroll
             for (int i = 0; i < 19; ++i) {
-                const double q = (double)f[b + (long long)(s * 19 + i) * L.array];
+                const double q = population(f, L, dr, s, i, x, y, z);
                 v[s] += q;
                 v[2] += qx(i) * q; v[3] += qy(i) * q; v[4] += qz(i) * q;
             }
@@ -166,14 +230,62 @@ __global__ void k_checksums_final(const double* __restrict__ partials, int nbloc
 }
 
 template <typename S>
-__global__ void k_pack(const S* __restrict__ f, Layout L, double* __restrict__ out) {
+__global__ void k_pack(const S* __restrict__ f, Layout L, DevRef dr, double* __restrict__ out) {
     const long long N = (long long)L.Lx * L.Ly * L.Lz;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= 38 * N) return;
     const int si = (int)(e / N);
     const long long n = e - si * N;
     const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
-    out[e] = (double)f[L.at(si / 19, si % 19, x, y, z)];
+    out[e] = population(f, L, dr, si / 19, si % 19, x, y, z);
+}
+
+// Deviation storage upload, pass 1: rho*_s = float32 of the float64 sum of
+// node n's populations, into rho[s * N + n].
+__global__ void k_unpack_dev_rho(Layout L, const double* __restrict__ in, float* __restrict__ rho) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        double a = 0.0;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) a += in[(long long)(s * 19 + i) * N + n];
+        rho[s * N + n] = (float)a;
+    }
+}
+
+// Pass 2: deviations from w_i rho*(x + c_i), node block with the rest
+// population closing the node's mass (the arithmetic of the kernels).
+template <typename T>
+__global__ void k_unpack_dev(Dev<T>* __restrict__ f, Layout L, DevRef dr, const double* __restrict__ in,
+                             const float* __restrict__ rho) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
+    unsigned short* d = reinterpret_cast<unsigned short*>(f);
+    float rest[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        float others = 0.f;
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            int xd = x + qx(i), yd = y + qy(i), zd = z + qz(i);
+            if (dr.periodic) {
+                xd = (xd + L.Lx) % L.Lx; yd = (yd + L.Ly) % L.Ly; zd = (zd + L.Lz) % L.Lz;
+            }
+            float rd = dr.rho_b[s];
+            if (xd >= 0 && xd < L.Lx && yd >= 0 && yd < L.Ly && zd >= 0 && zd < L.Lz)
+                rd = rho[s * N + ((long long)zd * L.Ly + yd) * L.Lx + xd];
+            const float ref = wgt<float>(i) * rd;
+            const unsigned short b = dev_from_f<T>((float)(in[(long long)(s * 19 + i) * N + n] - (double)ref));
+            d[L.dev_at(s, i, x, y, z)] = b;
+            others += ref + dev_to_f<T>(b);
+        }
+        rest[s] = rho[s * N + n] - others;
+    }
+    reinterpret_cast<float4*>(f)[L.dev_node(x, y, z)] = make_float4(rho[n], rho[N + n], rest[0], rest[1]);
 }
 
 template <typename S>
@@ -198,40 +310,64 @@ int moments_blocks(const Layout& L, int num_sms) {
 
 cudaError_t launch_moments(int prec, const void* f, const Layout& L, double* partials, int nblocks, double* result,
                            cudaStream_t s) {
-    if (prec == 0) k_moments<double><<<nblocks, kRedThreads, 0, s>>>((const double*)f, L, partials);
-    else k_moments<float><<<nblocks, kRedThreads, 0, s>>>((const float*)f, L, partials);
+    if (prec == kFP64) k_moments<double><<<nblocks, kRedThreads, 0, s>>>((const double*)f, L, partials);
+    else if (prec == kFP32) k_moments<float><<<nblocks, kRedThreads, 0, s>>>((const float*)f, L, partials);
+    else if (prec == kFP16Dev) k_moments<Dev<__half>><<<nblocks, kRedThreads, 0, s>>>((const Dev<__half>*)f, L, partials);
+    else k_moments<Dev<__nv_bfloat16>><<<nblocks, kRedThreads, 0, s>>>((const Dev<__nv_bfloat16>*)f, L, partials);
     k_moments_final<<<1, 32, 0, s>>>(partials, nblocks, result);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fields(int prec, const void* f, const Layout& L, double* ra, double* rb, double* u, cudaStream_t s) {
+cudaError_t launch_fields(int prec, const void* f, const Layout& L, const Model& m, double* ra, double* rb, double* u,
+                          cudaStream_t s) {
     const long long N = (long long)L.Lx * L.Ly * L.Lz;
     const unsigned blocks = (unsigned)((N + 255) / 256);
-    if (prec == 0) k_fields<double><<<blocks, 256, 0, s>>>((const double*)f, L, ra, rb, u);
-    else k_fields<float><<<blocks, 256, 0, s>>>((const float*)f, L, ra, rb, u);
+    const DevRef dr = dev_ref(m);
+    if (prec == kFP64) k_fields<double><<<blocks, 256, 0, s>>>((const double*)f, L, dr, ra, rb, u);
+    else if (prec == kFP32) k_fields<float><<<blocks, 256, 0, s>>>((const float*)f, L, dr, ra, rb, u);
+    else if (prec == kFP16Dev) k_fields<Dev<__half>><<<blocks, 256, 0, s>>>((const Dev<__half>*)f, L, dr, ra, rb, u);
+    else k_fields<Dev<__nv_bfloat16>><<<blocks, 256, 0, s>>>((const Dev<__nv_bfloat16>*)f, L, dr, ra, rb, u);
     return cudaGetLastError();
 }
 
-cudaError_t launch_checksums(int prec, const void* f, const Layout& L, double* partials, int nblocks, double* result5,
-                             cudaStream_t s) {
-    if (prec == 0) k_checksums<double><<<nblocks, kRedThreads, 0, s>>>((const double*)f, L, partials);
-    else k_checksums<float><<<nblocks, kRedThreads, 0, s>>>((const float*)f, L, partials);
+cudaError_t launch_checksums(int prec, const void* f, const Layout& L, const Model& m, double* partials, int nblocks,
+                             double* result5, cudaStream_t s) {
+    const DevRef dr = dev_ref(m);
+    if (prec == kFP64) k_checksums<double><<<nblocks, kRedThreads, 0, s>>>((const double*)f, L, dr, partials);
+    else if (prec == kFP32) k_checksums<float><<<nblocks, kRedThreads, 0, s>>>((const float*)f, L, dr, partials);
+    else if (prec == kFP16Dev)
+        k_checksums<Dev<__half>><<<nblocks, kRedThreads, 0, s>>>((const Dev<__half>*)f, L, dr, partials);
+    else k_checksums<Dev<__nv_bfloat16>><<<nblocks, kRedThreads, 0, s>>>((const Dev<__nv_bfloat16>*)f, L, dr, partials);
     k_checksums_final<<<1, 32, 0, s>>>(partials, nblocks, result5);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack(int prec, const void* f, const Layout& L, double* out, cudaStream_t s) {
+cudaError_t launch_pack(int prec, const void* f, const Layout& L, const Model& m, double* out, cudaStream_t s) {
     const long long E = 38LL * L.Lx * L.Ly * L.Lz;
     const unsigned blocks = (unsigned)((E + 255) / 256);
-    if (prec == 0) k_pack<double><<<blocks, 256, 0, s>>>((const double*)f, L, out);
-    else k_pack<float><<<blocks, 256, 0, s>>>((const float*)f, L, out);
+    const DevRef dr = dev_ref(m);
+    if (prec == kFP64) k_pack<double><<<blocks, 256, 0, s>>>((const double*)f, L, dr, out);
+    else if (prec == kFP32) k_pack<float><<<blocks, 256, 0, s>>>((const float*)f, L, dr, out);
+    else if (prec == kFP16Dev) k_pack<Dev<__half>><<<blocks, 256, 0, s>>>((const Dev<__half>*)f, L, dr, out);
+    else k_pack<Dev<__nv_bfloat16>><<<blocks, 256, 0, s>>>((const Dev<__nv_bfloat16>*)f, L, dr, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_unpack(int prec, void* f, const Layout& L, const double* in, cudaStream_t s) {
-    const long long E = 38LL * L.Lx * L.Ly * L.Lz;
+cudaError_t launch_unpack(int prec, void* f, const Layout& L, const Model& m, const double* in, float* scratch,
+                          cudaStream_t s) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    if (is_dev(prec)) {
+        if (!scratch) return cudaErrorInvalidValue;
+        const unsigned blocks = (unsigned)((N + 255) / 256);
+        const DevRef dr = dev_ref(m);
+        k_unpack_dev_rho<<<blocks, 256, 0, s>>>(L, in, scratch);
+        if (prec == kFP16Dev) k_unpack_dev<__half><<<blocks, 256, 0, s>>>((Dev<__half>*)f, L, dr, in, scratch);
+        else k_unpack_dev<__nv_bfloat16><<<blocks, 256, 0, s>>>((Dev<__nv_bfloat16>*)f, L, dr, in, scratch);
+        return cudaGetLastError();
+    }
+    const long long E = 38LL * N;
     const unsigned blocks = (unsigned)((E + 255) / 256);
-    if (prec == 0) k_unpack<double><<<blocks, 256, 0, s>>>((double*)f, L, in);
+    if (prec == kFP64) k_unpack<double><<<blocks, 256, 0, s>>>((double*)f, L, in);
     else k_unpack<float><<<blocks, 256, 0, s>>>((float*)f, L, in);
     return cudaGetLastError();
 }

@@ -60,6 +60,61 @@ __global__ void k_init(S* __restrict__ f, Layout L, double R, double xi, double 
         for (int i = 0; i < 19; ++i) f[L.at(s, i, x, y, z)] = (S)feq<double>(i, rho[s], ux, uy, uz, u2x);
 }
 
+// Initial densities of the tanh droplet at fluid node (x, y, z) (the same
+// arithmetic for a node and for the neighbours that refer to it).
+__device__ __forceinline__ void init_rho(const Layout& L, double R, double xi, double rho_hi, double rho_lo, int x,
+                                         int y, int z, double (&rho)[2]) {
+    const double px = x - 0.5 * (L.Lx - 1), py = y - 0.5 * (L.Ly - 1), pz = z - 0.5 * (L.Lz - 1);
+    const double r = sqrt(px * px + py * py + pz * pz);
+    const double th = tanh((r - R) / xi);
+    rho[0] = rho_lo + (rho_hi - rho_lo) * 0.5 * (1.0 - th);
+    rho[1] = rho_lo + (rho_hi - rho_lo) * 0.5 * (1.0 + th);
+}
+
+// Initial state in 16-bit deviation storage: the same equilibria as k_init,
+// stored as deviations from w_i rho*(x + c_i) (the ghost density rho_b
+// outside the box), the rest population closing each node's mass.
+template <typename T>
+__global__ void k_init_dev(Dev<T>* __restrict__ f, Layout L, double R, double xi, double rho_hi, double rho_lo,
+                           Grad A) {
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    if (n >= N) return;
+    const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
+    const double px = x - 0.5 * (L.Lx - 1), py = y - 0.5 * (L.Ly - 1), pz = z - 0.5 * (L.Lz - 1);
+    double rho[2];
+    init_rho(L, R, xi, rho_hi, rho_lo, x, y, z, rho);
+    const double ux = A.a[0] * px + A.a[1] * py + A.a[2] * pz;
+    const double uy = A.a[3] * px + A.a[4] * py + A.a[5] * pz;
+    const double uz = A.a[6] * px + A.a[7] * py + A.a[8] * pz;
+    const double u2x = 1.5 * (ux * ux + uy * uy + uz * uz);
+    const float rs[2] = {(float)rho[0], (float)rho[1]};
+    const float rb[2] = {(float)rho_lo, (float)rho_hi};
+    unsigned short* d = reinterpret_cast<unsigned short*>(f);
+    float rest[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        float others = 0.f;
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            const int xi_ = x + cx_(i), yi = y + cy_(i), zi = z + cz_(i);
+            float rd = rb[s];
+            if (xi_ >= 0 && xi_ < L.Lx && yi >= 0 && yi < L.Ly && zi >= 0 && zi < L.Lz) {
+                double rn[2];
+                init_rho(L, R, xi, rho_hi, rho_lo, xi_, yi, zi, rn);
+                rd = (float)rn[s];
+            }
+            const float ref = wgt<float>(i) * rd;
+            const float g = (float)feq<double>(i, rho[s], ux, uy, uz, u2x);
+            const unsigned short b = dev_from_f<T>(g - ref);
+            d[L.dev_at(s, i, x, y, z)] = b;
+            others += ref + dev_to_f<T>(b);
+        }
+        rest[s] = rs[s] - others;
+    }
+    reinterpret_cast<float4*>(f)[L.dev_node(x, y, z)] = make_float4(rs[0], rs[1], rest[0], rest[1]);
+}
+
 // ----------------------------------------------------------------------------
 // Ghost nodes (see shell_node for the face enumeration).  Corner nodes stream
 // into no fluid node and write nothing.
@@ -80,7 +135,8 @@ __global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, Mode
     C A[9];
 #pragma unroll
     for (int j = 0; j < 9; ++j) A[j] = (C)G.a[j];
-    ghost_node<S, C>(f, L, m, A, xc, yc, zc, x, y, z, d_err);
+    if constexpr (is_dev_t<S>::value) ghost_node_dev<decltype(dev_tag(S{})), C>(f, L, m, A, xc, yc, zc, x, y, z, d_err);
+    else ghost_node<S, C>(f, L, m, A, xc, yc, zc, x, y, z, d_err);
 }
 
 template <typename S, typename C, bool PER, int MAXT>
@@ -107,12 +163,18 @@ __global__ void __launch_bounds__(256) k_centre(const S* __restrict__ f, Layout 
     const long long N = (long long)L.Lx * L.Ly * L.Lz;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
-        const long long b = L.at(0, 0, x, y, z);
         double ra = 0.0, rb = 0.0;
+        if constexpr (is_dev_t<S>::value) {
+            const float4 nb = reinterpret_cast<const float4*>(f)[L.dev_node(x, y, z)];
+            ra = nb.x;
+            rb = nb.y;
+        } else {
+            const long long b = L.at(0, 0, x, y, z);
 #pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            ra += (double)f[b + (long long)i * L.array];
-            rb += (double)f[b + (long long)(19 + i) * L.array];
+            for (int i = 0; i < 19; ++i) {
+                ra += (double)f[b + (long long)i * L.array];
+                rb += (double)f[b + (long long)(19 + i) * L.array];
+            }
         }
         const double phi = (ra - rb) / (ra + rb);
         const double w = phi > 0.0 ? phi : 0.0;
@@ -157,26 +219,28 @@ constexpr int kMaxThreadsF64 = 256;
 
 }  // namespace
 
-Layout make_layout(int Lx, int Ly, int Lz, int elem_bytes) {
+Layout make_layout(int Lx, int Ly, int Lz, int prec) {
     Layout L;
     L.Lx = Lx; L.Ly = Ly; L.Lz = Lz;
-    const int align = 32 / elem_bytes;  // elements per 32-byte sector
+    const int align = 32 / elem_bytes_of(prec);  // elements per 32-byte sector
     L.x0 = align;
     L.pitch = ((L.x0 + Lx + 1 + align - 1) / align) * align;
     L.ny = Ly + 2;
     L.nz = Lz + 2;
     L.array = (long long)L.ny * L.pitch;
-    L.plane = 38LL * L.array;
+    // 16-bit deviation storage: 8 units of node block + 36 deviations per node
+    // (array is a multiple of 16, so every float4 block stays 16-byte aligned)
+    L.plane = (is_dev(prec) ? 44LL : 38LL) * L.array;
     L.total = (long long)L.nz * L.plane;
     return L;
 }
 
-Shape choose_shape(const Layout& L, int elem_bytes, int periodic, int ty_req, int zchunk_req, int num_sms) {
+Shape choose_shape(const Layout& L, int prec, int periodic, int ty_req, int zchunk_req, int num_sms) {
     Shape sh;
     sh.rows = 0;
-    if (ty_req <= 0 && rows_kernel_applies(L, elem_bytes == 4 ? 1 : 0, periodic)) {
+    if (ty_req <= 0 && rows_kernel_applies(L, prec, periodic)) {
         // one CTA per row
-        const int resident = rows_kernel_resident_ctas(L);
+        const int resident = rows_kernel_resident_ctas(L, prec);
         if (resident > 0) {
             // as many z chunks as fill the resident CTA slots once, but at
             // least ~32 planes per chunk: each chunk re-reads two planes
@@ -196,7 +260,8 @@ Shape choose_shape(const Layout& L, int elem_bytes, int periodic, int ty_req, in
             return sh;
         }
     }
-    const int maxt = elem_bytes == 8 ? kMaxThreadsF64 : kMaxThreadsF32;
+    const int cbytes = prec == kFP64 ? 8 : 4;  // compute type of the density ring
+    const int maxt = prec == kFP64 ? kMaxThreadsF64 : kMaxThreadsF32;
     sh.tx = L.Lx <= maxt ? L.Lx : 128;
     if (sh.tx > maxt) sh.tx = maxt;
     int ty = ty_req > 0 ? ty_req : maxt / sh.tx;
@@ -217,7 +282,7 @@ Shape choose_shape(const Layout& L, int elem_bytes, int periodic, int ty_req, in
     sh.zchunk = zc;
     sh.grid = dim3((L.Lx + sh.tx - 1) / sh.tx, (L.Ly + sh.ty - 1) / sh.ty, (L.Lz + zc - 1) / zc);
     sh.threads = sh.tx * sh.ty;
-    sh.smem = (size_t)4 * 2 * (sh.tx + 2) * (sh.ty + 2) * elem_bytes;
+    sh.smem = (size_t)4 * 2 * (sh.tx + 2) * (sh.ty + 2) * cbytes;
     const size_t red = (size_t)((sh.threads + 31) / 32) * 4 * sizeof(double);
     if (sh.smem < red) sh.smem = red;
     return sh;
@@ -228,8 +293,10 @@ cudaError_t launch_init(int prec, void* f, const Layout& L, double R, double xi,
     const long long N = (long long)L.Lx * L.Ly * L.Lz;
     const int T = 256;
     const unsigned blocks = (unsigned)((N + T - 1) / T);
-    if (prec == 0) k_init<double><<<blocks, T, 0, s>>>((double*)f, L, R, xi, rho_hi, rho_lo, A0);
-    else k_init<float><<<blocks, T, 0, s>>>((float*)f, L, R, xi, rho_hi, rho_lo, A0);
+    if (prec == kFP64) k_init<double><<<blocks, T, 0, s>>>((double*)f, L, R, xi, rho_hi, rho_lo, A0);
+    else if (prec == kFP32) k_init<float><<<blocks, T, 0, s>>>((float*)f, L, R, xi, rho_hi, rho_lo, A0);
+    else if (prec == kFP16Dev) k_init_dev<__half><<<blocks, T, 0, s>>>((Dev<__half>*)f, L, R, xi, rho_hi, rho_lo, A0);
+    else k_init_dev<__nv_bfloat16><<<blocks, T, 0, s>>>((Dev<__nv_bfloat16>*)f, L, R, xi, rho_hi, rho_lo, A0);
     return cudaGetLastError();
 }
 
@@ -239,22 +306,28 @@ cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Gra
     const int slow = (L.Lz + 2 > L.Ly ? L.Lz + 2 : L.Ly);
     const dim3 block(32, 8, 1);
     const dim3 grid((fast + 31) / 32, (slow + 7) / 8, 6);
-    if (prec == 0) k_ghost<double, double><<<grid, block, 0, s>>>((double*)f, L, m, A, cp, d_err);
-    else k_ghost<float, float><<<grid, block, 0, s>>>((float*)f, L, m, A, cp, d_err);
+    if (prec == kFP64) k_ghost<double, double><<<grid, block, 0, s>>>((double*)f, L, m, A, cp, d_err);
+    else if (prec == kFP32) k_ghost<float, float><<<grid, block, 0, s>>>((float*)f, L, m, A, cp, d_err);
+    else if (prec == kFP16Dev) k_ghost<Dev<__half>, float><<<grid, block, 0, s>>>((Dev<__half>*)f, L, m, A, cp, d_err);
+    else k_ghost<Dev<__nv_bfloat16>, float><<<grid, block, 0, s>>>((Dev<__nv_bfloat16>*)f, L, m, A, cp, d_err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_centre(int prec, const void* f, const Layout& L, CentreParts cp, cudaStream_t s) {
-    if (prec == 0) k_centre<double><<<cp.n, 256, 0, s>>>((const double*)f, L, cp);
-    else k_centre<float><<<cp.n, 256, 0, s>>>((const float*)f, L, cp);
+    if (prec == kFP64) k_centre<double><<<cp.n, 256, 0, s>>>((const double*)f, L, cp);
+    else if (prec == kFP32) k_centre<float><<<cp.n, 256, 0, s>>>((const float*)f, L, cp);
+    else if (prec == kFP16Dev) k_centre<Dev<__half>><<<cp.n, 256, 0, s>>>((const Dev<__half>*)f, L, cp);
+    else k_centre<Dev<__nv_bfloat16>><<<cp.n, 256, 0, s>>>((const Dev<__nv_bfloat16>*)f, L, cp);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stream_collide(int prec, const void* src, void* dst, const Layout& L, const Model& m,
                                   const Shape& sh, const Grad& A, CentreParts cp, int* d_err, cudaStream_t s) {
-    if (sh.rows) return launch_stream_collide_rows(src, dst, L, m, A, sh.zchunk, cp, d_err, s);
-    if (prec == 0) return stream_collide_t<double, double, kMaxThreadsF64>(src, dst, L, m, sh, cp, d_err, s);
-    return stream_collide_t<float, float, kMaxThreadsF32>(src, dst, L, m, sh, cp, d_err, s);
+    if (sh.rows) return launch_stream_collide_rows(prec, src, dst, L, m, A, sh.zchunk, cp, d_err, s);
+    if (prec == kFP64) return stream_collide_t<double, double, kMaxThreadsF64>(src, dst, L, m, sh, cp, d_err, s);
+    if (prec == kFP32) return stream_collide_t<float, float, kMaxThreadsF32>(src, dst, L, m, sh, cp, d_err, s);
+    if (prec == kFP16Dev) return stream_collide_t<Dev<__half>, float, kMaxThreadsF32>(src, dst, L, m, sh, cp, d_err, s);
+    return stream_collide_t<Dev<__nv_bfloat16>, float, kMaxThreadsF32>(src, dst, L, m, sh, cp, d_err, s);
 }
 
 }  // namespace lbmgb

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include "lbm_dev.cuh"
 #include "lbm_internal.h"
 #include "lbm_lattice.cuh"
 
@@ -40,6 +41,47 @@ struct Puller {
 
     // Post-streaming densities at (x, y, z), any position: outside the box
     // the ghost density (or the periodic image).
+    __device__ __forceinline__ void rho_at(int x, int y, int z, const ModelC<C>& m, C& ra, C& rb) const {
+        if (PER) {
+            x = wrap(x, L.Lx); y = wrap(y, L.Ly); z = wrap(z, L.Lz);
+        } else if (x < 0 || x >= L.Lx || y < 0 || y >= L.Ly || z < 0 || z >= L.Lz) {
+            ra = m.rho_b[0]; rb = m.rho_b[1];
+            return;
+        }
+        C f[2][19];
+        pull(x, y, z, f);
+        ra = sum19<C>(f[0]);
+        rb = sum19<C>(f[1]);
+    }
+};
+
+// 16-bit deviation storage: the pulled population (s, i >= 1) is rebuilt from
+// the node's own rho* and the deviation stored at x - c_i; the rest
+// population is the node's own f*_0.
+template <typename T, typename C, bool PER>
+struct Puller<Dev<T>, C, PER> {
+    const Dev<T>* __restrict__ src;
+    Layout L;
+
+    // word of the deviation pair of direction i pulled into (x, y, z)
+    __device__ __forceinline__ long long idx(int i, int x, int y, int z) const {
+        if (PER) return L.dev_word(i, wrap(x - cx_(i), L.Lx), wrap(y - cy_(i), L.Ly), wrap(z - cz_(i), L.Lz));
+        return L.dev_word(i, x - cx_(i), y - cy_(i), z - cz_(i));
+    }
+
+    __device__ __forceinline__ void pull(int x, int y, int z, C (&f)[2][19]) const {
+        const float4 nb = __ldg(reinterpret_cast<const float4*>(src) + L.dev_node(x, y, z));
+        f[0][0] = (C)nb.z;
+        f[1][0] = (C)nb.w;
+        const unsigned* d = reinterpret_cast<const unsigned*>(src);
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            const float2 v = dev_unpack2<T>(__ldg(d + idx(i, x, y, z)));
+            f[0][i] = wgt<C>(i) * (C)nb.x + (C)v.x;
+            f[1][i] = wgt<C>(i) * (C)nb.y + (C)v.y;
+        }
+    }
+
     __device__ __forceinline__ void rho_at(int x, int y, int z, const ModelC<C>& m, C& ra, C& rb) const {
         if (PER) {
             x = wrap(x, L.Lx); y = wrap(y, L.Ly); z = wrap(z, L.Lz);
@@ -210,7 +252,7 @@ __device__ __forceinline__ void tile_march(const S* __restrict__ src, S* __restr
                 cm[2] += wphi * pyc;
                 cm[3] += wphi * (C(z) - C(0.5) * C(L.Lz - 1));
             }
-            const long long base = L.at(0, 0, x, y, z);
+            C rest[2];
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 // tau_s F^s / rho_s = -G tau_s * (the other component's sum)
@@ -227,11 +269,29 @@ __device__ __forceinline__ void tile_march(const S* __restrict__ src, S* __restr
                 for (int i = 1; i < 19; ++i) {
                     const C f = fc[s][i];
                     const C g = feq<C>(i, rho[s], ux, uy, uz, u2x);
-                    const S o = (S)(f - (f - g) * m.inv_tau[s]);
-                    dst[base + (long long)(s * 19 + i) * L.array] = o;
-                    others += (C)o;
+                    const C o = f - (f - g) * m.inv_tau[s];
+                    if constexpr (is_dev_t<S>::value) {
+                        // deviation from w_i times the density of the node
+                        // this population streams to (ring plane z + c_iz)
+                        const int sd = cz_(i) == 0 ? s1 : (cz_(i) > 0 ? s2 : s0);
+                        const C ref = wgt<C>(i) * R(sd, s, tx + cx_(i), ty + cy_(i));
+                        const unsigned short b = dev_from_f<decltype(dev_tag(S{}))>((float)(o - ref));
+                        reinterpret_cast<unsigned short*>(dst)[L.dev_at(s, i, x, y, z)] = b;
+                        others += ref + (C)dev_to_f<decltype(dev_tag(S{}))>(b);
+                    } else {
+                        const S os = (S)o;
+                        dst[L.at(s, i, x, y, z)] = os;
+                        others += (C)os;
+                    }
                 }
-                dst[base + (long long)(s * 19) * L.array] = (S)(rho[s] - others);
+                rest[s] = rho[s] - others;
+            }
+            if constexpr (is_dev_t<S>::value) {
+                reinterpret_cast<float4*>(dst)[L.dev_node(x, y, z)] =
+                    make_float4((float)rho[0], (float)rho[1], (float)rest[0], (float)rest[1]);
+            } else {
+                dst[L.at(0, 0, x, y, z)] = (S)rest[0];
+                dst[L.at(1, 0, x, y, z)] = (S)rest[1];
             }
         }
     }
@@ -259,6 +319,39 @@ __device__ __forceinline__ void ghost_node(S* __restrict__ f, const Layout& L, c
         any = true;
 #pragma unroll
         for (int s = 0; s < 2; ++s) f[L.at(s, i, x, y, z)] = (S)feq<C>(i, (C)m.rho_b[s], ux, uy, uz, u2x);
+    }
+    if (any && (double)usq > m.mach2) atomicOr(d_err, 2);
+}
+
+// The same for 16-bit deviation storage: the deviation of each inward ghost
+// population from w_i rho*(y), y = (x, y, z) + c_i the fluid node it streams
+// to (rho* of the state in f).
+template <typename T, typename C>
+__device__ __forceinline__ void ghost_node_dev(Dev<T>* __restrict__ f, const Layout& L, const Model& m,
+                                               const C (&A)[9], C xc, C yc, C zc, int x, int y, int z,
+                                               int* __restrict__ d_err) {
+    const C px = (C(x) - C(0.5) * C(L.Lx - 1)) - xc, py = (C(y) - C(0.5) * C(L.Ly - 1)) - yc,
+            pz = (C(z) - C(0.5) * C(L.Lz - 1)) - zc;
+    const C ux = A[0] * px + A[1] * py + A[2] * pz;
+    const C uy = A[3] * px + A[4] * py + A[5] * pz;
+    const C uz = A[6] * px + A[7] * py + A[8] * pz;
+    const C usq = ux * ux + uy * uy + uz * uz;
+    const C u2x = C(1.5) * usq;
+    const float4* nb = reinterpret_cast<const float4*>(f);
+    unsigned short* d = reinterpret_cast<unsigned short*>(f);
+    bool any = false;
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        const int xi = x + cx_(i), yi = y + cy_(i), zi = z + cz_(i);
+        if (xi < 0 || xi >= L.Lx || yi < 0 || yi >= L.Ly || zi < 0 || zi >= L.Lz) continue;
+        any = true;
+        const float4 r = nb[L.dev_node(xi, yi, zi)];
+        const C rs[2] = {(C)r.x, (C)r.y};
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const C g = feq<C>(i, (C)m.rho_b[s], ux, uy, uz, u2x);
+            d[L.dev_at(s, i, x, y, z)] = dev_from_f<T>((float)(g - wgt<C>(i) * rs[s]));
+        }
     }
     if (any && (double)usq > m.mach2) atomicOr(d_err, 2);
 }

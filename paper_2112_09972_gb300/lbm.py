@@ -17,11 +17,12 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "liblbm_gb300.so")
 
-LBM_FP64, LBM_FP32 = 0, 1
+LBM_FP64, LBM_FP32, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2, 3
 LBM_BC_GHOST_LINEAR, LBM_BC_PERIODIC_TEST = 0, 1
 LBM_FRAME_DROPLET, LBM_FRAME_BOX = 0, 1
 FRAMES = {"droplet": LBM_FRAME_DROPLET, "box": LBM_FRAME_BOX}
-PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32}
+# "fp16dev" / "bf16dev": 16-bit deviation storage with float32 collision (lbm.h)
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16dev": LBM_FP16_DEV, "bf16dev": LBM_BF16_DEV}
 
 # Every function the header declares, for the export check.
 ABI_FUNCTIONS = [
@@ -161,7 +162,8 @@ class DropletLBM:
     """A droplet box behind the C ABI.
 
     ``box`` is (Lx, Ly, Lz) or an int; ``visc`` (nu_A, nu_B) in lattice units;
-    ``precision`` "fp32" or "fp64"; ``periodic`` selects the periodic test
+    ``precision`` "fp32", "fp64", "fp16dev" or "bf16dev" (16-bit deviation
+    storage, float32 collision); ``periodic`` selects the periodic test
     mode instead of the ghost-node boundary; ``frame`` "droplet" (the ghost
     flow is linear in the distance from the droplet's centre of mass) or "box".
     """

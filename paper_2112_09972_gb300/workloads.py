@@ -95,7 +95,19 @@ C1_PARITY = Workload("droplet32_R6_shear_Ca0.1", box=32, R=6.0, steps=2000, prec
 C2_THROUGHPUT = Workload("droplet128_R16_ou", box=128, R=16.0, steps=20000, precision="fp32",
                          driving="ou_eq15", seed=12346, T_corr=2000.0, u_lbm=0.1)
 
-WORKLOADS = {w.name: w for w in (C1_PARITY, C2_THROUGHPUT)}
+# 256^3 box, R = 32, 16-bit deviation storage (fp16 and bf16) with fp32
+# collision, the OU history of the throughput case (its own seed), 20000
+# steps.  Its reference runs are the FP64 oracle on the same problem scaled
+# to 64^3 (R = 8) and the full box in fp32 on the GPU.
+C4_PRECISION = Workload("droplet256_R32_ou_dev16", box=256, R=32.0, steps=20000, precision="fp16dev",
+                        driving="ou_eq15", seed=12348, T_corr=2000.0, u_lbm=0.1)
+
+# The 64^3, R = 8 downscale of C4_PRECISION (same seed and u_LBM) that the
+# oracle runs.
+C4_DOWNSCALED = Workload("droplet64_R8_ou_dev16", box=64, R=8.0, steps=20000, precision="fp16dev",
+                         driving="ou_eq15", seed=12348, T_corr=2000.0, u_lbm=0.1)
+
+WORKLOADS = {w.name: w for w in (C1_PARITY, C2_THROUGHPUT, C4_PRECISION, C4_DOWNSCALED)}
 
 
 @dataclass
