@@ -95,19 +95,29 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_traffic(workload):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged since."""
+# Sources that define the row kernel and its launch shape: a committed DRAM
+# traffic figure holds only while these are unchanged.
+ROW_KERNEL_SOURCES = ("lbm_fast.cu", "lbm_lattice.cuh", "lbm_internal.h", "lbm_dev.cuh", "lbm_step.cu")
+
+
+def row_kernel_sha1():
+    h = hashlib.sha1()
+    for name in ROW_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2112_09972_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def kernel_traffic(key):
+    """DRAM bytes per launch of the row kernel from profiles/traffic.json
+    (an ncu capture), if its sources are unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         d = json.load(fh)
-    h = hashlib.sha1()
-    for name in ("lbm_fast.cu", "lbm_lattice.cuh", "lbm_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_2112_09972_gb300", "csrc", name), "rb").read())
-    sha = h.hexdigest()
-    e = d.get(workload)
-    if not e or e.get("source_sha1") != sha:
+    e = d.get(key)
+    if not e or e.get("source_sha1") != row_kernel_sha1():
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -290,6 +300,7 @@ def precision_bench(steps, stream, dev):
              "kernel_avg_us": round(k_s * 1e6, 2),
              "achieved_gbs": round(achieved, 1),
              "frac": round(achieved / peak, 4),
+             "traffic": kernel_traffic(f"{w.name}/{prec}"),
              "D": D, "mass": [float(v) for v in mass]}
         if ref is None:
             ref = e

@@ -242,11 +242,16 @@ Shape choose_shape(const Layout& L, int prec, int periodic, int ty_req, int zchu
         // one CTA per row
         const int resident = rows_kernel_resident_ctas(L, prec);
         if (resident > 0) {
-            // as many z chunks as fill the resident CTA slots once, but at
-            // least ~32 planes per chunk: each chunk re-reads two planes
-            int chunks = resident / L.Ly;
-            const int by_depth = (L.Lz + 31) / 32;
-            if (chunks > by_depth) chunks = by_depth;
+            // Chunks of about 32 planes (each chunk re-reads two planes) when
+            // that gives at least half as many CTAs as fit on the GPU at
+            // once; measured on GB300, more and shorter chunks do not make
+            // the kernel faster at 128^3 and 256^3.  Small boxes take more
+            // chunks (down to 8 planes) to reach the resident CTA count.
+            int chunks = (L.Lz + 31) / 32;
+            if (2 * chunks * L.Ly < resident) {
+                chunks = resident / L.Ly;
+                if (chunks > L.Lz / 8) chunks = L.Lz / 8;
+            }
             if (zchunk_req > 0) chunks = (L.Lz + zchunk_req - 1) / zchunk_req;
             if (chunks < 1) chunks = 1;
             if (chunks > L.Lz) chunks = L.Lz;

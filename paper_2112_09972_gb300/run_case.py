@@ -1,0 +1,43 @@
+"""Run a named workload for a few steps through the C ABI (for profiling runs).
+
+    python -m paper_2112_09972_gb300.run_case --workload droplet128_R16_ou --steps 10
+    python -m paper_2112_09972_gb300.run_case --workload droplet256_R32_ou_dev16 --precision fp16dev
+
+Builds the library if needed, creates the box with the workload's radius and
+fluid parameters, loads its gradient history and takes ``--steps`` steps
+(ghost kernel + stream-collide kernel each), then prints D.  Each step
+launches the same kernels as the benchmark, so a profiler can select one
+launch of a kernel by name and launch count.
+"""
+
+import argparse
+
+import numpy as np
+
+from . import build, workloads
+from .lbm import DropletLBM
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--workload", default=workloads.C2_THROUGHPUT.name, choices=sorted(workloads.WORKLOADS))
+    p.add_argument("--precision", default=None, help="fp64, fp32, fp16dev or bf16dev (default: the workload's)")
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--tile-y", type=int, default=0)
+    p.add_argument("--z-chunk", type=int, default=0)
+    a = p.parse_args(argv)
+    w = workloads.WORKLOADS[a.workload]
+    build.build()
+    prec = a.precision or w.precision
+    g = DropletLBM((w.box,) * 3, w.R, w.visc, w.G, precision=prec, rho_hi=w.rho_hi, rho_lo=w.rho_lo, xi=w.xi,
+                   tile_y=a.tile_y, z_chunk=a.z_chunk)
+    hist = w.gradient_history(max(a.steps, 1))
+    g.set_gradient_table(np.arange(hist.shape[0]), hist)
+    g.step(a.steps)
+    D = g.deformation()[0]
+    ty, zc, ctas = g.launch_shape()
+    print(f"{w.name} {prec}: {a.steps} steps, D = {D:.6f}, launch shape tile_y={ty} z_chunk={zc} ctas={ctas}")
+
+
+if __name__ == "__main__":
+    main()
