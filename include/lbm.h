@@ -292,6 +292,12 @@ int lbm_batch_sync(lbm_batch* batch);
  */
 int lbm_batch_deformation(lbm_batch* batch, double* D, double* axes, double* centre);
 
+/*
+ * The ten float64 moments of w = max(phi, 0) of every box (as lbm_moments):
+ * m[10k .. 10k+9] for box k, coordinates from the box's centre.  Synchronises.
+ */
+int lbm_batch_moments(lbm_batch* batch, double* m);
+
 /* Populations of one box to / from the host (float64, lbm_get_populations layout). */
 int lbm_batch_get_populations(lbm_batch* batch, int32_t box, double* f);
 int lbm_batch_set_populations(lbm_batch* batch, int32_t box, const double* f);
@@ -316,6 +322,66 @@ void lbm_destroy(lbm_ctx* ctx);
 
 /* Static description of a status code. */
 const char* lbm_strerror(int code);
+
+/* ---------------------------------------------------------------------------
+ * Learned surrogate (an addition of this library; the paper compares the
+ * LBM droplet with the Maffettone-Minale model of Sec. 2, Eqs. 1, 2, 5, and
+ * names statistics over many trajectories as its next step, Sec. 6): a
+ * multilayer perceptron that maps a window of the velocity gradient A(t) to
+ * the droplet's conformation tensor M = I / det(I)^(1/3), I the central
+ * second-moment tensor of Eq. 4 (M = identity for a sphere).
+ *
+ * Layers z_l = h_{l-1} W_l^T + b_l, h_l = max(z_l, 0) for l < L, output layer
+ * linear.  Inputs are normalised as (x - x_mean) x_scale and outputs returned
+ * as y_hat / y_scale + y_mean.  Training minimises the mean over samples and
+ * outputs of (y_hat - (t - y_mean) y_scale)^2 with Adam (beta 0.9, 0.999,
+ * eps 1e-8).  Matrix products run on bfloat16 tensor cores with float32
+ * accumulation; inputs, weights, hidden activations and back-propagated
+ * gradients are stored in bfloat16, parameters and Adam moments in float32.
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_mlp lbm_mlp; /* opaque */
+
+/*
+ * sizes[0 .. nlayers]: input width, hidden widths (all multiples of 32, at
+ * most 8192) and output width (1 .. 32).  max_batch (a multiple of 32, at
+ * most 2^22) bounds the samples of one training step and the chunk of a
+ * forward pass.  Weights start He-normal from seed (std::mt19937_64), biases
+ * at zero; normalisation starts as the identity.  cuda_stream NULL: the
+ * network creates its own stream; device < 0: the current device.
+ */
+int lbm_mlp_create(lbm_mlp** out, int32_t nlayers, const int32_t* sizes, int32_t max_batch, uint64_t seed,
+                   void* cuda_stream, int32_t device);
+
+/* Input (sizes[0] entries each) and output (sizes[nlayers] entries, scale != 0) normalisation. */
+int lbm_mlp_set_normalisation(lbm_mlp* mlp, const float* x_mean, const float* x_scale, const float* y_mean,
+                              const float* y_scale);
+
+/* Number of parameters and their flat host layout: W_1 [sizes[1], sizes[0]]
+ * row-major, b_1 [sizes[1]], W_2, b_2, ...  set_params resets Adam. */
+int lbm_mlp_param_count(lbm_mlp* mlp, int64_t* n);
+int lbm_mlp_get_params(lbm_mlp* mlp, float* params);
+int lbm_mlp_set_params(lbm_mlp* mlp, const float* params);
+
+/* Outputs y [n, sizes[nlayers]] (device, float32) of inputs x [n, sizes[0]]
+ * (device, float32), any n >= 0 (processed in chunks of max_batch).  Async. */
+int lbm_mlp_forward(lbm_mlp* mlp, const float* x, float* y, int64_t n);
+
+/* For a network with 6 outputs read as M (xx, xy, xz, yy, yz, zz): the
+ * outputs into m6 [n, 6] and D of Eq. 4 of each predicted M into D [n]
+ * (device float64).  Async. */
+int lbm_mlp_deformation(lbm_mlp* mlp, const float* x, int64_t n, float* m6, double* D);
+
+/* Loss and gradients of n samples (32 <= n <= max_batch, n % 32 == 0;
+ * x, t device float32) without updating: *loss (host, may be NULL) and grads
+ * (host, the flat parameter layout, may be NULL).  Synchronises. */
+int lbm_mlp_gradients(lbm_mlp* mlp, const float* x, const float* t, int64_t n, double* loss, float* grads);
+
+/* One Adam step with learning rate lr on n samples (as lbm_mlp_gradients);
+ * loss (host) NULL keeps the call asynchronous. */
+int lbm_mlp_train_step(lbm_mlp* mlp, const float* x, const float* t, int64_t n, float lr, double* loss);
+
+int lbm_mlp_sync(lbm_mlp* mlp);
+void lbm_mlp_destroy(lbm_mlp* mlp);
 
 #ifdef __cplusplus
 }

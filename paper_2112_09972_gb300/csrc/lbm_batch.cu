@@ -640,6 +640,21 @@ int lbm_batch_deformation(lbm_batch* b, double* D, double* axes, double* centre)
     return LBM_OK;
 }
 
+int lbm_batch_moments(lbm_batch* b, double* m) {
+    if (!b || !m) return LBM_EINVAL;
+    cudaSetDevice(b->device);
+    int st = batch_init(b);
+    if (st) return st;
+    k_batch_moments<<<dim3(b->mblocks, b->nbox), 256, 0, b->stream>>>(b->d_boxes, b->parity, b->d_mparts);
+    k_batch_moments_final<<<b->nbox, 32, 0, b->stream>>>(b->d_mparts, b->mblocks, b->d_result, nullptr);
+    BATCH_TRY(cudaGetLastError());
+    BATCH_TRY(cudaMemcpyAsync(b->h_result, b->d_result, sizeof(double) * 26 * b->nbox, cudaMemcpyDeviceToHost,
+                              b->stream));
+    if ((st = batch_sync(b))) return st;
+    for (int k = 0; k < b->nbox; ++k) memcpy(m + 10 * k, b->h_result + 26 * k, sizeof(double) * 10);
+    return LBM_OK;
+}
+
 int lbm_batch_get_populations(lbm_batch* b, int32_t box, double* f) {
     if (!b || !f || box < 0 || box >= b->nbox) return LBM_EINVAL;
     cudaSetDevice(b->device);

@@ -32,7 +32,10 @@ ABI_FUNCTIONS = [
     "lbm_launch_shape", "lbm_destroy", "lbm_strerror", "lbm_moments_static",
     "lbm_batch_create", "lbm_batch_set_gradients", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_deformation",
     "lbm_batch_get_populations", "lbm_batch_set_populations", "lbm_batch_autotune", "lbm_batch_shape",
-    "lbm_batch_destroy",
+    "lbm_batch_destroy", "lbm_batch_moments",
+    "lbm_mlp_create", "lbm_mlp_set_normalisation", "lbm_mlp_param_count", "lbm_mlp_get_params",
+    "lbm_mlp_set_params", "lbm_mlp_forward", "lbm_mlp_deformation", "lbm_mlp_gradients", "lbm_mlp_train_step",
+    "lbm_mlp_sync", "lbm_mlp_destroy",
 ]
 
 
@@ -60,6 +63,7 @@ class LBMError(RuntimeError):
 
 _lib = None
 _DP = ctypes.POINTER(ctypes.c_double)
+_FP = ctypes.POINTER(ctypes.c_float)
 _I64P = ctypes.POINTER(ctypes.c_int64)
 _I32P = ctypes.POINTER(ctypes.c_int32)
 
@@ -107,6 +111,19 @@ def load_library(path=LIB_PATH):
         "lbm_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int32, _I32P, _I32P]),
         "lbm_batch_shape": (ctypes.c_int, [vp, _I32P, _I32P, _I32P]),
         "lbm_batch_destroy": (None, [vp]),
+        "lbm_batch_moments": (ctypes.c_int, [vp, _DP]),
+        "lbm_mlp_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int32, _I32P, ctypes.c_int32, ctypes.c_uint64,
+                                          vp, ctypes.c_int32]),
+        "lbm_mlp_set_normalisation": (ctypes.c_int, [vp, _FP, _FP, _FP, _FP]),
+        "lbm_mlp_param_count": (ctypes.c_int, [vp, _I64P]),
+        "lbm_mlp_get_params": (ctypes.c_int, [vp, _FP]),
+        "lbm_mlp_set_params": (ctypes.c_int, [vp, _FP]),
+        "lbm_mlp_forward": (ctypes.c_int, [vp, vp, vp, ctypes.c_int64]),
+        "lbm_mlp_deformation": (ctypes.c_int, [vp, vp, ctypes.c_int64, vp, vp]),
+        "lbm_mlp_gradients": (ctypes.c_int, [vp, vp, vp, ctypes.c_int64, _DP, _FP]),
+        "lbm_mlp_train_step": (ctypes.c_int, [vp, vp, vp, ctypes.c_int64, ctypes.c_float, _DP]),
+        "lbm_mlp_sync": (ctypes.c_int, [vp]),
+        "lbm_mlp_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -365,6 +382,12 @@ class BatchLBM:
         f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(self.shape_of(k)))
         _check(self._lib.lbm_batch_set_populations(self._h, int(k), _dptr(f)), "lbm_batch_set_populations")
 
+    def moments(self):
+        """The ten moments of every box, [nbox, 10] (see lbm_moments)."""
+        m = np.zeros(10 * self.nbox)
+        _check(self._lib.lbm_batch_moments(self._h, _dptr(m)), "lbm_batch_moments")
+        return m.reshape(self.nbox, 10)
+
     def autotune(self, trial_steps=4):
         zc, per = ctypes.c_int32(), ctypes.c_int32()
         _check(self._lib.lbm_batch_autotune(self._h, int(trial_steps), ctypes.byref(zc), ctypes.byref(per)),
@@ -376,3 +399,87 @@ class BatchLBM:
         _check(self._lib.lbm_batch_shape(self._h, ctypes.byref(zc), ctypes.byref(ctas), ctypes.byref(items)),
                "lbm_batch_shape")
         return zc.value, ctas.value, items.value
+
+
+def _fptr(a):
+    assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_FP)
+
+
+class MLP:
+    """The surrogate's multilayer perceptron behind the C ABI (lbm_mlp_*).
+
+    Device arrays are torch CUDA tensors (float32, contiguous) passed by
+    address; host arrays are numpy.  ``sizes`` = (d0, hidden..., dL).  The
+    network's kernels run on ``stream`` (a cudaStream_t handle; None: torch's
+    current stream, and the library's own stream when that is the default
+    stream): tensors passed in must be ready on that stream.
+    """
+
+    def __init__(self, sizes, max_batch=4096, seed=0, stream=None, device=-1):
+        lib = load_library()
+        self._lib = lib
+        self.sizes = tuple(int(v) for v in sizes)
+        if stream is None:
+            stream = current_torch_stream()
+        arr = (ctypes.c_int32 * len(self.sizes))(*self.sizes)
+        h = ctypes.c_void_p()
+        _check(lib.lbm_mlp_create(ctypes.byref(h), len(self.sizes) - 1, arr, int(max_batch), int(seed), stream,
+                                  int(device)), "lbm_mlp_create")
+        self._h = h
+        self.max_batch = int(max_batch)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_normalisation(self, x_mean, x_scale, y_mean, y_scale):
+        a = [np.ascontiguousarray(np.asarray(v, dtype=np.float32)) for v in (x_mean, x_scale, y_mean, y_scale)]
+        _check(self._lib.lbm_mlp_set_normalisation(self._h, *[_fptr(v) for v in a]), "lbm_mlp_set_normalisation")
+
+    def param_count(self):
+        n = ctypes.c_int64()
+        _check(self._lib.lbm_mlp_param_count(self._h, ctypes.byref(n)), "lbm_mlp_param_count")
+        return n.value
+
+    def get_params(self):
+        p = np.zeros(self.param_count(), dtype=np.float32)
+        _check(self._lib.lbm_mlp_get_params(self._h, _fptr(p)), "lbm_mlp_get_params")
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        _check(self._lib.lbm_mlp_set_params(self._h, _fptr(p)), "lbm_mlp_set_params")
+
+    def forward(self, x, y):
+        """y[n, dL] = network(x[n, d0]) (torch CUDA float32 tensors; async)."""
+        _check(self._lib.lbm_mlp_forward(self._h, x.data_ptr(), y.data_ptr(), int(x.shape[0])), "lbm_mlp_forward")
+
+    def deformation(self, x, m6, D):
+        """m6[n, 6] and D[n] (float64) of predicted conformation tensors (async)."""
+        _check(self._lib.lbm_mlp_deformation(self._h, x.data_ptr(), int(x.shape[0]), m6.data_ptr(), D.data_ptr()),
+               "lbm_mlp_deformation")
+
+    def gradients(self, x, t):
+        """(loss, flat gradients) of a batch, without an update."""
+        loss = np.zeros(1)
+        g = np.zeros(self.param_count(), dtype=np.float32)
+        _check(self._lib.lbm_mlp_gradients(self._h, x.data_ptr(), t.data_ptr(), int(x.shape[0]), _dptr(loss),
+                                           _fptr(g)), "lbm_mlp_gradients")
+        return float(loss[0]), g
+
+    def train_step(self, x, t, lr, want_loss=False):
+        loss = np.zeros(1) if want_loss else None
+        _check(self._lib.lbm_mlp_train_step(self._h, x.data_ptr(), t.data_ptr(), int(x.shape[0]), ctypes.c_float(lr),
+                                            _dptr(loss)), "lbm_mlp_train_step")
+        return float(loss[0]) if want_loss else None
+
+    def sync(self):
+        _check(self._lib.lbm_mlp_sync(self._h), "lbm_mlp_sync")
