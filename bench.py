@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-ensemble", action="store_true")
     p.add_argument("--ensemble-steps", type=int, default=200)
     p.add_argument("--no-precision", action="store_true")
+    p.add_argument("--no-surrogate", action="store_true")
     p.add_argument("--precision-steps", type=int, default=400)
     return p.parse_args()
 
@@ -315,6 +316,90 @@ def precision_bench(steps, stream, dev):
     return out
 
 
+def surrogate_bench(stream, dev, n_infer=65536, n_ref=512, n_train=1536, train_steps=30000):
+    """The learned surrogate against the LBM on droplets of edge 40 (R = 8):
+    trained on the batched LBM (n_train trajectories), then used on n_infer
+    fresh seeded trajectories, one M and D per trajectory after a spin-up and
+    one sampling interval.  The first n_ref of those trajectories also run on
+    the batched LBM, which gives the D errors (per sample, and of the D
+    statistics) and the batched LBM's droplets/s; plain = the single-box path,
+    one box after another."""
+    import numpy as np
+    import torch
+
+    from paper_2112_09972_gb300 import inputs, surrogate, workloads
+    from paper_2112_09972_gb300.lbm import BatchLBM, DropletLBM
+
+    edge, spinup, every, nsamp = 40, 1024, 8, 60
+    t0 = time.perf_counter()
+    hist = surrogate.gradient_histories(n_train, spinup + every * nsamp, edge, seed=12349)
+    X, M, _, _ = surrogate.lbm_windows(hist, edge, spinup, every, nsamp, stream=stream.cuda_stream)
+    t_data = time.perf_counter() - t0
+    sur = surrogate.Surrogate()
+    t0 = time.perf_counter()
+    sur.fit(X, M, steps=train_steps, batch=512, lr=1e-3, lr_final=1e-5)
+    t_train = time.perf_counter() - t0
+    # fresh trajectories: one window each, ending after the spin-up and one interval
+    n_steps = spinup + every
+    Wd, H = inputs.ou_final_windows(n_infer, n_steps, 200.0, 1.0, 12350, surrogate.WINDOW, surrogate.STRIDE, 0.1,
+                                    edge, n_full=n_ref)
+    Xi = np.ascontiguousarray(Wd.reshape(n_infer, -1), dtype=np.float32)
+    pin = torch.from_numpy(Xi).pin_memory()
+    sur.predict(pin[:4096])  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, Dp = sur.predict(pin)  # host windows in, D out: copies included
+    torch.cuda.synchronize()
+    t_sur = time.perf_counter() - t0
+    # LBM reference for the first n_ref trajectories, batched
+    # (the timed region includes the ensemble's initialisation and graph capture)
+    bt = BatchLBM([(edge,) * 3] * n_ref, [edge / 5.0] * n_ref, (1.0 / 6.0, 1.0 / 6.0), workloads.G_COUPLING,
+                  rho_lo=workloads.RHO_LO, rho_hi=workloads.RHO_HI, stream=stream.cuda_stream, device=dev)
+    bt.set_gradients(H)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bt.step(n_steps)
+    D_lbm, _, _ = bt.deformation()
+    t_lbm = time.perf_counter() - t0
+    bt.close()
+    # plain: one box through the single-box path, timed per step
+    g = DropletLBM((edge,) * 3, edge / 5.0, (1.0 / 6.0, 1.0 / 6.0), workloads.G_COUPLING, precision="fp32",
+                   rho_lo=workloads.RHO_LO, stream=stream.cuda_stream, device=dev)
+    g.set_gradient_table(np.arange(n_steps), H[:, 0])
+    g.step(20)
+    g.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    g.step(200)
+    b.record(stream)
+    g.sync()
+    t_plain_traj = a.elapsed_time(b) / 1e3 / 200 * n_steps
+    g.close()
+    sur.close()
+    Dr = Dp[:n_ref]
+    err = float(np.sqrt(np.mean((Dr - D_lbm) ** 2)) / np.sqrt(np.mean(D_lbm ** 2)))
+    stats = {"mean": abs(float(np.mean(Dr)) - float(np.mean(D_lbm))) / float(np.mean(D_lbm))}
+    for q in (50, 90, 99):
+        r = float(np.percentile(D_lbm, q))
+        stats[f"q{q}"] = abs(float(np.percentile(Dr, q)) - r) / r
+    fallback = int(np.count_nonzero(Dp > surrogate.D_FALLBACK))
+    return {
+        "workload": f"surrogate_edge{edge}_R8", "trajectory_steps": n_steps, "inferences": n_infer,
+        "window": [surrogate.WINDOW, surrogate.STRIDE], "train_trajectories": n_train,
+        "train_windows": int(X.shape[0]), "train_steps": train_steps,
+        "surrogate_droplets_per_s": round(n_infer / t_sur, 1),
+        "batched_lbm_droplets_per_s": round(n_ref / t_lbm, 2),
+        "plain_lbm_droplets_per_s": round(1.0 / t_plain_traj, 3),
+        "gain_vs_batched": round(n_infer / t_sur / (n_ref / t_lbm), 1),
+        "gain_vs_plain": round(n_infer / t_sur * t_plain_traj, 1),
+        "predicted_D_above_fallback": fallback,
+        "rel_rms_D_error_per_sample": round(err, 4),
+        "rel_D_statistics_error": {k: round(v, 5) for k, v in stats.items()},
+        "D_error_reference": f"batched LBM on the first {n_ref} trajectories",
+        "data_s": round(t_data, 1), "train_s": round(t_train, 1),
+    }
+
+
 def run_reference(args, w):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -435,6 +520,9 @@ def main():
     prec = None
     if not args.no_precision and world == 1:
         prec = precision_bench(args.precision_steps, stream, dev)
+    sur = None
+    if not args.no_surrogate and world == 1:
+        sur = surrogate_bench(stream, dev)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -477,6 +565,7 @@ def main():
         "cpu_baseline": cb,
         "ensemble": ens,
         "precision": prec,
+        "surrogate": sur,
         "D_last": samples[-1] if samples else None,
     }
     print(json.dumps(line))

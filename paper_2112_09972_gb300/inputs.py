@@ -55,6 +55,41 @@ def ou_gradient_history(n_steps, T_corr, tau_eta, seed, box_id=0):
     return A.reshape(n_steps, 9)
 
 
+def ou_final_windows(n_traj, n_steps, T_corr, tau_eta, seed, window, stride, u_lbm, L, n_full=0):
+    """Many OU gradient histories at once, without storing them whole.
+
+    The same process as ou_gradient_history (8 exact-update OU components on
+    the traceless basis), all trajectories driven by one Philox stream keyed
+    [seed, 2^32] (a different stream from the per-box histories), each
+    rescaled by Eq. 15 with its own maximum.  Returns (W, H): W [n_traj,
+    window, 9], the rescaled gradients of steps n_steps - 1 - stride (window -
+    1), ..., n_steps - 1 of every trajectory, and H [n_steps, n_full, 9], the
+    whole rescaled histories of the first n_full trajectories.
+    """
+    rng = np.random.Generator(np.random.Philox(key=[int(seed), 1 << 32]))
+    decay = np.exp(-1.0 / T_corr)
+    kick = np.sqrt(1.0 - np.exp(-2.0 / T_corr))
+    scale = np.array([1.0 / (tau_eta * np.sqrt(10.0))] * 5 + [1.0 / (tau_eta * np.sqrt(6.0))] * 3)
+    B = (traceless_basis() * scale[:, None, None]).reshape(8, 9)
+    rows = n_steps - 1 - stride * np.arange(window - 1, -1, -1)
+    slot = {int(r): j for j, r in enumerate(rows)}
+    W = np.empty((n_traj, window, 9))
+    H = np.empty((n_steps, n_full, 9))
+    amax = np.zeros(n_traj)
+    a = rng.standard_normal((n_traj, 8))
+    for t in range(n_steps):
+        if t > 0:
+            a = a * decay + kick * rng.standard_normal((n_traj, 8))
+        A = a @ B
+        amax = np.maximum(amax, np.max(np.abs(A), axis=1))
+        if t in slot:
+            W[:, slot[t]] = A
+        if n_full:
+            H[t] = A[:n_full]
+    f = float(u_lbm) / (float(L) * amax)
+    return W * f[:, None, None], H * f[None, :n_full, None]
+
+
 def simple_shear(gamma_dot):
     """A = gamma_dot e_x e_y^T, i.e. u_x = gamma_dot * y."""
     A = np.zeros(9)

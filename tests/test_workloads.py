@@ -1,7 +1,10 @@
-"""The workload constants match the oracle-measured golden values."""
+"""The workload constants match the oracle-measured golden values; the seeded
+input generators have the statistics they state."""
 
 import json
 import os
+
+import numpy as np
 
 from paper_2112_09972_gb300 import workloads
 
@@ -24,3 +27,23 @@ def test_parity_workload_parameters():
     hist = workloads.C2_THROUGHPUT.gradient_history(200)
     # Eq. 15: the element-wise maximum of the rescaled history is u_LBM / L
     assert abs(abs(hist).max() - 0.1 / 128) < 1e-18
+
+
+def test_ou_final_windows():
+    """The batched OU generator: windows are the rows of the whole histories,
+    traceless, Eq. 15-rescaled to u_LBM per trajectory, deterministic in the
+    seed, with the OU lag-one correlation exp(-1/T) (which the per-trajectory
+    rescaling leaves unchanged)."""
+    from paper_2112_09972_gb300 import inputs
+
+    n, steps, window, stride, T = 2000, 300, 16, 4, 50.0
+    W, H = inputs.ou_final_windows(n, steps, T, 1.0, 7, window, stride, 0.1, 40, n_full=n)
+    rows = steps - 1 - stride * np.arange(window - 1, -1, -1)
+    assert np.array_equal(W, H[rows].transpose(1, 0, 2))
+    assert np.max(np.abs(W[..., 0] + W[..., 4] + W[..., 8])) <= 1e-15
+    assert np.allclose(np.max(np.abs(H), axis=(0, 2)) * 40, 0.1, rtol=0, atol=1e-15)
+    W2, H2 = inputs.ou_final_windows(n, steps, T, 1.0, 7, window, stride, 0.1, 40, n_full=n)
+    assert np.array_equal(H2, H)
+    a, b = H[:-1].reshape(-1), H[1:].reshape(-1)
+    rho = float(np.sum(a * b) / np.sqrt(np.sum(a * a) * np.sum(b * b)))
+    assert abs(rho - np.exp(-1.0 / T)) <= 3e-3
