@@ -107,6 +107,11 @@ typedef struct {
     int32_t tile_y;      /* rows per CTA of the stream-collide kernel; 0: auto */
     int32_t z_chunk;     /* z planes per CTA of the stream-collide kernel; 0: auto */
     int32_t frame;       /* lbm_frame, default LBM_FRAME_DROPLET */
+    int32_t row_variant; /* row-tiled kernel: 1 per-thread loads of the pulled
+                            populations (each plane read twice, the second
+                            time from L2), 2 whole pulled rows staged in shared
+                            memory by bulk copies (cp.async.bulk, one read);
+                            0: automatic */
 } lbm_opts;
 
 /* Fill *opts with the defaults above. */

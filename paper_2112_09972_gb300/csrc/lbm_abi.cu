@@ -216,6 +216,7 @@ int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[
         return LBM_EINVAL;
     if (o.bc != LBM_BC_GHOST_LINEAR && o.bc != LBM_BC_PERIODIC_TEST) return LBM_EINVAL;
     if (o.frame != LBM_FRAME_DROPLET && o.frame != LBM_FRAME_BOX) return LBM_EINVAL;
+    if (o.row_variant < 0 || o.row_variant > 2) return LBM_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (box[a] < 4 || box[a] > 4096) return LBM_EINVAL;
     const int mn = std::min(box[0], std::min(box[1], box[2]));
@@ -253,7 +254,8 @@ int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[
     c->prec = o.precision;
     c->elem = elem_bytes_of(c->prec);
     c->L = make_layout(box[0], box[1], box[2], c->prec);
-    c->shape = choose_shape(c->L, c->prec, o.bc == LBM_BC_PERIODIC_TEST, o.tile_y, o.z_chunk, c->num_sms);
+    c->shape = choose_shape(c->L, c->prec, o.bc == LBM_BC_PERIODIC_TEST, o.tile_y, o.z_chunk, o.row_variant,
+                            c->num_sms);
     c->cur = 0;
     c->stream = (cudaStream_t)o.cuda_stream;
     c->own_stream = false;

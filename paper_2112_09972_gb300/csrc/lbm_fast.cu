@@ -133,6 +133,112 @@ __device__ __forceinline__ float4 ld_keep_f4(const float4* p, unsigned long long
     return v;
 }
 
+// ---- TMA-staged variant: bulk copies of whole pulled rows into shared memory ----
+
+// Bulk copy of `bytes` (a multiple of 16) from a 16-byte aligned global
+// address to this CTA's shared memory, counted on the CTA's mbarrier.
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+// Order this thread's earlier generic-proxy accesses to shared memory before
+// later async-proxy (bulk copy) writes to it.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ bool mbar_try_wait_cta(unsigned mbar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
+// Shared-memory image of one plane of one row for the staged variant: every
+// array the row's pulled populations come from, as a row segment that starts
+// at x = -4 (16-byte aligned) and covers x - c_ix for every x of the row.
+// Each source row is y - c_iy of plane p - c_iz, so over the grid every
+// population row is copied exactly once.
+template <int TX, typename ST>
+struct StagePlane;
+
+template <int TX>
+struct StagePlane<TX, float> {
+    static constexpr int SEG = TX + 8;  // floats per segment, x = -4 .. TX + 3
+    static constexpr unsigned BYTES = 38u * SEG * 4u;
+    static __device__ __forceinline__ void issue(const float* src, const Layout& L, int y, int p, unsigned dst,
+                                                 unsigned mbar) {
+#pragma unroll
+        for (int a = 0; a < 38; ++a) {
+            const int s = a / 19, i = a % 19;
+            bulk_g2s(dst + 4u * SEG * a, src + L.at(s, i, -4, y - cy_(i), p - cz_(i)), 4u * SEG, mbar);
+        }
+    }
+    static __device__ __forceinline__ void densities(const float* st, int x, float& ra, float& rb) {
+        ra = st[x + 4];
+        rb = st[19 * SEG + x + 4];
+#pragma unroll
+        for (int i = 1; i < 19; i += 2) {
+            ra += st[i * SEG + x - cx_(i) + 4] + st[(i + 1) * SEG + x - cx_(i + 1) + 4];
+            rb += st[(19 + i) * SEG + x - cx_(i) + 4] + st[(20 + i) * SEG + x - cx_(i + 1) + 4];
+        }
+    }
+    static __device__ __forceinline__ void populations(const float* st, int x, float (&f)[2][19]) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 19; ++i) f[s][i] = st[(s * 19 + i) * SEG + x - cx_(i) + 4];
+    }
+};
+
+template <int TX, typename T>
+struct StagePlane<TX, Dev<T>> {
+    static constexpr int SEG = TX + 8;  // words per deviation segment, x = -4 .. TX + 3
+    static constexpr unsigned NODE_BYTES = 16u * TX;
+    static constexpr unsigned BYTES = NODE_BYTES + 18u * SEG * 4u;
+    static __device__ __forceinline__ void issue(const Dev<T>* src, const Layout& L, int y, int p, unsigned dst,
+                                                 unsigned mbar) {
+        bulk_g2s(dst, reinterpret_cast<const float4*>(src) + L.dev_node(0, y, p), NODE_BYTES, mbar);
+        const unsigned* w = reinterpret_cast<const unsigned*>(src);
+#pragma unroll
+        for (int i = 1; i < 19; ++i)
+            bulk_g2s(dst + NODE_BYTES + 4u * SEG * (i - 1), w + L.dev_word(i, -4, y - cy_(i), p - cz_(i)), 4u * SEG,
+                     mbar);
+    }
+    static __device__ __forceinline__ const unsigned* words(const float* st) {
+        return reinterpret_cast<const unsigned*>(reinterpret_cast<const char*>(st) + NODE_BYTES);
+    }
+    static __device__ __forceinline__ void densities(const float* st, int x, float& ra, float& rb) {
+        const float4 o = reinterpret_cast<const float4*>(st)[x];
+        const unsigned* w = words(st);
+        float da = 0.f, db = 0.f;
+#pragma unroll
+        for (int i = 1; i < 19; i += 2) {
+            const float2 u = dev_unpack2<T>(w[(i - 1) * SEG + x - cx_(i) + 4]);
+            const float2 v = dev_unpack2<T>(w[i * SEG + x - cx_(i + 1) + 4]);
+            da += u.x + v.x;
+            db += u.y + v.y;
+        }
+        ra = o.z + (1.f - wgt<float>(0)) * o.x + da;
+        rb = o.w + (1.f - wgt<float>(0)) * o.y + db;
+    }
+    static __device__ __forceinline__ void populations(const float* st, int x, float (&f)[2][19]) {
+        const float4 o = reinterpret_cast<const float4*>(st)[x];
+        const unsigned* w = words(st);
+        f[0][0] = o.z;
+        f[1][0] = o.w;
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            const float2 v = dev_unpack2<T>(w[(i - 1) * SEG + x - cx_(i) + 4]);
+            f[0][i] = wgt<float>(i) * o.x + v.x;
+            f[1][i] = wgt<float>(i) * o.y + v.y;
+        }
+    }
+};
+
 // Storage-specific reads and writes of the row kernel.  A node is named by
 // its plane-0 indices (NodeIx); plane p adds p planes.
 struct NodeIx {
@@ -207,14 +313,26 @@ struct RowIO<Dev<T>> {
     }
 };
 
-template <int TX, int CY, int MINB, typename ST>
+// Shared memory of the staged variant beyond the density ring: NST stage
+// mbarriers, then (128-byte aligned) NST plane images.
+template <int TX, int CY, typename ST>
+struct StagedLayout {
+    static constexpr int NST = 3;  // planes z+1 (resident), z+2 and z+3 (in flight)
+    static constexpr size_t mbar_off = FastLayout<TX, CY>::bytes;
+    static constexpr size_t stage_off = ((mbar_off + 8 * NST + 127) / 128) * 128;
+    static constexpr size_t bytes = stage_off + (size_t)NST * StagePlane<TX, ST>::BYTES;
+};
+
+template <int TX, int CY, int MINB, typename ST, bool STAGED>
 __global__ void __launch_bounds__(TX, MINB)
     k_stream_collide_rows(const ST* __restrict__ src, ST* __restrict__ dst, Layout L, FastModel m, int zchunk,
                           CentreParts cp, int* __restrict__ d_err) {
     using IO = RowIO<ST>;
     using FL = FastLayout<TX, CY>;
-    constexpr int RW = FL::RW, HN = FL::HN, S = FL::S;
-    extern __shared__ __align__(16) float ring[];  // [S][3][RW][2], then S mbarriers
+    using SP = StagePlane<TX, ST>;
+    using SL = StagedLayout<TX, CY, ST>;
+    constexpr int RW = FL::RW, HN = FL::HN, S = FL::S, NST = SL::NST;
+    extern __shared__ __align__(128) float ring[];  // [S][3][RW][2], then S mbarriers (staged: see StagedLayout)
     unsigned long long* mbar = reinterpret_cast<unsigned long long*>(ring + FL::RING);
     __shared__ double red[4 * ((TX + 31) / 32)];
 
@@ -248,10 +366,18 @@ __global__ void __launch_bounds__(TX, MINB)
     const unsigned halo_ring = cluster_addr(ring_s, hside ? CY - 1 : 0);
     const unsigned halo_mbar = cluster_addr(mbar_s, hside ? CY - 1 : 0);
 
+    // staged variant: plane images and their mbarriers (one arrival, by
+    // thread 0, plus the bytes of the copies)
+    const unsigned smbar_s = smem_u32(ring) + (unsigned)SL::mbar_off;
+    const unsigned stage_s = smem_u32(ring) + (unsigned)SL::stage_off;
+    const float* stage = reinterpret_cast<const float*>(reinterpret_cast<const char*>(ring) + SL::stage_off);
+
     // ghost density in every slot (x halo columns keep it for good), barriers
     for (int e = x; e < FL::RING; e += TX) ring[e] = m.rho_b[e & 1];
     if (x == 0) {
         for (int k = 0; k < S; ++k) mbar_init(mbar_s + 8u * k, 1u);
+        if constexpr (STAGED)
+            for (int k = 0; k < NST; ++k) mbar_init(smbar_s + 8u * k, 1u);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     cluster.sync();  // barriers initialised before any remote store arrives
@@ -263,6 +389,42 @@ __global__ void __launch_bounds__(TX, MINB)
 
     auto slot_of = [&](int p) { return (p - (zc0 - 1)) % S; };
 
+    // Staged variant: plane p of this row lives in stage (p - zc0 + 1) mod NST.
+    // Thread 0 fills a stage (expect_tx, then the copies); every thread waits
+    // on the stage's mbarrier (bounded) before its first read of the plane.
+    // Only the planes this chunk reads and that lie in the box are copied.
+    auto stage_of = [&](int p) { return (p - zc0 + 1) % NST; };
+    auto plane_wanted = [&](int p) { return p >= 0 && p < L.Lz && p >= zc0 - 1 && p <= zc1; };
+    unsigned sphase = 0u;   // bit k: parity of stage k's next completion (every thread)
+    unsigned pending = 0u;  // thread 0: stages with copies it has not seen complete
+    auto fill = [&](int p) {
+        if (!plane_wanted(p)) return;
+        const int k = stage_of(p);
+        mbar_expect_tx(smbar_s + 8u * k, SP::BYTES);
+        SP::issue(src, L, y, p, stage_s + (unsigned)(k * SP::BYTES), smbar_s + 8u * k);
+        pending |= 1u << k;
+    };
+    auto stage_wait = [&](int p) {
+        const int k = stage_of(p);
+        const unsigned par = (sphase >> k) & 1u;
+        unsigned polls = 0;
+        bool ok = true;
+        while (!mbar_try_wait_cta(smbar_s + 8u * k, par)) {
+            if (++polls == kWaitPolls) {
+                atomicOr(d_err, 4);
+                ok = false;
+                break;
+            }
+        }
+        if (ok) pending &= ~(1u << k);
+        sphase ^= 1u << k;
+    };
+    auto stage_ptr = [&](int p) { return stage + (size_t)stage_of(p) * (SP::BYTES / 4); };
+    if constexpr (STAGED) {
+        if (x == 0)
+            for (int q = -1; q <= 1; ++q) fill(zc0 + q);
+    }
+
     // Post-streaming densities of plane p: the own node into row 0 of this
     // CTA's ring and into the neighbours' rows -1 / +1; the outer-halo node
     // (threads x < HN) into the edge CTA's row -1 / +1.  Ghost densities
@@ -271,7 +433,14 @@ __global__ void __launch_bounds__(TX, MINB)
         const int slot = slot_of(p);
         const bool in = p >= 0 && p < L.Lz;
         float ra = m.rho_b[0], rb = m.rho_b[1];
-        if (in) IO::densities(src, L, node0, p, keep, ra, rb);
+        if (in) {
+            if constexpr (STAGED) {
+                stage_wait(p);
+                SP::densities(stage_ptr(p), x, ra, rb);
+            } else {
+                IO::densities(src, L, node0, p, keep, ra, rb);
+            }
+        }
         *reinterpret_cast<float2*>(ring + ridx(slot, 0, x)) = make_float2(ra, rb);
         const unsigned mb = 8u * slot;
         if (rank > 0) st_async_f2(below_ring + 4u * ridx(slot, 1, x), ra, rb, below_mbar + mb);
@@ -305,13 +474,28 @@ __global__ void __launch_bounds__(TX, MINB)
     densities(zc0);
     wait_rows(zc0 - 1);
     wait_rows(zc0);
+    if constexpr (STAGED) {
+        __syncthreads();  // plane zc0 - 1 read by all: its stage takes plane zc0 + 2
+        if (x == 0) {
+            fence_proxy_async();
+            fill(zc0 + 2);
+        }
+    }
     for (int z = zc0; z < zc1; ++z) {
         densities(z + 1);
         // this node's populations for the collision, read while the
         // neighbour rows of plane z + 1 are in flight
         float f[2][19];
-        IO::populations(src, L, node0, z, f);
+        if constexpr (STAGED) SP::populations(stage_ptr(z), x, f);
+        else IO::populations(src, L, node0, z, f);
         __syncthreads();  // own row of plane z + 1 complete
+        if constexpr (STAGED) {
+            // plane z has been read by every thread: its stage takes plane z + 3
+            if (x == 0) {
+                fence_proxy_async();
+                fill(z + 3);
+            }
+        }
         wait_rows(z + 1);
 
         const int s0 = slot_of(z - 1), s1 = slot_of(z), s2 = slot_of(z + 1);
@@ -439,6 +623,18 @@ __global__ void __launch_bounds__(TX, MINB)
         // must be done reading it: the __syncthreads of the next iterations
         // (S > 3 planes apart) order that.
     }
+    // staged variant: copies whose completion thread 0 did not observe (a
+    // wait that gave up) are waited for again, bounded, before the CTA exits
+    if constexpr (STAGED) {
+        if (x == 0) {
+            for (int k = 0; k < NST; ++k) {
+                if (!((pending >> k) & 1u)) continue;
+                unsigned polls = 0;
+                while (!mbar_try_wait_cta(smbar_s + 8u * k, ((sphase >> k) & 1u) ^ 1u) && ++polls < kWaitPolls) {
+                }
+            }
+        }
+    }
     // no CTA leaves while another may still address its shared memory
     cluster.sync();
 
@@ -494,17 +690,24 @@ __global__ void __launch_bounds__(TX, MINB)
 
 constexpr int kRowMinBlocks = 6;
 
-// Resident CTAs per SM asked of the compiler: 6 x 128 threads.
-template <int TX>
+// Resident CTAs per SM asked of the compiler: 6 x 128 threads for the
+// direct-load variant; the staged variant is bounded by its shared memory
+// (about 2 x 128-thread CTAs per SM).
+template <int TX, bool STAGED>
 constexpr int row_min_blocks() {
-    return kRowMinBlocks * 128 / TX;
+    return STAGED ? (256 / TX > 0 ? 256 / TX : 1) : kRowMinBlocks * 128 / TX;
 }
 
-template <int TX, int CY, typename S>
+template <int TX, int CY, typename S, bool STAGED>
+constexpr size_t row_smem() {
+    return STAGED ? StagedLayout<TX, CY, S>::bytes : FastLayout<TX, CY>::bytes;
+}
+
+template <int TX, int CY, typename S, bool STAGED>
 cudaError_t launch_rows(const void* src, void* dst, const Layout& L, const Model& m, int zchunk, int nchunks,
                         CentreParts cp, int* d_err, cudaStream_t s) {
-    auto k = k_stream_collide_rows<TX, CY, row_min_blocks<TX>(), S>;
-    const size_t smem = FastLayout<TX, CY>::bytes;
+    auto k = k_stream_collide_rows<TX, CY, row_min_blocks<TX, STAGED>(), S, STAGED>;
+    const size_t smem = row_smem<TX, CY, S, STAGED>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     FastModel fm;
@@ -529,11 +732,14 @@ cudaError_t launch_rows(const void* src, void* dst, const Layout& L, const Model
     return cudaLaunchKernelEx(&cfg, k, (const S*)src, (S*)dst, L, fm, zchunk, cp, d_err);
 }
 
-template <int TX, int CY, typename S>
+template <int TX, int CY, typename S, bool STAGED>
 int max_clusters() {
-    auto k = k_stream_collide_rows<TX, CY, row_min_blocks<TX>(), S>;
-    const size_t smem = FastLayout<TX, CY>::bytes;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    auto k = k_stream_collide_rows<TX, CY, row_min_blocks<TX, STAGED>(), S, STAGED>;
+    const size_t smem = row_smem<TX, CY, S, STAGED>();
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(1, CY, 1);
     cfg.blockDim = dim3(TX, 1, 1);
@@ -555,27 +761,36 @@ int max_clusters() {
 
 constexpr int kRowCluster = 8;
 
-template <int TX, typename S>
+template <int TX, typename S, bool STAGED>
 cudaError_t rows_for(bool query, const void* src, void* dst, const Layout& L, const Model& m, int zchunk,
                      CentreParts cp, int* d_err, cudaStream_t s, int* resident) {
     if (query) {
-        *resident = max_clusters<TX, kRowCluster, S>() * kRowCluster;
+        *resident = max_clusters<TX, kRowCluster, S, STAGED>() * kRowCluster;
         return cudaSuccess;
     }
     const int nchunks = (L.Lz + zchunk - 1) / zchunk;
-    return launch_rows<TX, kRowCluster, S>(src, dst, L, m, zchunk, nchunks, cp, d_err, s);
+    return launch_rows<TX, kRowCluster, S, STAGED>(src, dst, L, m, zchunk, nchunks, cp, d_err, s);
 }
 
-// Dispatch on the row width and the storage type.
-cudaError_t rows_dispatch(int prec, bool query, const void* src, void* dst, const Layout& L, const Model& m,
-                          int zchunk, CentreParts cp, int* d_err, cudaStream_t s, int* resident) {
-#define LBM_ROWS_TX(TXV)                                                                                   \
-    if (L.Lx == TXV) {                                                                                     \
-        if (prec == kFP32) return rows_for<TXV, float>(query, src, dst, L, m, zchunk, cp, d_err, s, resident); \
-        if (prec == kFP16Dev)                                                                              \
-            return rows_for<TXV, Dev<__half>>(query, src, dst, L, m, zchunk, cp, d_err, s, resident);      \
-        if (prec == kBF16Dev)                                                                              \
-            return rows_for<TXV, Dev<__nv_bfloat16>>(query, src, dst, L, m, zchunk, cp, d_err, s, resident); \
+template <int TX, typename S>
+cudaError_t rows_variant(bool staged, bool query, const void* src, void* dst, const Layout& L, const Model& m,
+                         int zchunk, CentreParts cp, int* d_err, cudaStream_t s, int* resident) {
+    if (staged) return rows_for<TX, S, true>(query, src, dst, L, m, zchunk, cp, d_err, s, resident);
+    return rows_for<TX, S, false>(query, src, dst, L, m, zchunk, cp, d_err, s, resident);
+}
+
+// Dispatch on the row width, the storage type and the variant.
+cudaError_t rows_dispatch(int prec, bool staged, bool query, const void* src, void* dst, const Layout& L,
+                          const Model& m, int zchunk, CentreParts cp, int* d_err, cudaStream_t s, int* resident) {
+#define LBM_ROWS_TX(TXV)                                                                                        \
+    if (L.Lx == TXV) {                                                                                          \
+        if (prec == kFP32)                                                                                      \
+            return rows_variant<TXV, float>(staged, query, src, dst, L, m, zchunk, cp, d_err, s, resident);     \
+        if (prec == kFP16Dev)                                                                                   \
+            return rows_variant<TXV, Dev<__half>>(staged, query, src, dst, L, m, zchunk, cp, d_err, s, resident); \
+        if (prec == kBF16Dev)                                                                                   \
+            return rows_variant<TXV, Dev<__nv_bfloat16>>(staged, query, src, dst, L, m, zchunk, cp, d_err, s,   \
+                                                         resident);                                             \
     }
     LBM_ROWS_TX(32)
     LBM_ROWS_TX(64)
@@ -593,18 +808,19 @@ bool rows_kernel_applies(const Layout& L, int prec, int periodic) {
     return L.Ly % kRowCluster == 0 && L.Lz >= 2;
 }
 
-int rows_kernel_resident_ctas(const Layout& L, int prec) {
+int rows_kernel_resident_ctas(const Layout& L, int prec, bool staged) {
     int n = 0;
     Model m = {};
     CentreParts cp = {};
-    if (rows_dispatch(prec, true, nullptr, nullptr, L, m, 1, cp, nullptr, 0, &n) != cudaSuccess) return 0;
+    if (rows_dispatch(prec, staged, true, nullptr, nullptr, L, m, 1, cp, nullptr, 0, &n) != cudaSuccess) return 0;
     return n;
 }
 
-cudaError_t launch_stream_collide_rows(int prec, const void* src, void* dst, const Layout& L, const Model& m,
-                                       const Grad& A, int zchunk, CentreParts cp, int* d_err, cudaStream_t s) {
+cudaError_t launch_stream_collide_rows(int prec, bool staged, const void* src, void* dst, const Layout& L,
+                                       const Model& m, const Grad& A, int zchunk, CentreParts cp, int* d_err,
+                                       cudaStream_t s) {
     (void)A;  // this kernel reads the ghost shell written by the ghost kernel
-    return rows_dispatch(prec, false, src, dst, L, m, zchunk, cp, d_err, s, nullptr);
+    return rows_dispatch(prec, staged, false, src, dst, L, m, zchunk, cp, d_err, s, nullptr);
 }
 
 }  // namespace lbmgb

@@ -93,13 +93,16 @@ struct Shape {
     int rows;       // 1: the row-tiled cluster kernel (lbm_fast.cu), 0: the generic tile kernel
     int tx, ty;     // tile of the x-y plane per CTA
     int zchunk;     // z planes marched per CTA
+    int staged;     // row kernel: 1 the bulk-copy staged variant, 0 direct loads
     dim3 grid;
     int threads;
     size_t smem;
 };
 
 // ---- launchers (lbm_step.cu) ----
-Shape choose_shape(const Layout& L, int prec, int periodic, int ty_req, int zchunk_req, int num_sms);
+// staged_req: 1 direct loads, 2 staged, 0 automatic
+Shape choose_shape(const Layout& L, int prec, int periodic, int ty_req, int zchunk_req, int staged_req,
+                   int num_sms);
 cudaError_t launch_init(int prec, void* f, const Layout& L, double R, double xi, double rho_hi, double rho_lo,
                         Grad A0, cudaStream_t s);
 cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Grad A, CentreParts cp, int* d_err,
@@ -113,10 +116,13 @@ cudaError_t launch_centre(int prec, const void* f, const Layout& L, CentreParts 
 
 // ---- row-tiled cluster kernel (lbm_fast.cu): fp32 or 16-bit deviations, ghost boundary,
 //      Lx in {32, 64, 128, 256}, Ly % 8 == 0 ----
+// staged: the variant that stages whole pulled rows in shared memory with
+// bulk copies (cp.async.bulk) instead of per-thread loads.
 bool rows_kernel_applies(const Layout& L, int prec, int periodic);
-int rows_kernel_resident_ctas(const Layout& L, int prec);
-cudaError_t launch_stream_collide_rows(int prec, const void* src, void* dst, const Layout& L, const Model& m,
-                                       const Grad& A, int zchunk, CentreParts cp, int* d_err, cudaStream_t s);
+int rows_kernel_resident_ctas(const Layout& L, int prec, bool staged);
+cudaError_t launch_stream_collide_rows(int prec, bool staged, const void* src, void* dst, const Layout& L,
+                                       const Model& m, const Grad& A, int zchunk, CentreParts cp, int* d_err,
+                                       cudaStream_t s);
 
 // ---- launchers (lbm_reduce.cu) ----
 // Ten moments of w = max(phi, 0) and the deformation: result[0..9] moments,

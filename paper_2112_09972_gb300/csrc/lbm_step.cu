@@ -235,12 +235,15 @@ Layout make_layout(int Lx, int Ly, int Lz, int prec) {
     return L;
 }
 
-Shape choose_shape(const Layout& L, int prec, int periodic, int ty_req, int zchunk_req, int num_sms) {
+Shape choose_shape(const Layout& L, int prec, int periodic, int ty_req, int zchunk_req, int staged_req,
+                   int num_sms) {
     Shape sh;
     sh.rows = 0;
+    sh.staged = 0;
     if (ty_req <= 0 && rows_kernel_applies(L, prec, periodic)) {
         // one CTA per row
-        const int resident = rows_kernel_resident_ctas(L, prec);
+        const bool staged = staged_req == 2;
+        const int resident = rows_kernel_resident_ctas(L, prec, staged);
         if (resident > 0) {
             // Chunks of about 32 planes (each chunk re-reads two planes) when
             // that gives at least half as many CTAs as fit on the GPU at
@@ -256,6 +259,7 @@ Shape choose_shape(const Layout& L, int prec, int periodic, int ty_req, int zchu
             if (chunks < 1) chunks = 1;
             if (chunks > L.Lz) chunks = L.Lz;
             sh.rows = 1;
+            sh.staged = staged ? 1 : 0;
             sh.tx = L.Lx;
             sh.ty = 1;
             sh.zchunk = (L.Lz + chunks - 1) / chunks;
@@ -328,7 +332,7 @@ cudaError_t launch_centre(int prec, const void* f, const Layout& L, CentreParts 
 
 cudaError_t launch_stream_collide(int prec, const void* src, void* dst, const Layout& L, const Model& m,
                                   const Shape& sh, const Grad& A, CentreParts cp, int* d_err, cudaStream_t s) {
-    if (sh.rows) return launch_stream_collide_rows(prec, src, dst, L, m, A, sh.zchunk, cp, d_err, s);
+    if (sh.rows) return launch_stream_collide_rows(prec, sh.staged != 0, src, dst, L, m, A, sh.zchunk, cp, d_err, s);
     if (prec == kFP64) return stream_collide_t<double, double, kMaxThreadsF64>(src, dst, L, m, sh, cp, d_err, s);
     if (prec == kFP32) return stream_collide_t<float, float, kMaxThreadsF32>(src, dst, L, m, sh, cp, d_err, s);
     if (prec == kFP16Dev) return stream_collide_t<Dev<__half>, float, kMaxThreadsF32>(src, dst, L, m, sh, cp, d_err, s);

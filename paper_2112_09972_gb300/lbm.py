@@ -52,6 +52,7 @@ class lbm_opts(ctypes.Structure):
         ("tile_y", ctypes.c_int32),
         ("z_chunk", ctypes.c_int32),
         ("frame", ctypes.c_int32),
+        ("row_variant", ctypes.c_int32),
     ]
 
 
@@ -186,7 +187,7 @@ class DropletLBM:
     """
 
     def __init__(self, box, R, visc, G, precision="fp32", periodic=False, rho_hi=0.0, rho_lo=0.0, xi=0.0,
-                 mach_limit=0.0, stream=None, device=-1, tile_y=0, z_chunk=0, frame="droplet"):
+                 mach_limit=0.0, stream=None, device=-1, tile_y=0, z_chunk=0, frame="droplet", row_variant=0):
         lib = load_library()
         self._lib = lib
         if isinstance(box, int):
@@ -203,6 +204,7 @@ class DropletLBM:
         o.cuda_stream = stream
         o.device = int(device)
         o.tile_y, o.z_chunk = int(tile_y), int(z_chunk)
+        o.row_variant = int(row_variant)
         o.frame = FRAMES[frame]
         b = (ctypes.c_int32 * 3)(*self.box)
         v = (ctypes.c_double * 2)(float(visc[0]), float(visc[1]))

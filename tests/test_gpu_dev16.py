@@ -114,17 +114,21 @@ def test_initial_state_matches_storage_model(built, oracle_mod, storage):
 
 # (box, periodic, tile_y): the row-tiled cluster kernel (widths 64 and 256,
 # automatic) and the generic tile kernel (tile_y > 0, and the periodic mode)
-CASES = [((64, 24, 20), False, 0), ((256, 16, 12), False, 0), ((37, 29, 23), False, 3), ((30, 26, 22), True, 4)]
+# (box, periodic, tile_y, row variant): the row-tiled cluster kernel (widths
+# 64 and 256, per-thread loads and bulk-copy staging) and the generic tile
+# kernel (tile_y > 0, and the periodic mode)
+CASES = [((64, 24, 20), False, 0, 1), ((256, 16, 12), False, 0, 1), ((64, 24, 20), False, 0, 2),
+         ((256, 16, 12), False, 0, 2), ((37, 29, 23), False, 3, 0), ((30, 26, 22), True, 4, 0)]
 
 
 @pytest.mark.parametrize("storage", ["fp16dev", "bf16dev"])
-@pytest.mark.parametrize("box,periodic,tile_y", CASES)
-def test_one_step_matches_storage_model(built, oracle_mod, storage, box, periodic, tile_y):
+@pytest.mark.parametrize("box,periodic,tile_y,variant", CASES)
+def test_one_step_matches_storage_model(built, oracle_mod, storage, box, periodic, tile_y, variant):
     f0, A = _perturbed(oracle_mod, box, 4.0, periodic, seed=3)
     o = oracle_mod.OracleLBM(box, (1.0, 1.0), 3.5, (workloads.RHO_LO, 1.0), periodic=periodic, storage=storage)
     o.set_populations(f0)
     g = DropletLBM(box, 4.0, (0.5 / 3, 0.5 / 3), 3.5, precision=storage, periodic=periodic, rho_hi=1.0,
-                   rho_lo=workloads.RHO_LO, tile_y=tile_y, z_chunk=5)
+                   rho_lo=workloads.RHO_LO, tile_y=tile_y, z_chunk=5, row_variant=variant)
     g.set_populations(f0)
     rho_b = (workloads.RHO_LO, 1.0)
     # the upload is the storage model's conversion

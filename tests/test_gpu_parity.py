@@ -54,14 +54,16 @@ def c1_reference(oracle_mod):
     return dict(A=A, ra=ra, rb=rb, u=u, D=D, axes=axes, lam=lam, mass=o.checksums()[0])
 
 
-@pytest.mark.parametrize("precision,tile_y,tol_field,tol_D",
-                         [("fp64", 0, 1e-10, 1e-9), ("fp32", 0, 1e-4, 1e-3), ("fp32", 8, 1e-4, 1e-3)])
-def test_config1_parity_after_2000_steps(built, c1_reference, precision, tile_y, tol_field, tol_D):
-    """fp32 runs both stream-collide kernels: the row-tiled cluster kernel
-    (automatic for a 32-wide box) and the generic tile kernel (tile_y = 8)."""
+@pytest.mark.parametrize("precision,tile_y,variant,tol_field,tol_D",
+                         [("fp64", 0, 0, 1e-10, 1e-9), ("fp32", 0, 1, 1e-4, 1e-3), ("fp32", 0, 2, 1e-4, 1e-3),
+                          ("fp32", 8, 0, 1e-4, 1e-3)])
+def test_config1_parity_after_2000_steps(built, c1_reference, precision, tile_y, variant, tol_field, tol_D):
+    """fp32 runs every stream-collide kernel: the row-tiled cluster kernel
+    (a 32-wide box) with per-thread loads (variant 1) and with bulk-copy
+    staging (variant 2), and the generic tile kernel (tile_y = 8)."""
     w = workloads.C1_PARITY
     g = DropletLBM((w.box,) * 3, w.R, w.visc, w.G, precision=precision, rho_hi=w.rho_hi, rho_lo=w.rho_lo, xi=w.xi,
-                   tile_y=tile_y)
+                   tile_y=tile_y, row_variant=variant)
     g.set_gradient(c1_reference["A"], 0)
     g.step(w.steps)
     ra, rb, u = g.fields()
@@ -112,8 +114,9 @@ def test_interpolated_gradient_knots(built, oracle_mod):
     assert rel_linf(g.populations(), o.populations()) <= 1e-12
 
 
-@pytest.mark.parametrize("precision,tile_y,tol", [("fp64", 0, 1e-12), ("fp32", 0, 1e-5), ("fp32", 4, 1e-5)])
-def test_full_size_single_step_128(built, oracle_mod, precision, tile_y, tol):
+@pytest.mark.parametrize("precision,tile_y,variant,tol", [("fp64", 0, 0, 1e-12), ("fp32", 0, 1, 1e-5),
+                                                          ("fp32", 0, 2, 1e-5), ("fp32", 4, 0, 1e-5)])
+def test_full_size_single_step_128(built, oracle_mod, precision, tile_y, variant, tol):
     """128^3 with the benchmark's launch shape (fp32, automatic: the row-tiled
     cluster kernel) and the generic tile kernel: one step from an oracle state."""
     w = workloads.C2_THROUGHPUT
@@ -124,7 +127,8 @@ def test_full_size_single_step_128(built, oracle_mod, precision, tile_y, tol):
     o.step(hist[0])
     f0 = inputs.perturbed_populations(o.populations(), 1e-4, seed=5)
     o.set_populations(f0)
-    g = DropletLBM(box, w.R, w.visc, w.G, precision=precision, rho_hi=w.rho_hi, rho_lo=w.rho_lo, tile_y=tile_y)
+    g = DropletLBM(box, w.R, w.visc, w.G, precision=precision, rho_hi=w.rho_hi, rho_lo=w.rho_lo, tile_y=tile_y,
+                   row_variant=variant)
     g.set_populations(f0)
     g.set_gradient_table([0, 1, 2], hist)
     # the context's step counter is 0; the oracle steps with A(t=0) as well
@@ -240,12 +244,14 @@ def test_box_frame_short_run(built, oracle_mod):
     assert rel_linf(g.populations(), o.populations()) <= 1e-12
 
 
-@pytest.mark.parametrize("box", [(64, 24, 20), (128, 16, 9), (32, 40, 5)])
-def test_row_cluster_kernel_shapes(built, oracle_mod, box):
-    """The row-tiled cluster kernel on other widths, cluster counts and short
-    z extents (ragged last z chunk), fp32, 12 steps from a perturbed state."""
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("box", [(64, 24, 20), (128, 16, 9), (32, 40, 5), (256, 8, 6)])
+def test_row_cluster_kernel_shapes(built, oracle_mod, box, variant):
+    """The row-tiled cluster kernel (both variants) on other widths, cluster
+    counts and short z extents (ragged last z chunk), fp32, 12 steps from a
+    perturbed state."""
     tau = (1.0, 1.0)
-    o, g = _pair(oracle_mod, box, 1.5, tau, 3.5, "fp32", z_chunk=2)
+    o, g = _pair(oracle_mod, box, 1.5, tau, 3.5, "fp32", z_chunk=2, row_variant=variant)
     hist = inputs.ou_gradient_history(12, 20.0, 600.0, seed=4)
     o.init_droplet(1.5, 1.0, 1.0, workloads.RHO_LO, hist[0])
     f0 = inputs.perturbed_populations(o.populations(), 1e-3, seed=8)
