@@ -200,6 +200,19 @@ int lbm_set_populations(lbm_ctx* ctx, const double* f);
 /* float64 sums over the box: mass[s] = sum rho_s, mom[a] = sum rho u_a. */
 int lbm_checksums(lbm_ctx* ctx, double mass[2], double mom[3]);
 
+/*
+ * Breakup detection: the connected components (6-connected nodes) of the
+ * droplet phase phi > threshold of the current state, phi = (rho_A - rho_B) /
+ * (rho_A + rho_B) (0 is the interface).  *count receives the number of
+ * components with at least min_nodes nodes and sizes[0 .. max_sizes-1] their
+ * node counts, largest first (0 past the last).  A droplet that broke up
+ * has count >= 2.  Periodic images connect in the periodic test mode.
+ * Synchronises; allocates 16 bytes per node of scratch for the call
+ * (LBM_ETIMEOUT if the labelling did not settle within its sweep bound).
+ */
+int lbm_components(lbm_ctx* ctx, double threshold, int64_t min_nodes, int32_t* count, int64_t* sizes,
+                   int32_t max_sizes);
+
 /* Step counter n of the next step (the number of steps taken so far). */
 int lbm_get_step(lbm_ctx* ctx, int64_t* step);
 
@@ -327,6 +340,28 @@ void lbm_destroy(lbm_ctx* ctx);
 
 /* Static description of a status code. */
 const char* lbm_strerror(int code);
+
+/*
+ * Maffettone-Minale model (Sec. 2, Eqs. 1, 2, 4, 5) for n gradient histories
+ * at once, one GPU thread per trajectory: the morphology tensor M starts at the
+ * identity (a sphere) and follows
+ *   dM/dt = [f2(chi, Ca) tau_d (S M + M S) + tau_d (W M - M W)
+ *            - f1(chi) (M - 3 III_M / II_M I)] / tau_d
+ * in LBM time, with S, W the symmetric / antisymmetric parts of A(t),
+ * Ca = tau_d max|A_ij| (Eq. 3), II_M = ((tr M)^2 - M:M)/2, III_M = det M.
+ *   A       device float64 [T][n][9]: A of trajectory k at LBM step t (row-major,
+ *           lattice units), linear in t between rows;
+ *   tau_d   the droplet time eta_s R / sigma in LBM steps (> 0); chi the
+ *           viscosity ratio (> 0);
+ *   substeps classical RK4 steps per LBM step (>= 1);
+ *   record_every  D (Eq. 4) is written at t = 0, r, 2r, ... <= T - 1 into
+ *           D [floor((T - 1) / r) + 1][n] (device float64);
+ *   precision LBM_FP64 or LBM_FP32 arithmetic;
+ *   M       device float64 [n][6] (xx, xy, xz, yy, yz, zz) at t = T - 1, or NULL.
+ * Asynchronous on cuda_stream; allocates nothing.
+ */
+int lbm_mm_integrate(const double* A, int64_t T, int64_t n, double tau_d, double chi, int32_t substeps,
+                     int32_t record_every, int32_t precision, double* D, double* M, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------
  * Learned surrogate (an addition of this library; the paper compares the

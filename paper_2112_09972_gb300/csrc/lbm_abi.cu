@@ -468,6 +468,61 @@ int lbm_checksums(lbm_ctx* c, double mass[2], double mom[3]) {
     return LBM_OK;
 }
 
+int lbm_components(lbm_ctx* c, double threshold, int64_t min_nodes, int32_t* count, int64_t* sizes,
+                   int32_t max_sizes) {
+    if (!c || !count || !std::isfinite(threshold) || max_sizes < 0 || (max_sizes > 0 && !sizes)) return LBM_EINVAL;
+    int st = set_device(c);
+    if (st || (st = lazy_init(c))) return st;
+    const long long N = (long long)c->box[0] * c->box[1] * c->box[2];
+    if (N > INT32_MAX) return LBM_EINVAL;
+    // scratch: labels and sizes (N ints each), the change flag and root counter,
+    // and the root sizes (N 64-bit)
+    char* d = nullptr;
+    const size_t bytes = sizeof(int) * (2 * N + 2) + sizeof(long long) * N + 16;
+    LBM_TRY(cudaMallocAsync((void**)&d, bytes, c->stream));
+    int* label = (int*)d;
+    int* size = label + N;
+    int* flags = size + N;  // [0] changed, [1] root count
+    long long* out = (long long*)(((uintptr_t)(flags + 2) + 15) & ~(uintptr_t)15);
+    int h_flags[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(size, 0, sizeof(int) * (N + 2), c->stream);
+    if (e == cudaSuccess) e = launch_cc_init(c->prec, c->f[c->cur], c->L, threshold, label, c->stream);
+    // propagation sweeps until no label changes; bounded (a component's
+    // labels settle within its node count of sweeps)
+    const long long max_sweeps = std::min<long long>(N + 8, 1LL << 22);
+    bool converged = false;
+    for (long long it = 0; e == cudaSuccess && it < max_sweeps; it += 4) {
+        e = cudaMemsetAsync(flags, 0, sizeof(int), c->stream);
+        for (int q = 0; q < 4 && e == cudaSuccess; ++q) e = launch_cc_sweep(c->L, c->model.periodic, label, flags, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_flags, flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess && h_flags[0] == 0) {
+            converged = true;
+            break;
+        }
+    }
+    std::vector<long long> roots;
+    if (e == cudaSuccess && converged) e = launch_cc_sizes(c->L, label, size, flags + 1, out, (int)N, c->stream);
+    if (e == cudaSuccess && converged) e = cudaMemcpyAsync(h_flags, flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && converged) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && converged) {
+        try { roots.resize((size_t)h_flags[1]); } catch (...) { e = cudaErrorMemoryAllocation; }
+        if (e == cudaSuccess && !roots.empty())
+            e = cudaMemcpyAsync(roots.data(), out, sizeof(long long) * roots.size(), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    cudaFreeAsync(d, c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!converged) return LBM_ETIMEOUT;
+    std::vector<long long> kept;
+    for (long long v : roots)
+        if (v >= min_nodes) kept.push_back(v);
+    std::sort(kept.begin(), kept.end(), [](long long a, long long b) { return a > b; });
+    *count = (int32_t)kept.size();
+    for (int32_t k = 0; k < max_sizes; ++k) sizes[k] = k < (int32_t)kept.size() ? kept[k] : 0;
+    return sync_and_check(c);
+}
+
 int lbm_get_step(lbm_ctx* c, int64_t* step) {
     if (!c || !step) return LBM_EINVAL;
     *step = c->step;

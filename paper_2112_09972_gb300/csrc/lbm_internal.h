@@ -138,6 +138,12 @@ cudaError_t launch_fields(int prec, const void* f, const Layout& L, const Model&
 cudaError_t launch_checksums(int prec, const void* f, const Layout& L, const Model& m, double* partials,
                              int nblocks, double* result5, cudaStream_t s);
 cudaError_t launch_pack(int prec, const void* f, const Layout& L, const Model& m, double* out, cudaStream_t s);
+// Connected components of phi > threshold (6-connectivity): label init, one
+// propagation sweep (sets *changed), component sizes of the roots (first cap).
+cudaError_t launch_cc_init(int prec, const void* f, const Layout& L, double threshold, int* label, cudaStream_t s);
+cudaError_t launch_cc_sweep(const Layout& L, int periodic, int* label, int* changed, cudaStream_t s);
+cudaError_t launch_cc_sizes(const Layout& L, const int* label, int* size, int* count, long long* out, int cap,
+                            cudaStream_t s);
 // scratch: 2 N floats (16-bit deviation storage only; may be NULL otherwise)
 cudaError_t launch_unpack(int prec, void* f, const Layout& L, const Model& m, const double* in, float* scratch,
                           cudaStream_t s);

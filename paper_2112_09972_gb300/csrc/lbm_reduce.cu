@@ -299,6 +299,73 @@ __global__ void k_unpack(S* __restrict__ f, Layout L, const double* __restrict__
     f[L.at(si / 19, si % 19, x, y, z)] = (S)in[e];
 }
 
+// ---- connected components of the droplet phase (breakup detection) ----
+
+// label[n] = n where phi > threshold (phi = (rho_A - rho_B) / (rho_A + rho_B)), -1 elsewhere;
+// n = (z Ly + y) Lx + x.
+template <typename S>
+__global__ void k_cc_init(const S* __restrict__ f, Layout L, double threshold, int* __restrict__ label) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
+    double ra, rb;
+    node_rho(f, L, x, y, z, ra, rb);
+    label[n] = (ra - rb) / (ra + rb) > threshold ? (int)n : -1;
+}
+
+// One sweep of minimum-label propagation over the 6 face neighbours (wrapping
+// in the periodic mode), with pointer jumping; sets *changed when a label
+// decreased.  Labels only decrease and stay labels of the same component, so
+// repeated sweeps converge to the smallest index of each component.
+__global__ void k_cc_sweep(Layout L, int periodic, int* __restrict__ label, int* __restrict__ changed) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int own = label[n];
+    if (own < 0) return;
+    const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
+    int m = own;
+    const int dx[6] = {1, -1, 0, 0, 0, 0}, dy[6] = {0, 0, 1, -1, 0, 0}, dz[6] = {0, 0, 0, 0, 1, -1};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        int xn = x + dx[q], yn = y + dy[q], zn = z + dz[q];
+        if (periodic) {
+            xn = (xn + L.Lx) % L.Lx; yn = (yn + L.Ly) % L.Ly; zn = (zn + L.Lz) % L.Lz;
+        } else if (xn < 0 || xn >= L.Lx || yn < 0 || yn >= L.Ly || zn < 0 || zn >= L.Lz) {
+            continue;
+        }
+        const int v = label[((long long)zn * L.Ly + yn) * L.Lx + xn];
+        if (v >= 0 && v < m) m = v;
+    }
+    const int jump = label[m];  // the label of the smallest label seen (pointer jumping)
+    if (jump >= 0 && jump < m) m = jump;
+    if (m < own) {
+        label[n] = m;
+        *changed = 1;
+    }
+}
+
+// Component sizes: size[label[n]] += 1; then roots (label[n] == n) append
+// (root, size) to out with an atomic counter.
+__global__ void k_cc_sizes(Layout L, const int* __restrict__ label, int* __restrict__ size) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int v = label[n];
+    if (v >= 0) atomicAdd(size + v, 1);
+}
+
+__global__ void k_cc_roots(Layout L, const int* __restrict__ label, const int* __restrict__ size,
+                           int* __restrict__ count, long long* __restrict__ out, int cap) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    if (label[n] != (int)n) return;
+    const int k = atomicAdd(count, 1);
+    if (k < cap) out[k] = size[n];
+}
+
 }  // namespace
 
 int moments_blocks(const Layout& L, int num_sms) {
@@ -369,6 +436,35 @@ cudaError_t launch_unpack(int prec, void* f, const Layout& L, const Model& m, co
     const unsigned blocks = (unsigned)((E + 255) / 256);
     if (prec == kFP64) k_unpack<double><<<blocks, 256, 0, s>>>((double*)f, L, in);
     else k_unpack<float><<<blocks, 256, 0, s>>>((float*)f, L, in);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmgb
+
+namespace lbmgb {
+
+cudaError_t launch_cc_init(int prec, const void* f, const Layout& L, double threshold, int* label, cudaStream_t s) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const unsigned blocks = (unsigned)((N + 255) / 256);
+    if (prec == kFP64) k_cc_init<double><<<blocks, 256, 0, s>>>((const double*)f, L, threshold, label);
+    else if (prec == kFP32) k_cc_init<float><<<blocks, 256, 0, s>>>((const float*)f, L, threshold, label);
+    else if (prec == kFP16Dev) k_cc_init<Dev<__half>><<<blocks, 256, 0, s>>>((const Dev<__half>*)f, L, threshold, label);
+    else k_cc_init<Dev<__nv_bfloat16>><<<blocks, 256, 0, s>>>((const Dev<__nv_bfloat16>*)f, L, threshold, label);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cc_sweep(const Layout& L, int periodic, int* label, int* changed, cudaStream_t s) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    k_cc_sweep<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(L, periodic, label, changed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cc_sizes(const Layout& L, const int* label, int* size, int* count, long long* out, int cap,
+                            cudaStream_t s) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const unsigned blocks = (unsigned)((N + 255) / 256);
+    k_cc_sizes<<<blocks, 256, 0, s>>>(L, label, size);
+    k_cc_roots<<<blocks, 256, 0, s>>>(L, label, size, count, out, cap);
     return cudaGetLastError();
 }
 

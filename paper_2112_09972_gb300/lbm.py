@@ -35,7 +35,7 @@ ABI_FUNCTIONS = [
     "lbm_batch_destroy", "lbm_batch_moments",
     "lbm_mlp_create", "lbm_mlp_set_normalisation", "lbm_mlp_param_count", "lbm_mlp_get_params",
     "lbm_mlp_set_params", "lbm_mlp_forward", "lbm_mlp_deformation", "lbm_mlp_gradients", "lbm_mlp_train_step",
-    "lbm_mlp_sync", "lbm_mlp_destroy",
+    "lbm_mlp_sync", "lbm_mlp_destroy", "lbm_mm_integrate", "lbm_components",
 ]
 
 
@@ -125,6 +125,9 @@ def load_library(path=LIB_PATH):
         "lbm_mlp_train_step": (ctypes.c_int, [vp, vp, vp, ctypes.c_int64, ctypes.c_float, _DP]),
         "lbm_mlp_sync": (ctypes.c_int, [vp]),
         "lbm_mlp_destroy": (None, [vp]),
+        "lbm_components": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int64, _I32P, _I64P, ctypes.c_int32]),
+        "lbm_mm_integrate": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -280,6 +283,14 @@ class DropletLBM:
         mom = np.zeros(3)
         _check(self._lib.lbm_checksums(self._h, _dptr(mass), _dptr(mom)), "lbm_checksums")
         return mass, mom
+
+    def components(self, threshold=0.0, min_nodes=1, max_sizes=8):
+        """(count, sizes) of the droplet phase's connected components (lbm_components)."""
+        cnt = ctypes.c_int32()
+        sizes = np.zeros(max(int(max_sizes), 1), dtype=np.int64)
+        _check(self._lib.lbm_components(self._h, float(threshold), int(min_nodes), ctypes.byref(cnt),
+                                        sizes.ctypes.data_as(_I64P), int(max_sizes)), "lbm_components")
+        return cnt.value, sizes[:max_sizes]
 
     def step_count(self):
         s = ctypes.c_int64()
@@ -485,3 +496,23 @@ class MLP:
 
     def sync(self):
         _check(self._lib.lbm_mlp_sync(self._h), "lbm_mlp_sync")
+
+
+def mm_integrate(A, tau_d, chi, substeps=10, record_every=1, precision="fp64", want_M=False, stream=None):
+    """Maffettone-Minale D(t) of many trajectories on the GPU (lbm_mm_integrate).
+
+    ``A`` is a torch CUDA float64 tensor [T, n, 9]; returns torch CUDA tensors
+    D [floor((T-1)/record_every) + 1, n] and, if want_M, M [n, 6]."""
+    import torch
+
+    lib = load_library()
+    T, n = int(A.shape[0]), int(A.shape[1])
+    A = A.contiguous()
+    D = torch.empty(((T - 1) // record_every + 1, n), dtype=torch.float64, device=A.device)
+    M = torch.empty((n, 6), dtype=torch.float64, device=A.device) if want_M else None
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device).cuda_stream
+    _check(lib.lbm_mm_integrate(A.data_ptr(), T, n, float(tau_d), float(chi), int(substeps), int(record_every),
+                                PRECISIONS[precision], D.data_ptr(), None if M is None else M.data_ptr(), stream),
+           "lbm_mm_integrate")
+    return (D, M) if want_M else D
