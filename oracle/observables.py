@@ -15,6 +15,15 @@ that this repository adopts where the paper is silent:
 * ``coexistence_rho_lo`` -- the minority density of a flat interface:
   ln(h/l) = G (h - l), the balance c_s^2 grad rho_A = -G c_s^2 rho_A grad rho_B
   that Eq. 7 gives in the continuum limit.
+* ``surface_deformation`` -- D_LBM = sqrt(1 - Omega_0 / Omega) (Sec. 5,
+  Eq. 17), with the surface area Omega of the diffuse interface read as the
+  mean area of the level sets of phi between its extremes (the co-area
+  formula: Omega = sum |grad phi| / (phi_max - phi_min), central differences
+  at interior nodes) and Omega_0 = (36 pi V^2)^(1/3) the area of the sphere of
+  the droplet's volume V = sum (phi - phi_min) / (phi_max - phi_min).
+* ``reinject_mass`` -- the reading adopted for the mass reinjection that Sec. 2
+  cites: the droplet component's populations at nodes with phi > 0 are
+  multiplied by one factor, so that its total mass becomes the target.
 """
 
 import numpy as np
@@ -93,3 +102,35 @@ def velocity_error_E0(u, A, box):
     num = np.sqrt(np.mean(np.sum((u - v0) ** 2, axis=-1)))
     den = np.sqrt(np.mean(np.sum(v0 ** 2, axis=-1)))
     return num / den
+
+
+def phase_field(rho_a, rho_b):
+    """phi = (rho_A - rho_B) / (rho_A + rho_B)."""
+    return (rho_a - rho_b) / (rho_a + rho_b)
+
+
+def surface_deformation(rho_a, rho_b):
+    """(D_LBM, Omega, V) of Eq. 17 for density fields [z, y, x] (see the module notes)."""
+    phi = phase_field(np.asarray(rho_a, dtype=np.float64), np.asarray(rho_b, dtype=np.float64))
+    lo, hi = float(phi.min()), float(phi.max())
+    span = hi - lo
+    # central differences at interior nodes
+    gz = 0.5 * (phi[2:, 1:-1, 1:-1] - phi[:-2, 1:-1, 1:-1])
+    gy = 0.5 * (phi[1:-1, 2:, 1:-1] - phi[1:-1, :-2, 1:-1])
+    gx = 0.5 * (phi[1:-1, 1:-1, 2:] - phi[1:-1, 1:-1, :-2])
+    area = float(np.sum(np.sqrt(gx * gx + gy * gy + gz * gz))) / span
+    volume = float(np.sum(phi - lo)) / span
+    area0 = (36.0 * np.pi * volume * volume) ** (1.0 / 3.0)
+    return float(np.sqrt(max(0.0, 1.0 - area0 / area))), area, volume
+
+
+def reinject_mass(f, target):
+    """Populations f [2, 19, z, y, x] with the droplet component (0) scaled by
+    one factor at the nodes where phi > 0, so that its total mass is target."""
+    f = np.array(f, dtype=np.float64)
+    ra, rb = f[0].sum(axis=0), f[1].sum(axis=0)
+    inside = phase_field(ra, rb) > 0.0
+    m_in, m_out = float(ra[inside].sum()), float(ra[~inside].sum())
+    k = (target - m_out) / m_in
+    f[0][:, inside] *= k
+    return f
