@@ -213,6 +213,28 @@ int lbm_checksums(lbm_ctx* ctx, double mass[2], double mom[3]);
 int lbm_components(lbm_ctx* ctx, double threshold, int64_t min_nodes, int32_t* count, int64_t* sizes,
                    int32_t max_sizes);
 
+/*
+ * Surface-area deformation of Sec. 5, Eq. 17: D_lbm = sqrt(1 - Omega_0 /
+ * Omega), Omega the droplet's surface area and Omega_0 that of the sphere of
+ * its volume.  The diffuse interface's area is the mean area of the level
+ * sets of phi between its extremes (co-area formula): Omega = sum |grad phi| /
+ * (phi_max - phi_min), central differences at interior nodes; the volume
+ * V = sum (phi - phi_min) / (phi_max - phi_min); Omega_0 = (36 pi V^2)^(1/3).
+ * area and volume (may be NULL) receive Omega and V.  Synchronises;
+ * allocates 8 bytes per node of scratch for the call.
+ */
+int lbm_surface_deformation(lbm_ctx* ctx, double* D_lbm, double* area, double* volume);
+
+/*
+ * Mass reinjection (the reading adopted for the method Sec. 2 cites): the
+ * droplet component's populations at the nodes with phi > 0 are multiplied
+ * by one factor k so that the component's total mass becomes target (> 0);
+ * *factor (may be NULL) receives k.  float64 and float32 storage only
+ * (LBM_EINVAL for 16-bit deviations, or without a droplet phase).
+ * Synchronises.
+ */
+int lbm_reinject_mass(lbm_ctx* ctx, double target, double* factor);
+
 /* Step counter n of the next step (the number of steps taken so far). */
 int lbm_get_step(lbm_ctx* ctx, int64_t* step);
 

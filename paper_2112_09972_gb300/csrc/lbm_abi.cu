@@ -523,6 +523,55 @@ int lbm_components(lbm_ctx* c, double threshold, int64_t min_nodes, int32_t* cou
     return sync_and_check(c);
 }
 
+int lbm_surface_deformation(lbm_ctx* c, double* D_lbm, double* area, double* volume) {
+    if (!c || !D_lbm) return LBM_EINVAL;
+    int st = set_device(c);
+    if (st || (st = lazy_init(c))) return st;
+    const long long N = (long long)c->box[0] * c->box[1] * c->box[2];
+    double* phi = nullptr;
+    LBM_TRY(cudaMallocAsync(&phi, sizeof(double) * N, c->stream));
+    cudaError_t e = launch_surface_stats(c->prec, c->f[c->cur], c->L, phi, c->d_partials, c->red_blocks, c->d_result,
+                                         c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->h_result, c->d_result, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(phi, c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if ((st = sync_and_check(c))) return st;
+    const double sum = c->h_result[0], lo = c->h_result[1], hi = c->h_result[2], grad = c->h_result[3];
+    const double span = hi - lo;
+    if (!(span > 0.0)) {  // a uniform state has no interface
+        *D_lbm = 0.0;
+        if (area) *area = 0.0;
+        if (volume) *volume = 0.0;
+        return LBM_OK;
+    }
+    // Eq. 17: Omega = sum |grad phi| / span (co-area), V = sum (phi - min) / span
+    const double A = grad / span, V = (sum - (double)N * lo) / span;
+    const double A0 = std::cbrt(36.0 * M_PI * V * V);
+    *D_lbm = std::sqrt(std::max(0.0, 1.0 - A0 / A));
+    if (area) *area = A;
+    if (volume) *volume = V;
+    return LBM_OK;
+}
+
+int lbm_reinject_mass(lbm_ctx* c, double target, double* factor) {
+    if (!c || !(target > 0.0) || !std::isfinite(target)) return LBM_EINVAL;
+    if (is_dev(c->prec)) return LBM_EINVAL;
+    int st = set_device(c);
+    if (st || (st = lazy_init(c))) return st;
+    LBM_TRY(launch_mass_split(c->prec, c->f[c->cur], c->L, c->d_partials, c->red_blocks, c->d_result, c->stream));
+    LBM_TRY(cudaMemcpyAsync(c->h_result, c->d_result, sizeof(double) * 2, cudaMemcpyDeviceToHost, c->stream));
+    if ((st = sync_and_check(c))) return st;
+    const double m_in = c->h_result[0], m_out = c->h_result[1];
+    if (!(m_in > 0.0)) return LBM_EINVAL;  // no droplet phase to rescale
+    const double k = (target - m_out) / m_in;
+    if (!(k > 0.0) || !std::isfinite(k)) return LBM_EINVAL;
+    LBM_TRY(launch_reinject(c->prec, c->f[c->cur], c->L, k, c->stream));
+    LBM_TRY(launch_centre(c->prec, c->f[c->cur], c->L, c->centre, c->stream));
+    if (factor) *factor = k;
+    return sync_and_check(c);
+}
+
 int lbm_get_step(lbm_ctx* c, int64_t* step) {
     if (!c || !step) return LBM_EINVAL;
     *step = c->step;

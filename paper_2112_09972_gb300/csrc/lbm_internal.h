@@ -142,6 +142,13 @@ cudaError_t launch_pack(int prec, const void* f, const Layout& L, const Model& m
 // propagation sweep (sets *changed), component sizes of the roots (first cap).
 cudaError_t launch_cc_init(int prec, const void* f, const Layout& L, double threshold, int* label, cudaStream_t s);
 cudaError_t launch_cc_sweep(const Layout& L, int periodic, int* label, int* changed, cudaStream_t s);
+// Eq. 17 statistics of phi: {sum phi, min, max, sum |grad phi|}; mass of A
+// split at phi = 0; droplet-component scaling at phi > 0 (fp64 / fp32 only).
+cudaError_t launch_surface_stats(int prec, const void* f, const Layout& L, double* phi, double* partials, int nblocks,
+                                 double* out, cudaStream_t s);
+cudaError_t launch_mass_split(int prec, const void* f, const Layout& L, double* partials, int nblocks, double* out,
+                              cudaStream_t s);
+cudaError_t launch_reinject(int prec, void* f, const Layout& L, double k, cudaStream_t s);
 cudaError_t launch_cc_sizes(const Layout& L, const int* label, int* size, int* count, long long* out, int cap,
                             cudaStream_t s);
 // scratch: 2 N floats (16-bit deviation storage only; may be NULL otherwise)

@@ -366,6 +366,117 @@ __global__ void k_cc_roots(Layout L, const int* __restrict__ label, const int* _
     if (k < cap) out[k] = size[n];
 }
 
+// ---- surface-area deformation (Eq. 17) and mass reinjection ----
+
+// phi of every fluid node into phi[n] (n = (z Ly + y) Lx + x) and per-block
+// {sum phi, min phi, max phi}.
+template <typename S>
+__global__ void __launch_bounds__(kRedThreads) k_phi(const S* __restrict__ f, Layout L, double* __restrict__ phi,
+                                                     double* __restrict__ partials) {
+    __shared__ double red[3][kRedThreads / 32];
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    double sum = 0.0, lo = 1e300, hi = -1e300;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
+        double ra, rb;
+        node_rho(f, L, x, y, z, ra, rb);
+        const double p = (ra - rb) / (ra + rb);
+        phi[n] = p;
+        sum += p;
+        lo = fmin(lo, p);
+        hi = fmax(hi, p);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        sum += __shfl_down_sync(0xffffffffu, sum, o);
+        lo = fmin(lo, __shfl_down_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_down_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) { red[0][warp] = sum; red[1][warp] = lo; red[2][warp] = hi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kRedThreads / 32; ++w) {
+            red[0][0] += red[0][w];
+            red[1][0] = fmin(red[1][0], red[1][w]);
+            red[2][0] = fmax(red[2][0], red[2][w]);
+        }
+        double* out = partials + 4LL * blockIdx.x;
+        out[0] = red[0][0]; out[1] = red[1][0]; out[2] = red[2][0];
+    }
+}
+
+// Per-block sum of |grad phi| (central differences) over interior nodes into partials[4 b + 3].
+__global__ void __launch_bounds__(kRedThreads) k_grad_phi(Layout L, const double* __restrict__ phi,
+                                                          double* __restrict__ partials) {
+    double v[1] = {0.0};
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const long long sx = 1, sy = L.Lx, sz = (long long)L.Lx * L.Ly;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
+        if (x < 1 || x > L.Lx - 2 || y < 1 || y > L.Ly - 2 || z < 1 || z > L.Lz - 2) continue;
+        const double gx = 0.5 * (phi[n + sx] - phi[n - sx]);
+        const double gy = 0.5 * (phi[n + sy] - phi[n - sy]);
+        const double gz = 0.5 * (phi[n + sz] - phi[n - sz]);
+        v[0] += sqrt(gx * gx + gy * gy + gz * gz);
+    }
+    double out[1];
+    block_sum<1>(v, out);
+    if (threadIdx.x == 0) partials[4LL * blockIdx.x + 3] = out[0];
+}
+
+// Block order reduction of the partials: {sum phi, min, max, sum |grad phi|}.
+__global__ void k_phi_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double sum = 0.0, lo = 1e300, hi = -1e300, g = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        const double* p = partials + 4LL * b;
+        sum += p[0];
+        lo = fmin(lo, p[1]);
+        hi = fmax(hi, p[2]);
+        g += p[3];
+    }
+    out[0] = sum; out[1] = lo; out[2] = hi; out[3] = g;
+}
+
+// Per-block {mass of A where phi > 0, mass of A elsewhere}.
+template <typename S>
+__global__ void __launch_bounds__(kRedThreads) k_mass_split(const S* __restrict__ f, Layout L,
+                                                            double* __restrict__ partials) {
+    double v[2] = {0.0, 0.0};
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
+        double ra, rb;
+        node_rho(f, L, x, y, z, ra, rb);
+        v[(ra - rb) / (ra + rb) > 0.0 ? 0 : 1] += ra;
+    }
+    block_sum<2>(v, partials + 2LL * blockIdx.x);
+}
+
+__global__ void k_mass_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < nblocks; ++k) { a += partials[2LL * k]; b += partials[2LL * k + 1]; }
+    out[0] = a; out[1] = b;
+}
+
+// f_A,i *= k at the nodes where phi > 0 (phi of the populations before scaling).
+template <typename S>
+__global__ void k_reinject(S* __restrict__ f, Layout L, double k) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int x = (int)(n % L.Lx), y = (int)((n / L.Lx) % L.Ly), z = (int)(n / ((long long)L.Lx * L.Ly));
+    double ra, rb;
+    node_rho(f, L, x, y, z, ra, rb);
+    if (!((ra - rb) / (ra + rb) > 0.0)) return;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        S* q = f + L.at(0, i, x, y, z);
+        *q = (S)((double)*q * k);
+    }
+}
+
 }  // namespace
 
 int moments_blocks(const Layout& L, int num_sms) {
@@ -465,6 +576,42 @@ cudaError_t launch_cc_sizes(const Layout& L, const int* label, int* size, int* c
     const unsigned blocks = (unsigned)((N + 255) / 256);
     k_cc_sizes<<<blocks, 256, 0, s>>>(L, label, size);
     k_cc_roots<<<blocks, 256, 0, s>>>(L, label, size, count, out, cap);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmgb
+
+namespace lbmgb {
+
+// out[0..3] = {sum phi, min phi, max phi, sum |grad phi| over interior nodes};
+// scratch: N doubles (phi) and 4 nblocks doubles.
+cudaError_t launch_surface_stats(int prec, const void* f, const Layout& L, double* phi, double* partials, int nblocks,
+                                 double* out, cudaStream_t s) {
+    if (prec == kFP64) k_phi<double><<<nblocks, kRedThreads, 0, s>>>((const double*)f, L, phi, partials);
+    else if (prec == kFP32) k_phi<float><<<nblocks, kRedThreads, 0, s>>>((const float*)f, L, phi, partials);
+    else if (prec == kFP16Dev) k_phi<Dev<__half>><<<nblocks, kRedThreads, 0, s>>>((const Dev<__half>*)f, L, phi, partials);
+    else k_phi<Dev<__nv_bfloat16>><<<nblocks, kRedThreads, 0, s>>>((const Dev<__nv_bfloat16>*)f, L, phi, partials);
+    k_grad_phi<<<nblocks, kRedThreads, 0, s>>>(L, phi, partials);
+    k_phi_final<<<1, 32, 0, s>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+// out[0..1] = {mass of A where phi > 0, elsewhere}; partials: 2 nblocks doubles.
+cudaError_t launch_mass_split(int prec, const void* f, const Layout& L, double* partials, int nblocks, double* out,
+                              cudaStream_t s) {
+    if (prec == kFP64) k_mass_split<double><<<nblocks, kRedThreads, 0, s>>>((const double*)f, L, partials);
+    else if (prec == kFP32) k_mass_split<float><<<nblocks, kRedThreads, 0, s>>>((const float*)f, L, partials);
+    else return cudaErrorInvalidValue;
+    k_mass_final<<<1, 32, 0, s>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reinject(int prec, void* f, const Layout& L, double k, cudaStream_t s) {
+    const long long N = (long long)L.Lx * L.Ly * L.Lz;
+    const unsigned blocks = (unsigned)((N + 255) / 256);
+    if (prec == kFP64) k_reinject<double><<<blocks, 256, 0, s>>>((double*)f, L, k);
+    else if (prec == kFP32) k_reinject<float><<<blocks, 256, 0, s>>>((float*)f, L, k);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -35,7 +35,8 @@ ABI_FUNCTIONS = [
     "lbm_batch_destroy", "lbm_batch_moments",
     "lbm_mlp_create", "lbm_mlp_set_normalisation", "lbm_mlp_param_count", "lbm_mlp_get_params",
     "lbm_mlp_set_params", "lbm_mlp_forward", "lbm_mlp_deformation", "lbm_mlp_gradients", "lbm_mlp_train_step",
-    "lbm_mlp_sync", "lbm_mlp_destroy", "lbm_mm_integrate", "lbm_components",
+    "lbm_mlp_sync", "lbm_mlp_destroy", "lbm_mm_integrate", "lbm_components", "lbm_surface_deformation",
+    "lbm_reinject_mass",
 ]
 
 
@@ -125,6 +126,8 @@ def load_library(path=LIB_PATH):
         "lbm_mlp_train_step": (ctypes.c_int, [vp, vp, vp, ctypes.c_int64, ctypes.c_float, _DP]),
         "lbm_mlp_sync": (ctypes.c_int, [vp]),
         "lbm_mlp_destroy": (None, [vp]),
+        "lbm_surface_deformation": (ctypes.c_int, [vp, _DP, _DP, _DP]),
+        "lbm_reinject_mass": (ctypes.c_int, [vp, ctypes.c_double, _DP]),
         "lbm_components": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int64, _I32P, _I64P, ctypes.c_int32]),
         "lbm_mm_integrate": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp, vp]),
@@ -291,6 +294,19 @@ class DropletLBM:
         _check(self._lib.lbm_components(self._h, float(threshold), int(min_nodes), ctypes.byref(cnt),
                                         sizes.ctypes.data_as(_I64P), int(max_sizes)), "lbm_components")
         return cnt.value, sizes[:max_sizes]
+
+    def surface_deformation(self):
+        """(D_LBM, area, volume) of Eq. 17 (lbm_surface_deformation)."""
+        v = np.zeros(3)
+        _check(self._lib.lbm_surface_deformation(self._h, _dptr(v[0:1]), _dptr(v[1:2]), _dptr(v[2:3])),
+               "lbm_surface_deformation")
+        return float(v[0]), float(v[1]), float(v[2])
+
+    def reinject_mass(self, target):
+        """Rescale the droplet component inside phi > 0 to total mass target; returns the factor."""
+        k = np.zeros(1)
+        _check(self._lib.lbm_reinject_mass(self._h, float(target), _dptr(k)), "lbm_reinject_mass")
+        return float(k[0])
 
     def step_count(self):
         s = ctypes.c_int64()
