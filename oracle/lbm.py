@@ -39,6 +39,8 @@ def _load():
         lib.orc_set_threads.argtypes = [ctypes.c_int]
         lib.orc_set_storage.restype = ctypes.c_int
         lib.orc_set_storage.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        lib.orc_set_mrt.argtypes = [ctypes.c_void_p, ctypes.c_int, _DP]
+        lib.orc_moment_basis.argtypes = [_DP]
         lib.orc_round.restype = ctypes.c_double
         lib.orc_round.argtypes = [ctypes.c_int, ctypes.c_double]
         _lib = lib
@@ -58,6 +60,17 @@ def round_to(fmt: str, x: float) -> float:
     """x rounded to nearest-even in ``fmt`` ("float32", "binary16", "bfloat16"):
     the rounding of the oracle's storage model."""
     return float(_load().orc_round(ROUND_FORMATS[fmt], float(x)))
+
+
+# d'Humieres et al. (2002) rates for (s_e, s_eps, s_q, s_pi, s_m)
+MRT_RATES = (1.19, 1.4, 1.2, 1.4, 1.98)
+
+
+def moment_basis():
+    """The oracle's D3Q19 moment basis M [19, 19] (row k, direction i)."""
+    M = np.zeros(19 * 19)
+    _load().orc_moment_basis(_ptr(M))
+    return M.reshape(19, 19)
 
 
 def set_threads(n: int) -> int:
@@ -112,6 +125,9 @@ class OracleLBM:
     mass"), recomputed from the stored populations before every step;
     ``frame="box"`` measures it from the box centre.
 
+    ``mrt`` (rates s_e, s_eps, s_q, s_pi, s_m, e.g. ``MRT_RATES``) selects
+    the multi-relaxation-time collision of ``lbm_oracle.cpp`` instead of BGK.
+
     ``storage`` selects the storage model of ``lbm_oracle.cpp``: "exact"
     (full precision, the paper's method), or "fp16dev" / "bf16dev": after
     every state change the populations are replaced by the values 16-bit
@@ -120,7 +136,7 @@ class OracleLBM:
     population closing each node's mass).
     """
 
-    def __init__(self, box, tau, G, rho_b, periodic=False, frame="droplet", storage="exact"):
+    def __init__(self, box, tau, G, rho_b, periodic=False, frame="droplet", storage="exact", mrt=None):
         self.box = tuple(int(v) for v in box)
         self.nodes = self.box[0] * self.box[1] * self.box[2]
         self.tau = (float(tau[0]), float(tau[1]))
@@ -137,6 +153,11 @@ class OracleLBM:
         self.storage = storage
         if self._lib.orc_set_storage(self._h, STORAGE[storage]) != 0:
             raise ValueError(storage)
+        # mrt: None for BGK, or the rates (s_e, s_eps, s_q, s_pi, s_m) of the MRT operator
+        self.mrt = None if mrt is None else tuple(float(v) for v in mrt)
+        if self.mrt is not None:
+            r = np.ascontiguousarray(self.mrt, dtype=np.float64)
+            self._lib.orc_set_mrt(self._h, 1, _ptr(r))
         self.step_count = 0
 
     def __del__(self):

@@ -34,6 +34,16 @@
 // an addition of the library, not of the paper: the paper stores populations
 // at full precision.
 //
+// Optional MRT collision (orc_set_mrt), the multi-relaxation-time operator
+// Sec. 2 names: g* = g - M^-1 S M (g - g^eq), M the D3Q19 moment basis of
+// d'Humieres et al. (2002) (orthogonal rows, polynomials in c: density,
+// energy, energy square, momentum, energy flux, stress and its
+// higher-order partners, third-order moments), S = diag of the relaxation
+// rates.  The stress moments relax at 1/tau_s (Eq. 10); the momentum moments
+// also at 1/tau_s, so that the velocity shift of the forcing still puts F^s
+// into the fluid; the other rates are parameters.  With every rate 1/tau_s it
+// is the BGK operator.
+//
 // Build: g++ -O2 -ffp-contract=off -fopenmp -shared -fPIC (see build.py).
 // Loops over nodes run in parallel over z planes; every node's result is
 // independent of the thread count.  The moment and checksum sums are serial
@@ -69,6 +79,45 @@ double equilibrium(int i, double rho, const double u[3]) {
     return rho * weight(i) * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
 }
 
+// Row k of the D3Q19 moment basis of d'Humieres et al. (2002) at velocity c:
+// 0 rho, 1 e, 2 eps, 3 j_x, 4 q_x, 5 j_y, 6 q_y, 7 j_z, 8 q_z, 9 3p_xx,
+// 10 3pi_xx, 11 p_ww, 12 pi_ww, 13 p_xy, 14 p_yz, 15 p_xz, 16 m_x, 17 m_y, 18 m_z.
+double moment_row(int k, int cx, int cy, int cz) {
+    const double c2 = cx * cx + cy * cy + cz * cz;
+    switch (k) {
+        case 0: return 1.0;
+        case 1: return 19.0 * c2 - 30.0;
+        case 2: return (21.0 * c2 * c2 - 53.0 * c2 + 24.0) / 2.0;
+        case 3: return cx;
+        case 4: return (5.0 * c2 - 9.0) * cx;
+        case 5: return cy;
+        case 6: return (5.0 * c2 - 9.0) * cy;
+        case 7: return cz;
+        case 8: return (5.0 * c2 - 9.0) * cz;
+        case 9: return 3.0 * cx * cx - c2;
+        case 10: return (3.0 * c2 - 5.0) * (3.0 * cx * cx - c2);
+        case 11: return cy * cy - cz * cz;
+        case 12: return (3.0 * c2 - 5.0) * (cy * cy - cz * cz);
+        case 13: return cx * cy;
+        case 14: return cy * cz;
+        case 15: return cx * cz;
+        case 16: return (cy * cy - cz * cz) * cx;
+        case 17: return (cz * cz - cx * cx) * cy;
+        default: return (cx * cx - cy * cy) * cz;
+    }
+}
+
+// Relaxation rate of moment k for component relaxation time tau.
+double moment_rate(int k, double tau, const double* r) {
+    if (k == 0 || k == 3 || k == 5 || k == 7) return 1.0 / tau;  // density (any rate) and momentum
+    if (k == 9 || k == 11 || k == 13 || k == 14 || k == 15) return 1.0 / tau;  // stress: viscosity, Eq. 10
+    if (k == 1) return r[0];
+    if (k == 2) return r[1];
+    if (k == 4 || k == 6 || k == 8) return r[2];
+    if (k == 10 || k == 12) return r[3];
+    return r[4];  // 16, 17, 18
+}
+
 // x rounded to nearest-even in a binary format with p significant bits and
 // smallest normal exponent emin (gradual underflow below it); the values
 // rounded here are far below every format's largest finite number.
@@ -89,6 +138,8 @@ struct Oracle {
     int L[3];
     bool periodic;
     int storage = 0;  // 0 full precision, 1 binary16 deviations, 2 bfloat16 deviations
+    bool mrt = false;
+    double mrt_rates[5] = {0, 0, 0, 0, 0};  // s_e, s_eps, s_q, s_pi, s_m
     double tau[2];
     double G;
     double rho_b[2];
@@ -197,6 +248,21 @@ int orc_set_storage(void* h, int mode) {
     o->storage = mode;
     o->apply_storage();
     return 0;
+}
+
+// MRT collision: enable != 0 with rates[5] = {s_e, s_eps, s_q, s_pi, s_m};
+// enable == 0 returns to BGK.
+void orc_set_mrt(void* h, int enable, const double* rates) {
+    Oracle* o = (Oracle*)h;
+    o->mrt = enable != 0;
+    if (rates)
+        for (int k = 0; k < 5; ++k) o->mrt_rates[k] = rates[k];
+}
+
+// The moment basis, exported for its tests: M[19][19], M[k][i] = row k at c_i.
+void orc_moment_basis(double* M) {
+    for (int k = 0; k < 19; ++k)
+        for (int i = 0; i < 19; ++i) M[19 * k + i] = moment_row(k, CX[i], CY[i], CZ[i]);
 }
 
 // The rounding of the storage model, exported for its tests:
@@ -360,10 +426,31 @@ void orc_step(void* h, const double* A, const double* centre, double* flux_in, d
                 for (int s = 0; s < 2; ++s) {
                     double ueq[3];
                     for (int a = 0; a < 3; ++a) ueq[a] = ucommon[a] + o->tau[s] * F[s][a] / rho_s[s];
-                    for (int i = 0; i < 19; ++i) {
-                        double f = o->fstream[o->pidx(s, i, n)];
-                        double geq = equilibrium(i, rho_s[s], ueq);
-                        o->fpost[o->pidx(s, i, n)] = f - (f - geq) / o->tau[s];
+                    if (!o->mrt) {
+                        for (int i = 0; i < 19; ++i) {
+                            double f = o->fstream[o->pidx(s, i, n)];
+                            double geq = equilibrium(i, rho_s[s], ueq);
+                            o->fpost[o->pidx(s, i, n)] = f - (f - geq) / o->tau[s];
+                        }
+                    } else {
+                        // g* = g - M^T D^-1 S M (g - g_eq), D = diag of the row norms
+                        double dev[19], rel[19];
+                        for (int i = 0; i < 19; ++i)
+                            dev[i] = o->fstream[o->pidx(s, i, n)] - equilibrium(i, rho_s[s], ueq);
+                        for (int k = 0; k < 19; ++k) {
+                            double mk = 0.0, norm = 0.0;
+                            for (int i = 0; i < 19; ++i) {
+                                const double e = moment_row(k, CX[i], CY[i], CZ[i]);
+                                mk += e * dev[i];
+                                norm += e * e;
+                            }
+                            rel[k] = moment_rate(k, o->tau[s], o->mrt_rates) * mk / norm;
+                        }
+                        for (int i = 0; i < 19; ++i) {
+                            double back = 0.0;
+                            for (int k = 0; k < 19; ++k) back += moment_row(k, CX[i], CY[i], CZ[i]) * rel[k];
+                            o->fpost[o->pidx(s, i, n)] = o->fstream[o->pidx(s, i, n)] - back;
+                        }
                     }
                 }
             }
