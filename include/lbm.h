@@ -93,6 +93,15 @@ typedef enum {
     LBM_FRAME_BOX = 1
 } lbm_frame;
 
+typedef enum {
+    LBM_COLLISION_BGK = 0, /* single relaxation time 1/tau per component (Eqs. 9, 10) */
+    /* multi-relaxation-time collision (Sec. 2), d'Humieres et al. (2002)
+       D3Q19 moment basis: g* = g - M^-1 S M (g - g_eq); stress and momentum
+       moments relax at 1/tau (Eq. 10; the velocity-shift forcing), the others
+       at opts->mrt_rates.  Runs on the generic kernel. */
+    LBM_COLLISION_MRT = 1
+} lbm_collision;
+
 typedef struct {
     int32_t precision;   /* lbm_precision, default LBM_FP32 */
     int32_t bc;          /* lbm_bc, default LBM_BC_GHOST_LINEAR */
@@ -112,6 +121,11 @@ typedef struct {
                             time from L2), 2 whole pulled rows staged in shared
                             memory by bulk copies (cp.async.bulk, one read);
                             0: automatic */
+    int32_t collision;   /* lbm_collision, default LBM_COLLISION_BGK */
+    double mrt_rates[5]; /* MRT rates of the energy, energy-square, energy-flux,
+                            stress-partner and third-order moments (s_e, s_eps,
+                            s_q, s_pi, s_m), each in (0, 2); <= 0: 1.19, 1.4,
+                            1.2, 1.4, 1.98 */
 } lbm_opts;
 
 /* Fill *opts with the defaults above. */

@@ -217,6 +217,12 @@ int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[
     if (o.bc != LBM_BC_GHOST_LINEAR && o.bc != LBM_BC_PERIODIC_TEST) return LBM_EINVAL;
     if (o.frame != LBM_FRAME_DROPLET && o.frame != LBM_FRAME_BOX) return LBM_EINVAL;
     if (o.row_variant < 0 || o.row_variant > 2) return LBM_EINVAL;
+    if (o.collision != LBM_COLLISION_BGK && o.collision != LBM_COLLISION_MRT) return LBM_EINVAL;
+    double mrt_rates[5] = {1.19, 1.4, 1.2, 1.4, 1.98};  // d'Humieres et al. (2002)
+    for (int k = 0; k < 5; ++k) {
+        if (o.mrt_rates[k] > 0.0) mrt_rates[k] = o.mrt_rates[k];
+        if (!(mrt_rates[k] > 0.0 && mrt_rates[k] < 2.0)) return LBM_EINVAL;
+    }
     for (int a = 0; a < 3; ++a)
         if (box[a] < 4 || box[a] > 4096) return LBM_EINVAL;
     const int mn = std::min(box[0], std::min(box[1], box[2]));
@@ -251,11 +257,13 @@ int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[
     c->model.periodic = o.bc == LBM_BC_PERIODIC_TEST;
     c->model.mach2 = mach * mach / 3.0;
     c->model.droplet_frame = o.frame == LBM_FRAME_DROPLET;
+    c->model.mrt = o.collision == LBM_COLLISION_MRT;
+    for (int k = 0; k < 5; ++k) c->model.mrt_rates[k] = mrt_rates[k];
     c->prec = o.precision;
     c->elem = elem_bytes_of(c->prec);
     c->L = make_layout(box[0], box[1], box[2], c->prec);
-    c->shape = choose_shape(c->L, c->prec, o.bc == LBM_BC_PERIODIC_TEST, o.tile_y, o.z_chunk, o.row_variant,
-                            c->num_sms);
+    c->shape = choose_shape(c->L, c->prec, o.bc == LBM_BC_PERIODIC_TEST, c->model.mrt, o.tile_y, o.z_chunk,
+                            o.row_variant, c->num_sms);
     c->cur = 0;
     c->stream = (cudaStream_t)o.cuda_stream;
     c->own_stream = false;

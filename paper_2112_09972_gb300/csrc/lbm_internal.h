@@ -69,6 +69,8 @@ struct Model {
     int periodic;      // 1: periodic test mode, no ghosts
     double mach2;      // guard on |u_ghost|^2 (lattice units)
     int droplet_frame; // 1: ghost flow A (x - x_c), x_c the droplet's centre of mass
+    int mrt;           // 1: MRT collision (generic kernel) with the free rates below
+    double mrt_rates[5];  // s_e, s_eps, s_q, s_pi, s_m
 };
 
 // Per-CTA partial sums {sum w, sum w x, sum w y, sum w z} of the droplet
@@ -100,8 +102,9 @@ struct Shape {
 };
 
 // ---- launchers (lbm_step.cu) ----
-// staged_req: 1 direct loads, 2 staged, 0 automatic
-Shape choose_shape(const Layout& L, int prec, int periodic, int ty_req, int zchunk_req, int staged_req,
+// staged_req: 1 direct loads, 2 staged, 0 automatic; mrt: the MRT collision
+// (generic kernel only)
+Shape choose_shape(const Layout& L, int prec, int periodic, int mrt, int ty_req, int zchunk_req, int staged_req,
                    int num_sms);
 cudaError_t launch_init(int prec, void* f, const Layout& L, double R, double xi, double rho_hi, double rho_lo,
                         Grad A0, cudaStream_t s);

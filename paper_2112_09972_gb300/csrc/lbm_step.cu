@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, Mode
     else ghost_node<S, C>(f, L, m, A, xc, yc, zc, x, y, z, d_err);
 }
 
-template <typename S, typename C, bool PER, int MAXT>
+template <typename S, typename C, bool PER, bool MRT, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, Layout L,
                                                           ModelC<C> m, int TX, int TY, int zchunk, CentreParts cp,
                                                           int* __restrict__ d_err) {
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_stream_collide(const S* __restrict_
     const int zc0 = blockIdx.z * zchunk;
     const int zc1 = min(zc0 + zchunk, L.Lz);
     C cm[4] = {C(0), C(0), C(0), C(0)};
-    tile_march<S, C, PER>(src, dst, L, m, TX, TY, blockIdx.x * TX, blockIdx.y * TY, zc0, zc1,
+    tile_march<S, C, PER, MRT>(src, dst, L, m, TX, TY, blockIdx.x * TX, blockIdx.y * TY, zc0, zc1,
                           reinterpret_cast<C*>(smem_raw), d_err, cm);
     double cmd[4] = {(double)cm[0], (double)cm[1], (double)cm[2], (double)cm[3]};
     __syncthreads();  // the ring is reused as reduction scratch
@@ -195,7 +195,16 @@ ModelC<C> model_c(const Model& m) {
         r.rho_b[s] = (C)m.rho_b[s];
     }
     r.G = (C)m.G;
+    for (int k = 0; k < 5; ++k) r.mrt[k] = (C)m.mrt_rates[k];
     return r;
+}
+
+template <typename S, typename C, bool PER, bool MRT, int MAXT>
+void stream_collide_launch(const void* src, void* dst, const Layout& L, const ModelC<C>& mc, const Shape& sh,
+                           CentreParts cp, int* d_err, cudaStream_t s) {
+    auto k = k_stream_collide<S, C, PER, MRT, MAXT>;
+    if (sh.smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+    k<<<sh.grid, sh.threads, sh.smem, s>>>((const S*)src, (S*)dst, L, mc, sh.tx, sh.ty, sh.zchunk, cp, d_err);
 }
 
 template <typename S, typename C, int MAXT>
@@ -203,13 +212,11 @@ cudaError_t stream_collide_t(const void* src, void* dst, const Layout& L, const 
                              CentreParts cp, int* d_err, cudaStream_t s) {
     const ModelC<C> mc = model_c<C>(m);
     if (m.periodic) {
-        auto k = k_stream_collide<S, C, true, MAXT>;
-        if (sh.smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
-        k<<<sh.grid, sh.threads, sh.smem, s>>>((const S*)src, (S*)dst, L, mc, sh.tx, sh.ty, sh.zchunk, cp, d_err);
+        if (m.mrt) stream_collide_launch<S, C, true, true, MAXT>(src, dst, L, mc, sh, cp, d_err, s);
+        else stream_collide_launch<S, C, true, false, MAXT>(src, dst, L, mc, sh, cp, d_err, s);
     } else {
-        auto k = k_stream_collide<S, C, false, MAXT>;
-        if (sh.smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
-        k<<<sh.grid, sh.threads, sh.smem, s>>>((const S*)src, (S*)dst, L, mc, sh.tx, sh.ty, sh.zchunk, cp, d_err);
+        if (m.mrt) stream_collide_launch<S, C, false, true, MAXT>(src, dst, L, mc, sh, cp, d_err, s);
+        else stream_collide_launch<S, C, false, false, MAXT>(src, dst, L, mc, sh, cp, d_err, s);
     }
     return cudaGetLastError();
 }
@@ -235,12 +242,12 @@ Layout make_layout(int Lx, int Ly, int Lz, int prec) {
     return L;
 }
 
-Shape choose_shape(const Layout& L, int prec, int periodic, int ty_req, int zchunk_req, int staged_req,
+Shape choose_shape(const Layout& L, int prec, int periodic, int mrt, int ty_req, int zchunk_req, int staged_req,
                    int num_sms) {
     Shape sh;
     sh.rows = 0;
     sh.staged = 0;
-    if (ty_req <= 0 && rows_kernel_applies(L, prec, periodic)) {
+    if (ty_req <= 0 && !mrt && rows_kernel_applies(L, prec, periodic)) {
         // one CTA per row
         const bool staged = staged_req == 2;
         const int resident = rows_kernel_resident_ctas(L, prec, staged);

@@ -16,6 +16,7 @@ namespace {
 template <typename C>
 struct ModelC {
     C inv_tau[2], tau[2], G, rho_b[2];
+    C mrt[5];  // MRT free rates s_e, s_eps, s_q, s_pi, s_m (used by MRT instantiations)
 };
 
 template <typename S, typename C, bool PER>
@@ -154,7 +155,7 @@ __device__ void centre_epilogue(double (&cm)[4], CentreParts cp, double* scratch
 // TX * TY (the extra threads only help with the halo); every thread must
 // call this (it synchronises the block).  Returns the thread's partial
 // droplet moments {sum w, sum w x, sum w y, sum w z} of the written state.
-template <typename S, typename C, bool PER>
+template <typename S, typename C, bool PER, bool MRT = false>
 __device__ __forceinline__ void tile_march(const S* __restrict__ src, S* __restrict__ dst, const Layout& L,
                                            const ModelC<C>& m, int TX, int TY, int x0, int y0, int zc0, int zc1,
                                            C* ring, int* __restrict__ d_err, C (&cm)[4]) {
@@ -261,15 +262,27 @@ __device__ __forceinline__ void tile_march(const S* __restrict__ src, S* __restr
                 const C uy = up[1] + sh * acc[1 - s][1];
                 const C uz = up[2] + sh * acc[1 - s][2];
                 const C u2x = C(1.5) * (ux * ux + uy * uy + uz * uz);
+                // post-collision populations: BGK, or MRT relaxation of the moments
+                C out[19];
+                if constexpr (MRT) {
+                    C dv[19];
+#pragma unroll
+                    for (int i = 0; i < 19; ++i) dv[i] = fc[s][i] - feq<C>(i, rho[s], ux, uy, uz, u2x);
+                    mrt_relax<C>(fc[s], dv, m.inv_tau[s], m.mrt, out);
+                } else {
+#pragma unroll
+                    for (int i = 1; i < 19; ++i) {
+                        const C f = fc[s][i];
+                        out[i] = f - (f - feq<C>(i, rho[s], ux, uy, uz, u2x)) * m.inv_tau[s];
+                    }
+                }
                 // moving populations; the rest population then closes the
                 // mass balance exactly (sum of outputs = rho), which keeps
                 // fp32 rounding from drifting the interface
                 C others = C(0);
 #pragma unroll
                 for (int i = 1; i < 19; ++i) {
-                    const C f = fc[s][i];
-                    const C g = feq<C>(i, rho[s], ux, uy, uz, u2x);
-                    const C o = f - (f - g) * m.inv_tau[s];
+                    const C o = out[i];
                     if constexpr (is_dev_t<S>::value) {
                         // deviation from w_i times the density of the node
                         // this population streams to (ring plane z + c_iz)

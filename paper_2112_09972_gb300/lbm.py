@@ -54,6 +54,8 @@ class lbm_opts(ctypes.Structure):
         ("z_chunk", ctypes.c_int32),
         ("frame", ctypes.c_int32),
         ("row_variant", ctypes.c_int32),
+        ("collision", ctypes.c_int32),
+        ("mrt_rates", ctypes.c_double * 5),
     ]
 
 
@@ -193,7 +195,8 @@ class DropletLBM:
     """
 
     def __init__(self, box, R, visc, G, precision="fp32", periodic=False, rho_hi=0.0, rho_lo=0.0, xi=0.0,
-                 mach_limit=0.0, stream=None, device=-1, tile_y=0, z_chunk=0, frame="droplet", row_variant=0):
+                 mach_limit=0.0, stream=None, device=-1, tile_y=0, z_chunk=0, frame="droplet", row_variant=0,
+                 mrt=None):
         lib = load_library()
         self._lib = lib
         if isinstance(box, int):
@@ -211,6 +214,12 @@ class DropletLBM:
         o.device = int(device)
         o.tile_y, o.z_chunk = int(tile_y), int(z_chunk)
         o.row_variant = int(row_variant)
+        # mrt: None (BGK), True (MRT, default free rates) or the rates (s_e, s_eps, s_q, s_pi, s_m)
+        if mrt is not None and mrt is not False:
+            o.collision = 1
+            if mrt is not True:
+                for k, v in enumerate(mrt):
+                    o.mrt_rates[k] = float(v)
         o.frame = FRAMES[frame]
         b = (ctypes.c_int32 * 3)(*self.box)
         v = (ctypes.c_double * 2)(float(visc[0]), float(visc[1]))
