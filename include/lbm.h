@@ -456,7 +456,16 @@ int lbm_mlp_gradients(lbm_mlp* mlp, const float* x, const float* t, int64_t n, d
  * loss (host) NULL keeps the call asynchronous. */
 int lbm_mlp_train_step(lbm_mlp* mlp, const float* x, const float* t, int64_t n, float lr, double* loss);
 
+/* Wait for the network's stream; LBM_ETIMEOUT if a bounded tensor-core wait gave up. */
 int lbm_mlp_sync(lbm_mlp* mlp);
+
+/* Matrix products: path 0 (default) runs tcgen05 tensor cores on every
+ * product whose M and N are multiples of 128, K of 64, and whose operand,
+ * output, bias and mask rows start on 16-byte boundaries (inputs x that are
+ * not 16-byte aligned still run, through the scalar normalisation); warp-level
+ * mma.sync takes the rest.  Path 1 runs mma.sync only.  Both accumulate in
+ * float32.  LBM_EINVAL for a path other than 0 or 1. */
+int lbm_mlp_set_tensor_path(lbm_mlp* mlp, int32_t path);
 void lbm_mlp_destroy(lbm_mlp* mlp);
 
 #ifdef __cplusplus

@@ -35,7 +35,7 @@ ABI_FUNCTIONS = [
     "lbm_batch_destroy", "lbm_batch_moments",
     "lbm_mlp_create", "lbm_mlp_set_normalisation", "lbm_mlp_param_count", "lbm_mlp_get_params",
     "lbm_mlp_set_params", "lbm_mlp_forward", "lbm_mlp_deformation", "lbm_mlp_gradients", "lbm_mlp_train_step",
-    "lbm_mlp_sync", "lbm_mlp_destroy", "lbm_mm_integrate", "lbm_components", "lbm_surface_deformation",
+    "lbm_mlp_sync", "lbm_mlp_destroy", "lbm_mlp_set_tensor_path", "lbm_mm_integrate", "lbm_components", "lbm_surface_deformation",
     "lbm_reinject_mass",
 ]
 
@@ -128,6 +128,7 @@ def load_library(path=LIB_PATH):
         "lbm_mlp_train_step": (ctypes.c_int, [vp, vp, vp, ctypes.c_int64, ctypes.c_float, _DP]),
         "lbm_mlp_sync": (ctypes.c_int, [vp]),
         "lbm_mlp_destroy": (None, [vp]),
+        "lbm_mlp_set_tensor_path": (ctypes.c_int, [vp, ctypes.c_int32]),
         "lbm_surface_deformation": (ctypes.c_int, [vp, _DP, _DP, _DP]),
         "lbm_reinject_mass": (ctypes.c_int, [vp, ctypes.c_double, _DP]),
         "lbm_components": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int64, _I32P, _I64P, ctypes.c_int32]),
@@ -521,6 +522,10 @@ class MLP:
 
     def sync(self):
         _check(self._lib.lbm_mlp_sync(self._h), "lbm_mlp_sync")
+
+    def set_tensor_path(self, path):
+        """0: tcgen05 tensor cores where the shape allows (default); 1: mma.sync only."""
+        _check(self._lib.lbm_mlp_set_tensor_path(self._h, int(path)), "lbm_mlp_set_tensor_path")
 
 
 def mm_integrate(A, tau_d, chi, substeps=10, record_every=1, precision="fp64", want_M=False, stream=None):

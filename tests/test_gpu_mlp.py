@@ -51,7 +51,7 @@ def _setup(n, seed):
     from paper_2112_09972_gb300.lbm import MLP
 
     rng = np.random.default_rng(seed)
-    net = MLP(SIZES, max_batch=256, seed=seed)
+    net = MLP(SIZES, max_batch=max(256, n), seed=seed)
     # non-zero biases, and a normalisation that matters
     p = net.get_params()
     p += rng.normal(0.0, 0.05, p.shape).astype(np.float32)
@@ -86,9 +86,14 @@ def test_forward_matches_float64(built):
     assert np.max(np.abs(yn - rn)) <= 3e-2 * np.max(np.abs(rn))
 
 
-def test_gradients_match_float64(built):
-    n = 128
+@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("n", [128, 4096])
+def test_gradients_match_float64(built, n, path):
+    """n = 4096: the weight gradients (K = n) are cut into K slices whose
+    float32 partials are added in order, on either tensor path, and the bias
+    gradients sum 16 row slices."""
     net, norm, x, t, xd, td = _setup(n, 2)
+    net.set_tensor_path(path)
     loss, g = net.gradients(xd, td)
     cpu = _cpu_model(net, SIZES, norm)
     loss_r, gr = cpu.loss_and_gradients(x, t, rounding=True)
@@ -172,3 +177,34 @@ def test_invalid_shapes_rejected(built):
         MLP((576, 256, 64), max_batch=64)  # more than 32 outputs
     with pytest.raises(LBMError):
         MLP((576, 256, 6), max_batch=100)  # batch not a multiple of 32
+
+
+def test_tcgen05_and_mma_sync_paths_agree(built):
+    """Batch 256: the hidden-layer products (M 256, N 256, K 576 / 256) and the
+    weight gradients (K = 256) run on tcgen05 tensor cores by default and on
+    mma.sync with path 1.  Both accumulate bfloat16 products in float32 in a
+    different order, so a stored bfloat16 activation can round the other way:
+    outputs agree to 1e-2 of their largest magnitude, gradients to 2e-2 in
+    relative L2 norm per layer; a wrong operand layout would miss by O(1)."""
+    import torch
+
+    n = 256
+    net, norm, x, t, xd, td = _setup(n, 4)
+    out = {}
+    for path in (0, 1):
+        net.set_tensor_path(path)
+        y = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+        net.forward(xd, y)
+        net.sync()
+        loss, g = net.gradients(xd, td)
+        out[path] = ((y.cpu().numpy() - norm[2]) * np.asarray(norm[3]), loss, g)
+    y0, l0, g0 = out[0]
+    y1, l1, g1 = out[1]
+    assert np.max(np.abs(y0 - y1)) <= 1e-2 * np.max(np.abs(y1))
+    assert abs(l0 - l1) <= 1e-2 * l1
+    o = 0
+    for d_in, d_out in zip(SIZES[:-1], SIZES[1:]):
+        for size in (d_in * d_out, d_out):
+            a, b = g0[o:o + size], g1[o:o + size]
+            o += size
+            assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b)
