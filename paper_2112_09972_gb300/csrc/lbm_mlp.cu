@@ -24,8 +24,10 @@
 // inputs normalised as (x - x_mean) x_scale, outputs y = y_hat / y_scale +
 // y_mean, loss = mean over samples and outputs of (y_hat - t_hat)^2.
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -189,34 +191,64 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_nt(GemmArgs g) {
 }
 
 // ---------------------------------------------------------------------------
-// The same C = A B^T on the 5th-generation tensor cores (tcgen05): a 128 x 128
-// float32 tile accumulates in tensor memory (TMEM, 128 columns); operands are
-// staged K-major in shared memory in the 128-byte swizzled layout by cp.async;
-// one thread issues tcgen05.mma (kind::f16, bfloat16 inputs, M 128, N 128,
-// K 16) and commits each K chunk to that stage's mbarrier; the four warps then
-// read their 32 TMEM lanes (rows) with tcgen05.ld and apply the epilogue.
-// Requires M and N multiples of 128 and K a multiple of 64.
-constexpr int TC_M = 128, TC_N = 128, TC_K = 64;
-constexpr int kTcThreads = 128;
-constexpr unsigned kTcWaitPolls = 1u << 22;
+// The same C = A B^T on the 5th-generation tensor cores: a persistent kernel,
+// one CTA per SM walking 128 x BN output tiles (BN in {32, 64, 128}; the K
+// slices of a split-K product are tiles too), with three roles:
+//   warp 0    -- one thread loads the A and B tiles of each 64-wide K chunk by
+//                TMA (cp.async.bulk.tensor, 128-byte swizzle) into a ring of
+//                kTcStages stages, counting the bytes on the stage's "full"
+//                mbarrier, once the products of the chunk that used the stage
+//                before have released it (its "empty" mbarrier);
+//   warp 1    -- allocates 256 TMEM columns (two 128-column float32
+//                accumulators); one thread issues tcgen05.mma (kind::f16,
+//                M 128, N BN, K 16) for each chunk, releases the stage with
+//                tcgen05.commit, and commits a finished tile to its
+//                accumulator's "full" mbarrier;
+//   warps 2-5 -- the epilogue: each warp reads its 32 TMEM lanes (rows) with
+//                tcgen05.ld, applies the fused epilogue, stores 16-byte
+//                vectors and hands the accumulator back (its "empty"
+//                mbarrier), while the tensor core fills the other one.
+// Every wait is bounded.  A wait that gives up sets bit 1 of *err and stops
+// every role; before the CTA exits, the copies and products it issued are
+// waited for (bounded) and the tensor memory is released.
+constexpr int TC_M = 128, TC_K = 64;
+constexpr int kTcThreads = 192;
+constexpr int kTcStages = 6;
+constexpr unsigned kTcTileA = TC_M * TC_K * 2;               // 16 KB
+constexpr unsigned kTcStageBytes = 2 * kTcTileA;             // A tile + B tile (BN <= 128 rows)
+constexpr int kTcBars = 2 * kTcStages + 2 + 2 + 1;           // full, empty, acc full, acc empty, drain
+constexpr unsigned kTcSmem = 1024 + kTcStages * kTcStageBytes + 8 * kTcBars + 16;
+constexpr unsigned long long kTcWaitNs = 2000000000ull;  // 2 s per wait
+constexpr unsigned kTcCols = 256;
+
+// Tiles of one product: m_tiles x n_tiles output tiles of 128 x bn, times
+// the K slices.
+struct TcShape {
+    int m_tiles, n_tiles, slices, bn;
+};
 
 __device__ __forceinline__ unsigned tc_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-// Shared-memory matrix descriptor: start address, leading-dimension (K
-// direction) and stride-dimension (M/N direction) byte offsets, no swizzle.
-__device__ __forceinline__ unsigned long long tc_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+// Shared-memory matrix descriptor of a 128-byte swizzled K-major tile: start
+// address, stride between 8-row atoms (SBO), swizzle mode 2 (128 bytes).
+__device__ __forceinline__ unsigned long long tc_desc_sw128(unsigned addr) {
     unsigned long long d = 0;
     d |= (unsigned long long)((addr >> 4) & 0x3FFFu);
-    d |= (unsigned long long)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (unsigned long long)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= 1ull << 46;  // descriptor version of sm_100 and later
-    return d;          // base offset 0, swizzle mode 0 (none)
+    d |= 1ull << 16;                             // leading byte offset: unused with this swizzle
+    d |= (unsigned long long)(1024 >> 4) << 32;  // next 8-row atom
+    d |= 1ull << 46;                             // descriptor version of sm_100 and later
+    d |= 2ull << 61;                             // 128-byte swizzle
+    return d;
 }
 
 // Instruction descriptor of kind::f16: float32 D, bfloat16 A and B, both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr unsigned tc_idesc(int M, int N) {
+__device__ __forceinline__ unsigned tc_idesc(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mbar_init(unsigned mbar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
 }
 
 __device__ __forceinline__ bool tc_mbar_try_wait(unsigned mbar, unsigned parity) {
@@ -231,210 +263,275 @@ __device__ __forceinline__ bool tc_mbar_try_wait(unsigned mbar, unsigned parity)
     return ok != 0u;
 }
 
-// Shared memory of k_gemm_tc: kTcStages stages of the A and B tiles of one K
-// chunk, each tile 128 rows of 128 bytes (64 bfloat16) in the 128-byte
-// swizzled K-major layout (8-row atoms of 1024 bytes; the 16-byte piece j of
-// row r sits at piece j ^ (r % 8) of its row), then one mbarrier per stage
-// and the TMEM base address.  Chunks are loaded kTcAhead chunks ahead, into
-// the stage whose products (two chunks back) have completed.  Three stages
-// (97 KB) let two CTAs share an SM, so that one's epilogue overlaps the
-// other's loads and products.
-constexpr int kTcStages = 3, kTcAhead = kTcStages - 2;
-constexpr unsigned kTcTileBytes = TC_M * TC_K * 2;  // 16 KB per operand tile
-constexpr unsigned kTcSmem = 1024 + kTcStages * 2 * kTcTileBytes + 8 * kTcStages + 16;
-
-__device__ __forceinline__ void cp_async16(unsigned dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+__device__ __forceinline__ unsigned long long tc_now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-// Shared-memory matrix descriptor of a 128-byte swizzled K-major tile: start
-// address, stride between 8-row atoms (SBO), swizzle mode 2 (128 bytes).
-__device__ __forceinline__ unsigned long long tc_desc_sw128(unsigned addr) {
-    unsigned long long d = 0;
-    d |= (unsigned long long)((addr >> 4) & 0x3FFFu);
-    d |= 1ull << 16;                          // leading byte offset: unused with this swizzle
-    d |= (unsigned long long)(1024 >> 4) << 32;  // next 8-row atom
-    d |= 1ull << 46;                          // descriptor version of sm_100 and later
-    d |= 2ull << 61;                          // 128-byte swizzle
-    return d;
+// Bounded wait for the phase of the given parity: gives up after
+// kTcWaitNs of wall time (try_wait may suspend the thread for a while, so
+// the bound is on time, not on polls), or early once *stop is set (if stop
+// is not null).
+__device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity, const volatile int* stop) {
+    if (tc_mbar_try_wait(mbar, parity)) return true;
+    const unsigned long long t0 = tc_now_ns();
+    for (;;) {
+        if (tc_mbar_try_wait(mbar, parity)) return true;
+        if ((stop && *stop) || tc_now_ns() - t0 > kTcWaitNs) return false;
+    }
 }
 
-__global__ void __launch_bounds__(kTcThreads, 2) k_gemm_tc(GemmArgs g, int* __restrict__ err) {
+__device__ __forceinline__ void tc_expect_tx(unsigned mbar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tc_arrive(unsigned mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// TMA load of the box at (c0 = K, c1 = row) of a 2-D tensor map into shared
+// memory, counted on mbar.  c0 is a multiple of 64 elements (128 bytes).
+__device__ __forceinline__ void tc_tma_load(unsigned dst, const CUtensorMap* map, int c0, int c1, unsigned mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(unsigned mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+// Epilogue of 32 consecutive columns n .. n + 31 of row m (accumulators r):
+// 16-byte stores of the fused result.
+__device__ __forceinline__ void tc_store32(const GemmArgs& g, float* Cf, int m, int n, const unsigned (&r)[32]) {
+    if (g.epi == kStoreF32 || g.epi == kBiasF32) {
+        float4* dst = reinterpret_cast<float4*>(Cf + (long long)m * g.ldc + n);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float4 v = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                   __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+            if (g.epi == kBiasF32) {
+                const float4 bq = reinterpret_cast<const float4*>(g.bias + n)[q];
+                v.x += bq.x; v.y += bq.y; v.z += bq.z; v.w += bq.w;
+            }
+            dst[q] = v;
+        }
+        return;
+    }
+    uint4* dst = reinterpret_cast<uint4*>(g.Cb + (long long)m * g.ldc + n);
+    const uint4* mk = g.epi == kMaskBf16 ? reinterpret_cast<const uint4*>(g.mask + (long long)m * g.ldm + n) : nullptr;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(r[8 * q + e]);
+        if (g.epi == kBiasReluBf16) {
+            const float4 b0 = reinterpret_cast<const float4*>(g.bias + n)[2 * q];
+            const float4 b1 = reinterpret_cast<const float4*>(g.bias + n)[2 * q + 1];
+            const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = fmaxf(v[e] + bb[e], 0.f);
+        } else {  // kMaskBf16: keep where the stored activation is positive
+            const uint4 mv = mk[q];
+            const unsigned mw[4] = {mv.x, mv.y, mv.z, mv.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (!(__uint_as_float(mw[e] << 16) > 0.f)) v[2 * e] = 0.f;
+                if (!(__uint_as_float(mw[e] & 0xFFFF0000u) > 0.f)) v[2 * e + 1] = 0.f;
+            }
+        }
+        unsigned w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);  // .x at the lower address
+            w[e] = *reinterpret_cast<const unsigned*>(&h);
+        }
+        dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g,
+              TcShape sh, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
-    gemm_slice(g);
+    __shared__ int stop_flag;
     const unsigned raw = tc_smem(tc_smem_raw);
     const unsigned base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
-    const unsigned mbar0 = base + kTcStages * 2 * kTcTileBytes;  // mbarrier of stage s at mbar0 + 8 s
-    unsigned* tmem_slot = reinterpret_cast<unsigned*>(tc_smem_raw + (mbar0 + 8 * kTcStages - raw));
+    const unsigned bar0 = base + kTcStages * kTcStageBytes;
+    const unsigned drain_bar = bar0 + 8u * (2 * kTcStages + 4);
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(tc_smem_raw + (bar0 + 8u * kTcBars - raw));
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (kTcStages + s); };
+    auto accf_bar = [&](int b) { return bar0 + 8u * (2 * kTcStages + b); };
+    auto acce_bar = [&](int b) { return bar0 + 8u * (2 * kTcStages + 2 + b); };
+    volatile int* stop = &stop_flag;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TC_N;
 
-    if (warp == 0) {  // 128 TMEM columns: lanes = rows, columns = N
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(tc_smem(tmem_slot))
+    if (t == 0) {
+        stop_flag = 0;
+        for (int s = 0; s < kTcStages; ++s) {
+            tc_mbar_init(full_bar(s), 1);
+            tc_mbar_init(empty_bar(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc_mbar_init(accf_bar(b), 1);
+            tc_mbar_init(acce_bar(b), 4);  // one arrival per epilogue warp
+        }
+        tc_mbar_init(drain_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(tmem_slot)),
+                     "n"(kTcCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (t == 0) {
-        for (int st = 0; st < kTcStages; ++st)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0 + 8u * st) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tmem_slot;
 
-    constexpr unsigned IDESC = tc_idesc(TC_M, TC_N);
-    const int nk = g.K / TC_K;
-    auto tile = [&](int st) { return base + (unsigned)(2 * st) * kTcTileBytes; };
-    auto load = [&](int kt, int st) {  // one commit group per call (empty past the last chunk)
-        if (kt < nk) {
-            const unsigned a_s = tile(st), b_s = a_s + kTcTileBytes;
-            const int k0 = kt * TC_K;
-            for (int c = t; c < TC_M * (TC_K / 8); c += kTcThreads) {
-                const int r = c >> 3, j = c & 7;
-                const unsigned off = (unsigned)((r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4));
-                cp_async16(a_s + off, g.A + (long long)(m0 + r) * g.lda + k0 + 8 * j);
-                cp_async16(b_s + off, g.B + (long long)(n0 + r) * g.ldb + k0 + 8 * j);
-            }
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
+    const int tiles_mn = sh.m_tiles * sh.n_tiles, tiles = tiles_mn * sh.slices;
+    // K range of a tile: chunks [k0 / 64, k0 / 64 + nk)
+    auto tile_k = [&](int tile, int& k0, int& nk) {
+        const int z = tile / tiles_mn;
+        k0 = g.k_len > 0 ? z * g.k_len : 0;
+        nk = (g.k_len > 0 ? min(g.k_len, g.K - k0) : g.K) / TC_K;
     };
-    bool ok = true;
-    unsigned phase = 0, pending = 0;  // per stage: parity of its next completion, a commit not yet waited
-    auto wait_stage = [&](int st) {
-        unsigned polls = 0;
-        while (!tc_mbar_try_wait(mbar0 + 8u * st, (phase >> st) & 1u)) {
-            if (++polls == kTcWaitPolls) {
-                ok = false;
-                return;
-            }
-        }
-        phase ^= 1u << st;
-        pending &= ~(1u << st);
+    auto give_up = [&]() {
+        *stop = 1;
+        atomicOr(err, 1);
     };
+    unsigned issued = 0;  // warp 0, lane 0: chunks loaded
 
-    for (int q = 0; q < kTcAhead; ++q) load(q, q);
-    for (int kt = 0; kt < nk; ++kt) {
-        const int st = kt % kTcStages;
-        // chunk kt + kTcAhead goes to the stage chunk kt - 2 used
-        const int nx = kt + kTcAhead, sx = nx % kTcStages;
-        if (nx < nk && ((pending >> sx) & 1u)) wait_stage(sx);
-        load(nx, sx);
-        asm volatile("cp.async.wait_group %0;" ::"n"(kTcAhead) : "memory");  // chunk kt has landed
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");        // generic writes -> tensor core reads
-        if (!__syncthreads_and(ok ? 1 : 0)) {
-            ok = false;
-            break;
+    if (warp == 0) {
+        if (lane == 0) {
+            const unsigned bytes = kTcTileA + (unsigned)sh.bn * TC_K * 2u;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < tiles && !*stop; tile += gridDim.x) {
+                const int r = tile % tiles_mn, m0 = (r / sh.n_tiles) * TC_M, n0 = (r % sh.n_tiles) * sh.bn;
+                int k0, nk;
+                tile_k(tile, k0, nk);
+                for (int kt = 0; kt < nk; ++kt) {
+                    const int s = (int)(issued % kTcStages);
+                    const unsigned round = issued / kTcStages;
+                    if (round > 0 && !tc_wait(empty_bar(s), (round - 1u) & 1u, stop)) {
+                        give_up();
+                        ok = false;
+                        break;
+                    }
+                    const unsigned a_s = base + (unsigned)s * kTcStageBytes;
+                    tc_expect_tx(full_bar(s), bytes);
+                    tc_tma_load(a_s, &tmA, k0 + kt * TC_K, m0, full_bar(s));
+                    tc_tma_load(a_s + kTcTileA, &tmB, k0 + kt * TC_K, n0, full_bar(s));
+                    ++issued;
+                }
+            }
         }
-        if (t == 0) {
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const unsigned idesc = tc_idesc(TC_M, sh.bn);
+            unsigned it = 0, tc = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < tiles && !*stop; tile += gridDim.x) {
+                int k0, nk;
+                tile_k(tile, k0, nk);
+                const int buf = (int)(tc & 1u);
+                const unsigned use = tc >> 1;
+                if (use > 0 && !tc_wait(acce_bar(buf), (use - 1u) & 1u, stop)) {
+                    give_up();
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned acc = tmem + (unsigned)buf * 128u;
+                for (int kt = 0; kt < nk; ++kt, ++it) {
+                    const int s = (int)(it % kTcStages);
+                    if (!tc_wait(full_bar(s), (it / kTcStages) & 1u, stop)) {
+                        give_up();
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const unsigned a_s = base + (unsigned)s * kTcStageBytes, b_s = a_s + kTcTileA;
+#pragma unroll
+                    for (int kk = 0; kk < TC_K / 16; ++kk) {
+                        // K step of 16 = 32 bytes along the swizzled 128-byte rows
+                        const unsigned long long ad = tc_desc_sw128(a_s + 32u * kk);
+                        const unsigned long long bd = tc_desc_sw128(b_s + 32u * kk);
+                        const unsigned accumulate = (kt > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(acc),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+                            : "memory");
+                    }
+                    tc_commit(empty_bar(s));  // the stage is free once these products complete
+                }
+                if (!ok) break;
+                tc_commit(accf_bar(buf));
+                ++tc;
+            }
+            tc_commit(drain_bar);  // completes when every product issued above has
+        }
+    } else {
+        const int q = warp & 3;  // a warp reads TMEM lanes 32 (warp % 4) .. + 31
+        unsigned tc = 0;
+        for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++tc) {
+            const int buf = (int)(tc & 1u);
+            int okw = 1;
+            if (lane == 0) okw = tc_wait(accf_bar(buf), (tc >> 1) & 1u, stop) ? 1 : 0;
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            if (!okw) {
+                if (lane == 0) give_up();
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned a_s = tile(st), b_s = a_s + kTcTileBytes;
-#pragma unroll
-            for (int kk = 0; kk < TC_K / 16; ++kk) {
-                // K step of 16 = 32 bytes along the swizzled 128-byte rows
-                const unsigned long long ad = tc_desc_sw128(a_s + 32u * kk);
-                const unsigned long long bd = tc_desc_sw128(b_s + 32u * kk);
-                const unsigned acc = (kt > 0 || kk > 0) ? 1u : 0u;
+            const int r = tile % tiles_mn, m0 = (r / sh.n_tiles) * TC_M, n0 = (r % sh.n_tiles) * sh.bn;
+            float* Cf = g.Cf ? g.Cf + (long long)(tile / tiles_mn) * g.c_split : nullptr;
+            const int m = m0 + q * 32 + lane;
+#pragma unroll 1
+            for (int cb = 0; cb < sh.bn; cb += 32) {
+                unsigned v[32];
+                const unsigned addr = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(buf * 128 + cb);
                 asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
-                    : "memory");
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                    "[%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(addr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                tc_store32(g, Cf, m, n0 + cb, v);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             mbar0 + 8u * st)
-                         : "memory");
-        }
-        pending |= 1u << st;
-    }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy outlives the loop
-    // the products not waited for yet (at most one per stage)
-    for (int st = 0; st < kTcStages; ++st)
-        if ((pending >> st) & 1u) wait_stage(st);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    ok = __syncthreads_and(ok ? 1 : 0) != 0;
-    if (!ok) {
-        // a wait gave up: report it, and wait once more (bounded) for the
-        // products in flight before the tensor memory is released
-        if (t == 0) atomicOr(err, 1);
-        for (int st = 0; st < kTcStages; ++st) {
-            if (!((pending >> st) & 1u)) continue;
-            unsigned polls = 0;
-            while (!tc_mbar_try_wait(mbar0 + 8u * st, (phase >> st) & 1u) && ++polls < kTcWaitPolls) {
-            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) tc_arrive(acce_bar(buf));  // the accumulator may be overwritten
         }
     }
 
-    // epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 (rows), 32 columns at a time
-    if (ok) {
-        const int m = m0 + warp * 32 + lane;
-#pragma unroll 1
-        for (int cb = 0; cb < TC_N; cb += 32) {
-            unsigned r[32];
-            const unsigned addr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)cb;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-                "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                : "r"(addr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            // this thread's row, 32 consecutive columns: 16-byte stores
-            const int n = n0 + cb;
-            if (g.epi == kStoreF32 || g.epi == kBiasF32) {
-                float4* dst = reinterpret_cast<float4*>(g.Cf + (long long)m * g.ldc + n);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    float4 v = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                                           __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
-                    if (g.epi == kBiasF32) {
-                        const float4 bq = reinterpret_cast<const float4*>(g.bias + n)[q];
-                        v.x += bq.x; v.y += bq.y; v.z += bq.z; v.w += bq.w;
-                    }
-                    dst[q] = v;
-                }
-            } else {
-                uint4* dst = reinterpret_cast<uint4*>(g.Cb + (long long)m * g.ldc + n);
-                const uint4* mk =
-                    g.epi == kMaskBf16 ? reinterpret_cast<const uint4*>(g.mask + (long long)m * g.ldm + n) : nullptr;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float v[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(r[8 * q + e]);
-                    if (g.epi == kBiasReluBf16) {
-                        const float4 b0 = reinterpret_cast<const float4*>(g.bias + n)[2 * q];
-                        const float4 b1 = reinterpret_cast<const float4*>(g.bias + n)[2 * q + 1];
-                        const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) v[e] = fmaxf(v[e] + bb[e], 0.f);
-                    } else {  // kMaskBf16: keep where the stored activation is positive
-                        const uint4 mv = mk[q];
-                        const unsigned mw[4] = {mv.x, mv.y, mv.z, mv.w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            if (!(__uint_as_float(mw[e] << 16) > 0.f)) v[2 * e] = 0.f;
-                            if (!(__uint_as_float(mw[e] & 0xFFFF0000u) > 0.f)) v[2 * e + 1] = 0.f;
-                        }
-                    }
-                    unsigned w[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);  // .x at the lower address
-                        w[e] = *reinterpret_cast<const unsigned*>(&h);
-                    }
-                    dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
-                }
-            }
+    __syncthreads();
+    if (warp == 0 && lane == 0 && *stop) {
+        // copies issued but perhaps not consumed: the last one of each stage
+        for (int s = 0; s < kTcStages; ++s) {
+            if (issued <= (unsigned)s) continue;
+            const unsigned last = issued - 1u - ((issued - 1u - (unsigned)s) % kTcStages);
+            tc_wait(full_bar(s), (last / kTcStages) & 1u, nullptr);
         }
     }
+    if (warp == 1 && lane == 0 && !tc_wait(drain_bar, 0u, nullptr)) atomicOr(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTcCols) : "memory");
+    }
 }
 
 namespace {
@@ -679,24 +776,63 @@ unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Whether k_gemm_tc takes this product: the 128 x 128 x 64 tiling, 16-byte
-// aligned operand rows for cp.async, and 16-byte aligned output, bias and
-// mask rows for the vector epilogue.
-bool tc_ok(const lbm_mlp* c, const GemmArgs& a) {
-    if (c->tensor_path != 0 || a.M % TC_M || a.N % TC_N || a.K % TC_K || a.k_len % TC_K) return false;
-    if (!aligned16(a.A) || !aligned16(a.B) || a.lda % 8 || a.ldb % 8) return false;
+// cuTensorMapEncodeTiled from the driver, found once through the runtime
+// (no link against the driver library); null if the driver lacks it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// TMA map of a bfloat16 [rows, K] matrix with row stride ld (elements):
+// boxes of 64 (K) x box_rows, 128-byte swizzle (the layout k_gemm_tc's
+// descriptors name).
+bool tc_map(CUtensorMap* map, const bf16* ptr, int rows, int K, int ld, int box_rows) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(bf16)};
+    const cuuint32_t box[2] = {(cuuint32_t)TC_K, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(ptr), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The N tile with which k_gemm_tc takes this product, or 0 for k_gemm_nt:
+// M a multiple of 128, N of 32 (the tile is the largest of 128, 64, 32
+// dividing it), K and the K slice of 64; 16-byte aligned operand rows for TMA
+// and 16-byte aligned output, bias and mask rows for the vector epilogue.
+int tc_bn(const lbm_mlp* c, const GemmArgs& a) {
+    if (c->tensor_path != 0 || !tensor_map_encoder()) return 0;
+    if (a.M % TC_M || a.K % TC_K || a.k_len % TC_K) return 0;
+    const int bn = a.N % 128 == 0 ? 128 : a.N % 64 == 0 ? 64 : a.N % 32 == 0 ? 32 : 0;
+    if (!bn || !aligned16(a.A) || !aligned16(a.B) || a.lda % 8 || a.ldb % 8) return 0;
+    bool ok;
     switch (a.epi) {
-        case kStoreF32: return aligned16(a.Cf) && a.ldc % 4 == 0 && a.c_split % 4 == 0;
-        case kBiasF32: return aligned16(a.Cf) && a.ldc % 4 == 0 && aligned16(a.bias);
-        case kBiasReluBf16: return aligned16(a.Cb) && a.ldc % 8 == 0 && aligned16(a.bias);
-        default: return aligned16(a.Cb) && a.ldc % 8 == 0 && aligned16(a.mask) && a.ldm % 8 == 0;
+        case kStoreF32: ok = aligned16(a.Cf) && a.ldc % 4 == 0 && a.c_split % 4 == 0; break;
+        case kBiasF32: ok = aligned16(a.Cf) && a.ldc % 4 == 0 && aligned16(a.bias); break;
+        case kBiasReluBf16: ok = aligned16(a.Cb) && a.ldc % 8 == 0 && aligned16(a.bias); break;
+        default: ok = aligned16(a.Cb) && a.ldc % 8 == 0 && aligned16(a.mask) && a.ldm % 8 == 0;
     }
+    return ok ? bn : 0;
 }
 
 cudaError_t launch_gemm(lbm_mlp* c, const GemmArgs& a, int slices) {
-    if (tc_ok(c, a)) {
-        const dim3 grid(a.N / TC_N, a.M / TC_M, slices);
-        k_gemm_tc<<<grid, kTcThreads, kTcSmem, c->stream>>>(a, c->d_err);
+    const int bn = tc_bn(c, a);
+    CUtensorMap ma, mb;
+    if (bn && tc_map(&ma, a.A, a.M, a.K, a.lda, TC_M) && tc_map(&mb, a.B, a.N, a.K, a.ldb, bn)) {
+        const TcShape sh{a.M / TC_M, a.N / bn, slices, bn};
+        const long long tiles = (long long)sh.m_tiles * sh.n_tiles * slices;
+        const int grid = (int)std::min<long long>(tiles, c->sms);  // persistent: one CTA per SM at most
+        k_gemm_tc<<<grid, kTcThreads, kTcSmem, c->stream>>>(ma, mb, a, sh, c->d_err);
     } else {
         const dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, slices);
         k_gemm_nt<<<grid, kGemmThreads, 0, c->stream>>>(a);
@@ -719,16 +855,16 @@ cudaError_t gemm(lbm_mlp* c, const bf16* A, int lda, const bf16* B, int ldb, int
 }
 
 // out [M, N] (row stride N) = A B^T for a long K (the batch of the weight
-// gradients): K is cut into slices so that the tiles x slices fill about two
-// CTAs per SM, each slice at least 8 K chunks; the float32 partials go to the
+// gradients): K is cut into slices so that there are about two tiles x
+// slices per SM, each slice at least 8 K chunks; the float32 partials go to the
 // workspace and k_splitsum adds them in slice order.
 cudaError_t gemm_long_k(lbm_mlp* c, const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K,
                         float* out) {
     GemmArgs a = gemm_args(A, lda, B, ldb, M, N, K, kStoreF32, nullptr, nullptr, 0, out, nullptr, N);
-    const bool tc = tc_ok(c, a);
-    const int unit = tc ? TC_K : BK;
+    const int bn = tc_bn(c, a);
+    const int unit = bn ? TC_K : BK;
     const long long tiles =
-        tc ? (long long)(M / TC_M) * (N / TC_N) : (long long)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+        bn ? (long long)(M / TC_M) * (N / bn) : (long long)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
     long long S = std::max(1LL, 2LL * c->sms / tiles);
     S = std::min<long long>(std::min<long long>(S, kMaxSplit), std::max(1, K / (8 * unit)));
     if (S <= 1) return launch_gemm(c, a, 1);

@@ -86,6 +86,31 @@ def test_forward_matches_float64(built):
     assert np.max(np.abs(yn - rn)) <= 3e-2 * np.max(np.abs(rn))
 
 
+def test_forward_many_tiles_per_cta(built):
+    """Batch 20,480: 320 output tiles of the hidden layers on at most one CTA
+    per SM, so each persistent CTA takes two or three tiles (its stage ring
+    and both tensor-memory accumulators wrap).  Every row against the
+    mma.sync path, and 512 sampled rows against the float64 MLP that rounds
+    at the same points."""
+    import torch
+
+    n = 20480
+    net, norm, x, _, xd, _ = _setup(n, 6)
+    outs = []
+    for path in (0, 1):
+        net.set_tensor_path(path)
+        y = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+        net.forward(xd, y)
+        net.sync()
+        outs.append((y.cpu().numpy().astype(np.float64) - norm[2]) * np.asarray(norm[3], dtype=np.float64))
+    y0, y1 = outs
+    assert np.max(np.abs(y0 - y1)) <= 1e-2 * np.max(np.abs(y1))
+    rows = np.random.default_rng(3).choice(n, 512, replace=False)
+    cpu = _cpu_model(net, SIZES, norm)
+    ref = (cpu.forward(x[rows], rounding=True) - norm[2]) * np.asarray(norm[3], dtype=np.float64)
+    assert np.max(np.abs(y0[rows] - ref)) <= 3e-3 * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("path", [0, 1])
 @pytest.mark.parametrize("n", [128, 4096])
 def test_gradients_match_float64(built, n, path):
@@ -180,9 +205,10 @@ def test_invalid_shapes_rejected(built):
 
 
 def test_tcgen05_and_mma_sync_paths_agree(built):
-    """Batch 256: the hidden-layer products (M 256, N 256, K 576 / 256) and the
-    weight gradients (K = 256) run on tcgen05 tensor cores by default and on
-    mma.sync with path 1.  Both accumulate bfloat16 products in float32 in a
+    """Batch 256: the forward products (N tiles of 128 and, for the 32-wide
+    output layer, 32), the masked back-propagation products and the weight
+    gradients (N tile 64 for the 576-wide first layer) run on tcgen05 tensor
+    cores by default and on mma.sync with path 1.  Both accumulate bfloat16 products in float32 in a
     different order, so a stored bfloat16 activation can round the other way:
     outputs agree to 1e-2 of their largest magnitude, gradients to 2e-2 in
     relative L2 norm per layer; a wrong operand layout would miss by O(1)."""
