@@ -119,8 +119,11 @@ typedef struct {
     int32_t row_variant; /* row-tiled kernel: 1 per-thread loads of the pulled
                             populations (each plane read twice, the second
                             time from L2), 2 whole pulled rows staged in shared
-                            memory by bulk copies (cp.async.bulk, one read);
-                            0: automatic */
+                            memory by bulk copies (cp.async.bulk, one read),
+                            3 loader and collider threads per row (warp-
+                            specialised: each population read once, staged in
+                            shared memory for the collision); 0: automatic;
+                            LBM_EINVAL outside 0..3 */
     int32_t collision;   /* lbm_collision, default LBM_COLLISION_BGK */
     double mrt_rates[5]; /* MRT rates of the energy, energy-square, energy-flux,
                             stress-partner and third-order moments (s_e, s_eps,

@@ -216,7 +216,7 @@ int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[
         return LBM_EINVAL;
     if (o.bc != LBM_BC_GHOST_LINEAR && o.bc != LBM_BC_PERIODIC_TEST) return LBM_EINVAL;
     if (o.frame != LBM_FRAME_DROPLET && o.frame != LBM_FRAME_BOX) return LBM_EINVAL;
-    if (o.row_variant < 0 || o.row_variant > 2) return LBM_EINVAL;
+    if (o.row_variant < 0 || o.row_variant > 3) return LBM_EINVAL;
     if (o.collision != LBM_COLLISION_BGK && o.collision != LBM_COLLISION_MRT) return LBM_EINVAL;
     double mrt_rates[5] = {1.19, 1.4, 1.2, 1.4, 1.98};  // d'Humieres et al. (2002)
     for (int k = 0; k < 5; ++k) {

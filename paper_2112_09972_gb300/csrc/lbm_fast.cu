@@ -273,6 +273,19 @@ struct RowIO<float> {
 #pragma unroll
             for (int i = 0; i < 19; ++i) f[s][i] = pulled_last(src, L, b, s, i);
     }
+    // one read of the 38 pulled populations and the densities summed from
+    // them in the order of densities() (the warp-specialised kernel)
+    static __device__ __forceinline__ void load_all(const float* __restrict__ src, const Layout& L, NodeIx n, int p,
+                                                    float (&f)[2][19], float& ra, float& rb) {
+        populations(src, L, n, p, f);
+        ra = f[0][0];
+        rb = f[1][0];
+#pragma unroll
+        for (int i = 1; i < 19; i += 2) {
+            ra += f[0][i] + f[0][i + 1];
+            rb += f[1][i] + f[1][i + 1];
+        }
+    }
 };
 
 template <typename T>
@@ -311,6 +324,30 @@ struct RowIO<Dev<T>> {
             f[1][i] = wgt<float>(i) * o.y + v.y;
         }
     }
+    // one read of the block and the 18 pulled words: the populations of
+    // populations() and the densities of densities(), with their arithmetic
+    static __device__ __forceinline__ void load_all(const Dev<T>* __restrict__ src, const Layout& L, NodeIx n, int p,
+                                                    float (&f)[2][19], float& ra, float& rb) {
+        const float4 o = __ldlu(reinterpret_cast<const float4*>(src) + n.a + (long long)p * (L.plane >> 3));
+        const unsigned* d = reinterpret_cast<const unsigned*>(src);
+        const long long b = n.b + (long long)p * (L.plane >> 1);
+        f[0][0] = o.z;
+        f[1][0] = o.w;
+        float da = 0.f, db = 0.f;
+#pragma unroll
+        for (int i = 1; i < 19; i += 2) {
+            const float2 u = dev_unpack2<T>(__ldlu(dev_ptr(d, L, b, i)));
+            const float2 v = dev_unpack2<T>(__ldlu(dev_ptr(d, L, b, i + 1)));
+            da += u.x + v.x;
+            db += u.y + v.y;
+            f[0][i] = wgt<float>(i) * o.x + u.x;
+            f[1][i] = wgt<float>(i) * o.y + u.y;
+            f[0][i + 1] = wgt<float>(i + 1) * o.x + v.x;
+            f[1][i + 1] = wgt<float>(i + 1) * o.y + v.y;
+        }
+        ra = o.z + (1.f - wgt<float>(0)) * o.x + da;
+        rb = o.w + (1.f - wgt<float>(0)) * o.y + db;
+    }
 };
 
 // Shared memory of the staged variant beyond the density ring: NST stage
@@ -322,6 +359,145 @@ struct StagedLayout {
     static constexpr size_t stage_off = ((mbar_off + 8 * NST + 127) / 128) * 128;
     static constexpr size_t bytes = stage_off + (size_t)NST * StagePlane<TX, ST>::BYTES;
 };
+
+// Collision of node (x, y, z) from its 38 pulled populations f and the
+// density ring (slots s0, s1, s2 hold planes z - 1, z, z + 1; row 0 is this
+// CTA's row, rows -1 / +1 its neighbours, columns -1 and TX the x halo):
+// momentum (Eq. 6), Shan-Chen force (Eq. 7), common velocity with the force
+// shift, BGK relaxation to the equilibrium of Eq. 8 (Eqs. 9, 10), and the
+// store of the post-collision state (float32 populations with the rest
+// population closing the mass balance, or 16-bit deviations).  Also
+// accumulates the centre-of-mass partials of the droplet phase and flags
+// non-finite densities.  Shared by the row kernels so that every variant
+// computes bit-identical states.
+template <int TX, typename ST>
+__device__ __forceinline__ void collide_node(const float* ring, int s0, int s1, int s2, int x, int y, int z,
+                                             const float (&f)[2][19], const FastModel& m, const Layout& L,
+                                             ST* __restrict__ dst, int* __restrict__ d_err, float (&cm)[4], float px,
+                                             float py) {
+    constexpr int RW = TX + 2;
+    auto ridx = [&](int slot, int row, int col) { return ((slot * 3 + row + 1) * RW + col + 1) * 2; };
+    // neighbour density of component s at offset (dx, dy, dz)
+    auto nb = [&](int s, int dx, int dy, int dz) -> float {
+        const int slot = dz == 0 ? s1 : (dz > 0 ? s2 : s0);
+        return ring[ridx(slot, dy, x + dx) + s];
+    };
+    const float rho[2] = {ring[ridx(s1, 0, x)], ring[ridx(s1, 0, x) + 1]};
+    // momentum (Eq. 6), opposite pairs differenced first
+    float j[2][3];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        float jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+        for (int i = 1; i < 19; i += 2) {
+            const float d = f[s][i] - f[s][i + 1];
+            if (cx_(i)) jx += (float)cx_(i) * d;
+            if (cy_(i)) jy += (float)cy_(i) * d;
+            if (cz_(i)) jz += (float)cz_(i) * d;
+        }
+        j[s][0] = jx; j[s][1] = jy; j[s][2] = jz;
+    }
+    // Shan-Chen force (Eq. 7) sums, neighbour pairs differenced first
+    float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int i = 1; i < 19; i += 2) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const float d = wgt<float>(i) * (nb(s, cx_(i), cy_(i), cz_(i)) - nb(s, -cx_(i), -cy_(i), -cz_(i)));
+            if (cx_(i)) acc[s][0] += (float)cx_(i) * d;
+            if (cy_(i)) acc[s][1] += (float)cy_(i) * d;
+            if (cz_(i)) acc[s][2] += (float)cz_(i) * d;
+        }
+    }
+    const float den = rho[0] * m.inv_tau[0] + rho[1] * m.inv_tau[1];
+    float up[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) up[a] = (j[0][a] * m.inv_tau[0] + j[1][a] * m.inv_tau[1]) / den;
+    if (!(isfinite(rho[0]) && isfinite(rho[1]))) atomicOr(d_err, 1);
+    {
+        const float phi = (rho[0] - rho[1]) / (rho[0] + rho[1]);
+        const float w = phi > 0.f ? phi : 0.f;
+        cm[0] += w;
+        cm[1] += w * px;
+        cm[2] += w * py;
+        cm[3] += w * ((float)z - 0.5f * (float)(L.Lz - 1));
+    }
+    if constexpr (is_dev_t<ST>::value) {
+        // 16-bit deviations from w_i times the density of the node each
+        // population streams to (this CTA's density planes), the pair of
+        // components of one direction in one word
+        using T = decltype(dev_tag(ST{}));
+        float ux[2], uy[2], uz[2], u2x[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const float sh = -m.G * m.tau[s];  // tau_s F^s / rho_s per unit of the other sum
+            ux[s] = up[0] + sh * acc[1 - s][0];
+            uy[s] = up[1] + sh * acc[1 - s][1];
+            uz[s] = up[2] + sh * acc[1 - s][2];
+            u2x[s] = 1.5f * (ux[s] * ux[s] + uy[s] * uy[s] + uz[s] * uz[s]);
+        }
+        unsigned* d = reinterpret_cast<unsigned*>(dst);
+        const long long db = L.dev_word(1, x, y, z);
+        float others[2] = {0.f, 0.f};
+#pragma unroll
+        for (int i = 1; i < 19; i += 2) {
+            float da[2], dbv[2], refa[2], refb[2];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const float cu = (float)cx_(i) * ux[s] + (float)cy_(i) * uy[s] + (float)cz_(i) * uz[s];
+                const float rw = rho[s] * wgt<float>(i);
+                const float even = rw * (1.f + 4.5f * cu * cu - u2x[s]);
+                const float odd = rw * (3.f * cu);
+                const float fa = f[s][i], fb = f[s][i + 1];
+                const float oa = fa - (fa - (even + odd)) * m.inv_tau[s];
+                const float ob = fb - (fb - (even - odd)) * m.inv_tau[s];
+                refa[s] = wgt<float>(i) * nb(s, cx_(i), cy_(i), cz_(i));
+                refb[s] = wgt<float>(i) * nb(s, -cx_(i), -cy_(i), -cz_(i));
+                da[s] = oa - refa[s];
+                dbv[s] = ob - refb[s];
+            }
+            const unsigned wa = dev_pack2<T>(da[0], da[1]), wb = dev_pack2<T>(dbv[0], dbv[1]);
+            __stcs(d + db + (long long)(i - 1) * L.array, wa);
+            __stcs(d + db + (long long)i * L.array, wb);
+            // the values the readers will rebuild, for the mass balance
+            const float2 qa = dev_unpack2<T>(wa), qb = dev_unpack2<T>(wb);
+            others[0] += (refa[0] + qa.x) + (refb[0] + qb.x);
+            others[1] += (refa[1] + qa.y) + (refb[1] + qb.y);
+        }
+        __stcs(reinterpret_cast<float4*>(dst) + L.dev_node(x, y, z),
+               make_float4(rho[0], rho[1], rho[0] - others[0], rho[1] - others[1]));
+    } else {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const float sh = -m.G * m.tau[s];  // tau_s F^s / rho_s per unit of the other sum
+            const float ux = up[0] + sh * acc[1 - s][0];
+            const float uy = up[1] + sh * acc[1 - s][1];
+            const float uz = up[2] + sh * acc[1 - s][2];
+            const float u2x = 1.5f * (ux * ux + uy * uy + uz * uz);
+            const float it = m.inv_tau[s];
+            const float r = rho[s];
+            // moving populations; the rest population then closes the mass
+            // balance exactly (sum of outputs = rho), which keeps fp32
+            // rounding from drifting the interface
+            const long long b = L.at(s, 0, x, y, z);
+            float others = 0.f;
+#pragma unroll
+            for (int i = 1; i < 19; i += 2) {
+                const float cu = (float)cx_(i) * ux + (float)cy_(i) * uy + (float)cz_(i) * uz;
+                const float rw = r * wgt<float>(i);
+                const float even = rw * (1.f + 4.5f * cu * cu - u2x);
+                const float odd = rw * (3.f * cu);
+                const float fa = f[s][i], fb = f[s][i + 1];
+                const float oa = fa - (fa - (even + odd)) * it;
+                const float ob = fb - (fb - (even - odd)) * it;
+                __stcs(dst + b + (long long)i * L.array, oa);
+                __stcs(dst + b + (long long)(i + 1) * L.array, ob);
+                others += oa + ob;
+            }
+            __stcs(dst + b, r - others);
+        }
+    }
+}
 
 template <int TX, int CY, int MINB, typename ST, bool STAGED>
 __global__ void __launch_bounds__(TX, MINB)
@@ -498,127 +674,8 @@ __global__ void __launch_bounds__(TX, MINB)
         }
         wait_rows(z + 1);
 
-        const int s0 = slot_of(z - 1), s1 = slot_of(z), s2 = slot_of(z + 1);
-        // neighbour density of component s at offset (dx, dy, dz)
-        auto nb = [&](int s, int dx, int dy, int dz) -> float {
-            const int slot = dz == 0 ? s1 : (dz > 0 ? s2 : s0);
-            return ring[ridx(slot, dy, x + dx) + s];
-        };
-        const float rho[2] = {ring[ridx(s1, 0, x)], ring[ridx(s1, 0, x) + 1]};
-        // momentum (Eq. 6), opposite pairs differenced first
-        float j[2][3];
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            float jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-            for (int i = 1; i < 19; i += 2) {
-                const float d = f[s][i] - f[s][i + 1];
-                if (cx_(i)) jx += (float)cx_(i) * d;
-                if (cy_(i)) jy += (float)cy_(i) * d;
-                if (cz_(i)) jz += (float)cz_(i) * d;
-            }
-            j[s][0] = jx; j[s][1] = jy; j[s][2] = jz;
-        }
-        // Shan-Chen force (Eq. 7) sums, neighbour pairs differenced first
-        float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-#pragma unroll
-        for (int i = 1; i < 19; i += 2) {
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const float d = wgt<float>(i) * (nb(s, cx_(i), cy_(i), cz_(i)) - nb(s, -cx_(i), -cy_(i), -cz_(i)));
-                if (cx_(i)) acc[s][0] += (float)cx_(i) * d;
-                if (cy_(i)) acc[s][1] += (float)cy_(i) * d;
-                if (cz_(i)) acc[s][2] += (float)cz_(i) * d;
-            }
-        }
-        const float den = rho[0] * m.inv_tau[0] + rho[1] * m.inv_tau[1];
-        float up[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) up[a] = (j[0][a] * m.inv_tau[0] + j[1][a] * m.inv_tau[1]) / den;
-        if (!(isfinite(rho[0]) && isfinite(rho[1]))) atomicOr(d_err, 1);
-        {
-            const float phi = (rho[0] - rho[1]) / (rho[0] + rho[1]);
-            const float w = phi > 0.f ? phi : 0.f;
-            cm[0] += w;
-            cm[1] += w * px;
-            cm[2] += w * py;
-            cm[3] += w * ((float)z - 0.5f * (float)(L.Lz - 1));
-        }
-        if constexpr (is_dev_t<ST>::value) {
-            // 16-bit deviations from w_i times the density of the node each
-            // population streams to (this CTA's density planes), the pair of
-            // components of one direction in one word
-            using T = decltype(dev_tag(ST{}));
-            float ux[2], uy[2], uz[2], u2x[2];
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const float sh = -m.G * m.tau[s];  // tau_s F^s / rho_s per unit of the other sum
-                ux[s] = up[0] + sh * acc[1 - s][0];
-                uy[s] = up[1] + sh * acc[1 - s][1];
-                uz[s] = up[2] + sh * acc[1 - s][2];
-                u2x[s] = 1.5f * (ux[s] * ux[s] + uy[s] * uy[s] + uz[s] * uz[s]);
-            }
-            unsigned* d = reinterpret_cast<unsigned*>(dst);
-            const long long db = L.dev_word(1, x, y, z);
-            float others[2] = {0.f, 0.f};
-#pragma unroll
-            for (int i = 1; i < 19; i += 2) {
-                float da[2], dbv[2], refa[2], refb[2];
-#pragma unroll
-                for (int s = 0; s < 2; ++s) {
-                    const float cu = (float)cx_(i) * ux[s] + (float)cy_(i) * uy[s] + (float)cz_(i) * uz[s];
-                    const float rw = rho[s] * wgt<float>(i);
-                    const float even = rw * (1.f + 4.5f * cu * cu - u2x[s]);
-                    const float odd = rw * (3.f * cu);
-                    const float fa = f[s][i], fb = f[s][i + 1];
-                    const float oa = fa - (fa - (even + odd)) * m.inv_tau[s];
-                    const float ob = fb - (fb - (even - odd)) * m.inv_tau[s];
-                    refa[s] = wgt<float>(i) * nb(s, cx_(i), cy_(i), cz_(i));
-                    refb[s] = wgt<float>(i) * nb(s, -cx_(i), -cy_(i), -cz_(i));
-                    da[s] = oa - refa[s];
-                    dbv[s] = ob - refb[s];
-                }
-                const unsigned wa = dev_pack2<T>(da[0], da[1]), wb = dev_pack2<T>(dbv[0], dbv[1]);
-                __stcs(d + db + (long long)(i - 1) * L.array, wa);
-                __stcs(d + db + (long long)i * L.array, wb);
-                // the values the readers will rebuild, for the mass balance
-                const float2 qa = dev_unpack2<T>(wa), qb = dev_unpack2<T>(wb);
-                others[0] += (refa[0] + qa.x) + (refb[0] + qb.x);
-                others[1] += (refa[1] + qa.y) + (refb[1] + qb.y);
-            }
-            __stcs(reinterpret_cast<float4*>(dst) + L.dev_node(x, y, z),
-                   make_float4(rho[0], rho[1], rho[0] - others[0], rho[1] - others[1]));
-        } else {
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const float sh = -m.G * m.tau[s];  // tau_s F^s / rho_s per unit of the other sum
-                const float ux = up[0] + sh * acc[1 - s][0];
-                const float uy = up[1] + sh * acc[1 - s][1];
-                const float uz = up[2] + sh * acc[1 - s][2];
-                const float u2x = 1.5f * (ux * ux + uy * uy + uz * uz);
-                const float it = m.inv_tau[s];
-                const float r = rho[s];
-                // moving populations; the rest population then closes the mass
-                // balance exactly (sum of outputs = rho), which keeps fp32
-                // rounding from drifting the interface
-                const long long b = L.at(s, 0, x, y, z);
-                float others = 0.f;
-#pragma unroll
-                for (int i = 1; i < 19; i += 2) {
-                    const float cu = (float)cx_(i) * ux + (float)cy_(i) * uy + (float)cz_(i) * uz;
-                    const float rw = r * wgt<float>(i);
-                    const float even = rw * (1.f + 4.5f * cu * cu - u2x);
-                    const float odd = rw * (3.f * cu);
-                    const float fa = f[s][i], fb = f[s][i + 1];
-                    const float oa = fa - (fa - (even + odd)) * it;
-                    const float ob = fb - (fb - (even - odd)) * it;
-                    __stcs(dst + b + (long long)i * L.array, oa);
-                    __stcs(dst + b + (long long)(i + 1) * L.array, ob);
-                    others += oa + ob;
-                }
-                __stcs(dst + b, r - others);
-            }
-        }
+        collide_node<TX, ST>(ring, slot_of(z - 1), slot_of(z), slot_of(z + 1), x, y, z, f, m, L, dst, d_err, cm, px,
+                             py);
         // Before a later plane reuses this plane's own-row slot, all threads
         // must be done reading it: the __syncthreads of the next iterations
         // (S > 3 planes apart) order that.
@@ -681,6 +738,239 @@ __global__ void __launch_bounds__(TX, MINB)
 #pragma unroll
             for (int q = 0; q < 4; ++q) cp.sum[q] = s4[q];
             // frame origin x_c = sum w x / sum w (box centre when there is no droplet)
+            const bool have = s4[0] > 0.0;
+            for (int q = 0; q < 3; ++q) cp.sum[4 + q] = have ? s4[1 + q] / s4[0] : 0.0;
+            *cp.counter = 0u;
+        }
+    }
+}
+
+// ---- Warp-specialised variant: loader and collider threads per row ----
+//
+// A CTA of 2 TX threads owns one row: threads 0 .. TX-1 (loaders) and
+// TX .. 2 TX-1 (colliders) each take node x = t mod TX.  Per plane p a loader
+// reads the node's 38 pulled populations once, sums its densities into the
+// ring (own row, the neighbour CTAs' rows by st.async, the outer-halo node as
+// in the direct variant) and stages the populations in shared memory (NP
+// planes in flight); the colliders collide plane z from shared memory once
+// the densities of plane z + 1 have landed.  Loads of later planes are in
+// flight while earlier planes are collided, on other warps, and no
+// population is read twice.
+//
+// Barriers (all waits bounded): ring slot k completes when this CTA's TX
+// loaders have written their own row of the slot's plane and the 2 TX x 8
+// bytes of the rows -1 / +1 have landed; full[b] when the loaders have staged
+// a plane in buffer b; empty[b] when the colliders are done with it.
+//
+// Ring slots: a loader pushes plane p's densities only after it has staged
+// plane p - 1, which waited for its colliders to be done with plane
+// p - 1 - NP = p - 3; those colliders finished plane p - 3 only after the CTAs
+// next to them had pushed plane p - 2.  So a loader is at most two planes
+// ahead of the loaders of the CTAs next to it in the cluster and at most
+// 2 (CY - 1) planes ahead of any CTA of the cluster (the outer-halo rows go
+// from every CTA to the edge CTAs), whose colliders may still be reading
+// three planes behind that CTA's own loader: S = 2 CY + 2 slots.
+template <int TX, int CY>
+struct WsLayout {
+    static constexpr int RW = TX + 2;
+    static constexpr int HN = 2 * TX / CY;
+    static constexpr int S = 2 * CY + 2;
+    static constexpr int NP = 2;
+    static constexpr int RING = S * 3 * RW * 2;  // [slot][row -1..1][col][component] floats
+    static constexpr int POPS = NP * 38 * TX;    // [buffer][s * 19 + i][x] floats
+    static constexpr unsigned TX_BYTES = 2u * TX * 2u * 4u;
+    static constexpr int NBAR = S + 2 * NP;
+    static constexpr size_t bytes = sizeof(float) * (RING + POPS) + sizeof(unsigned long long) * NBAR;
+};
+
+__device__ __forceinline__ void mbar_arrive(unsigned mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wall-time bound of one wait of the warp-specialised kernel.
+constexpr unsigned long long kWsWaitNs = 2000000000ull;
+// Bounded wait for the phase of the given parity (cluster scope: remote
+// st.async bytes count on the ring barriers); false when it gave up.
+__device__ __forceinline__ bool ws_wait(unsigned mbar, unsigned parity, bool cluster_scope) {
+    auto poll = [&]() { return cluster_scope ? mbar_try_wait(mbar, parity) : mbar_try_wait_cta(mbar, parity); };
+    if (poll()) return true;
+    const unsigned long long t0 = now_ns();
+    while (!poll())
+        if (now_ns() - t0 > kWsWaitNs) return false;
+    return true;
+}
+
+template <int TX, int CY, int MINB, typename ST>
+__global__ void __launch_bounds__(2 * TX, MINB)
+    k_stream_collide_ws(const ST* __restrict__ src, ST* __restrict__ dst, Layout L, FastModel m, int zchunk,
+                        CentreParts cp, int* __restrict__ d_err) {
+    using IO = RowIO<ST>;
+    using WL = WsLayout<TX, CY>;
+    constexpr int RW = WL::RW, HN = WL::HN, S = WL::S, NP = WL::NP;
+    extern __shared__ __align__(128) float ring[];  // [S][3][RW][2], then [NP][38][TX], then NBAR mbarriers
+    float* pops = ring + WL::RING;
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(pops + WL::POPS);
+    __shared__ double red[4 * ((2 * TX + 31) / 32)];
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int t = threadIdx.x;
+    const bool loader = t < TX;
+    const int x = loader ? t : t - TX;
+    const int y = blockIdx.y;
+    const int rank = (int)cluster.block_rank();  // == y % CY for cluster dims (1, CY, 1)
+    const int Y0 = y - rank;
+    const int zc0 = blockIdx.z * zchunk;
+    const int zc1 = min(zc0 + zchunk, L.Lz);
+
+    // outer-halo node of loader threads x < HN (as in the direct variant)
+    const bool hthr = loader && x < HN;
+    const int hside = x < HN / 2 ? 0 : 1;
+    const int hcol = rank * (HN / 2) + (x % (HN / 2));
+    const int hy = hside ? Y0 + CY : Y0 - 1;
+    const bool hin = hy >= 0 && hy < L.Ly;
+
+    auto ridx = [&](int slot, int row, int col) { return ((slot * 3 + row + 1) * RW + col + 1) * 2; };
+    const unsigned ring_s = smem_u32(ring);
+    const unsigned rbar_s = smem_u32(bars);        // S ring-slot barriers
+    const unsigned full_s = rbar_s + 8u * S;       // NP: a plane staged
+    const unsigned empty_s = full_s + 8u * NP;     // NP: a staged plane read
+    const unsigned below_ring = rank > 0 ? cluster_addr(ring_s, rank - 1) : 0u;  // their row +1
+    const unsigned below_mbar = rank > 0 ? cluster_addr(rbar_s, rank - 1) : 0u;
+    const unsigned above_ring = rank < CY - 1 ? cluster_addr(ring_s, rank + 1) : 0u;  // their row -1
+    const unsigned above_mbar = rank < CY - 1 ? cluster_addr(rbar_s, rank + 1) : 0u;
+    const unsigned halo_ring = cluster_addr(ring_s, hside ? CY - 1 : 0);
+    const unsigned halo_mbar = cluster_addr(rbar_s, hside ? CY - 1 : 0);
+
+    for (int e = t; e < WL::RING; e += 2 * TX) ring[e] = m.rho_b[e & 1];  // ghost density, x halo columns for good
+    if (t == 0) {
+        for (int k = 0; k < S; ++k) mbar_init(rbar_s + 8u * k, (unsigned)TX);
+        for (int b = 0; b < NP; ++b) {
+            mbar_init(full_s + 8u * b, (unsigned)TX);
+            mbar_init(empty_s + 8u * b, (unsigned)TX);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cluster.sync();  // barriers initialised before any remote store arrives
+
+    auto slot_of = [&](int p) { return (p - (zc0 - 1)) % S; };
+    float cm[4] = {0.f, 0.f, 0.f, 0.f};
+
+    if (loader) {
+        const NodeIx node0 = IO::node(L, x, y);
+        const NodeIx hnode0 = IO::node(L, hcol, hin ? hy : 0);
+        unsigned long long keep;
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
+        unsigned ephase = 0u;  // bit b: parity of empty[b]'s next phase
+        for (int p = zc0 - 1; p <= zc1; ++p) {
+            const bool in = p >= 0 && p < L.Lz;
+            const bool staged = p >= zc0 && p < zc1;  // a plane this CTA collides
+            float f[2][19];
+            float ra = m.rho_b[0], rb = m.rho_b[1];
+            if (in) IO::load_all(src, L, node0, p, f, ra, rb);
+            float ha = m.rho_b[0], hb = m.rho_b[1];
+            if (hthr && in && hin) IO::densities(src, L, hnode0, p, keep, ha, hb);  // read again by its own CTA
+            // densities first: the colliders of plane p - 1 wait for them
+            const int slot = slot_of(p);
+            const unsigned mb = 8u * slot;
+            *reinterpret_cast<float2*>(ring + ridx(slot, 0, x)) = make_float2(ra, rb);
+            if (rank > 0) st_async_f2(below_ring + 4u * ridx(slot, 1, x), ra, rb, below_mbar + mb);
+            if (rank < CY - 1) st_async_f2(above_ring + 4u * ridx(slot, -1, x), ra, rb, above_mbar + mb);
+            if (hthr) st_async_f2(halo_ring + 4u * ridx(slot, hside ? 1 : -1, hcol), ha, hb, halo_mbar + mb);
+            if (x == 0) mbar_expect_tx(rbar_s + mb, WL::TX_BYTES);  // this thread's arrival, and the bytes
+            else mbar_arrive(rbar_s + mb);
+            // then the populations, into a buffer the colliders are done with
+            // (plane p - NP); they wait in registers meanwhile
+            if (staged) {
+                const int b = (p - zc0) % NP;
+                if (p - zc0 >= NP) {
+                    if (!ws_wait(empty_s + 8u * b, (ephase >> b) & 1u, false)) atomicOr(d_err, 4);
+                    ephase ^= 1u << b;
+                }
+                float* P = pops + (size_t)b * 38 * TX;
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int i = 0; i < 19; ++i) P[(s * 19 + i) * TX + x] = f[s][i];
+                mbar_arrive(full_s + 8u * b);
+            }
+        }
+    } else {
+        const float px = (float)x - 0.5f * (float)(L.Lx - 1), py = (float)y - 0.5f * (float)(L.Ly - 1);
+        unsigned rphase = 0u, fphase = 0u;  // bit k: parity of ring slot k's / full[k]'s next phase
+        auto wait_ring = [&](int p) {
+            const int slot = slot_of(p);
+            if (!ws_wait(rbar_s + 8u * slot, (rphase >> slot) & 1u, true)) atomicOr(d_err, 4);
+            rphase ^= 1u << slot;
+        };
+        wait_ring(zc0 - 1);
+        wait_ring(zc0);
+        for (int z = zc0; z < zc1; ++z) {
+            wait_ring(z + 1);
+            const int b = (z - zc0) % NP;
+            if (!ws_wait(full_s + 8u * b, (fphase >> b) & 1u, false)) atomicOr(d_err, 4);
+            fphase ^= 1u << b;
+            float f[2][19];
+            const float* P = pops + (size_t)b * 38 * TX;
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < 19; ++i) f[s][i] = P[(s * 19 + i) * TX + x];
+            collide_node<TX, ST>(ring, slot_of(z - 1), slot_of(z), slot_of(z + 1), x, y, z, f, m, L, dst, d_err, cm,
+                                 px, py);
+            // the buffer may take plane z + NP (released after the collision,
+            // so that the populations can stay in shared memory until used)
+            mbar_arrive(empty_s + 8u * b);
+        }
+    }
+    // no CTA leaves while another may still address its shared memory
+    cluster.sync();
+
+    // centre-of-mass partials of the written state (fixed-order reduction)
+    const int lane = t & 31, warp = t >> 5;
+    constexpr int nwarps = (2 * TX + 31) / 32;
+    double cmd[4] = {(double)cm[0], (double)cm[1], (double)cm[2], (double)cm[3]};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double a = cmd[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) red[4 * warp + q] = a;
+    }
+    __syncthreads();
+    __shared__ unsigned last;
+    const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            double a = lane < nwarps ? red[4 * lane + q] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) cp.p[4 * cta + q] = a;
+        }
+        if (lane == 0) {
+            __threadfence();
+            last = atomicAdd(cp.counter, 1u) == total - 1 ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+    if (last && warp == 0) {
+        __threadfence();
+        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        for (unsigned bb = lane; bb < total; bb += 32)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s4[q] += __ldcg(cp.p + 4LL * bb + q);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s4[q] += __shfl_down_sync(0xffffffffu, s4[q], o);
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cp.sum[q] = s4[q];
             const bool have = s4[0] > 0.0;
             for (int q = 0; q < 3; ++q) cp.sum[4 + q] = have ? s4[1 + q] / s4[0] : 0.0;
             *cp.counter = 0u;
@@ -772,24 +1062,79 @@ cudaError_t rows_for(bool query, const void* src, void* dst, const Layout& L, co
     return launch_rows<TX, kRowCluster, S, STAGED>(src, dst, L, m, zchunk, nchunks, cp, d_err, s);
 }
 
+// Resident CTAs per SM asked of the compiler for the warp-specialised
+// variant (2 TX threads, about 93 KB of shared memory at TX = 128: two CTAs
+// of 256 threads per SM).
+template <int TX>
+constexpr int ws_min_blocks() {
+    return TX >= 256 ? 1 : 256 / TX;
+}
+
+template <int TX, int CY, typename S>
+cudaError_t ws_for(bool query, const void* src, void* dst, const Layout& L, const Model& m, int zchunk,
+                   CentreParts cp, int* d_err, cudaStream_t s, int* resident) {
+    auto k = k_stream_collide_ws<TX, CY, ws_min_blocks<TX>(), S>;
+    const size_t smem = WsLayout<TX, CY>::bytes;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+        if (query) {
+            cudaGetLastError();
+            *resident = 0;
+            return cudaSuccess;
+        }
+        return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(2 * TX, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = CY;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (query) {
+        cfg.gridDim = dim3(1, CY, 1);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        *resident = n * CY;
+        return cudaSuccess;
+    }
+    FastModel fm;
+    for (int q = 0; q < 2; ++q) {
+        fm.inv_tau[q] = (float)(1.0 / m.tau[q]);
+        fm.tau[q] = (float)m.tau[q];
+        fm.rho_b[q] = (float)m.rho_b[q];
+    }
+    fm.G = (float)m.G;
+    cfg.gridDim = dim3(1, L.Ly, (L.Lz + zchunk - 1) / zchunk);
+    cfg.stream = s;
+    return cudaLaunchKernelEx(&cfg, k, (const S*)src, (S*)dst, L, fm, zchunk, cp, d_err);
+}
+
 template <int TX, typename S>
-cudaError_t rows_variant(bool staged, bool query, const void* src, void* dst, const Layout& L, const Model& m,
+cudaError_t rows_variant(int variant, bool query, const void* src, void* dst, const Layout& L, const Model& m,
                          int zchunk, CentreParts cp, int* d_err, cudaStream_t s, int* resident) {
-    if (staged) return rows_for<TX, S, true>(query, src, dst, L, m, zchunk, cp, d_err, s, resident);
+    if (variant == kRowWs) return ws_for<TX, kRowCluster, S>(query, src, dst, L, m, zchunk, cp, d_err, s, resident);
+    if (variant == kRowStaged) return rows_for<TX, S, true>(query, src, dst, L, m, zchunk, cp, d_err, s, resident);
     return rows_for<TX, S, false>(query, src, dst, L, m, zchunk, cp, d_err, s, resident);
 }
 
 // Dispatch on the row width, the storage type and the variant.
-cudaError_t rows_dispatch(int prec, bool staged, bool query, const void* src, void* dst, const Layout& L,
+cudaError_t rows_dispatch(int prec, int variant, bool query, const void* src, void* dst, const Layout& L,
                           const Model& m, int zchunk, CentreParts cp, int* d_err, cudaStream_t s, int* resident) {
 #define LBM_ROWS_TX(TXV)                                                                                        \
     if (L.Lx == TXV) {                                                                                          \
         if (prec == kFP32)                                                                                      \
-            return rows_variant<TXV, float>(staged, query, src, dst, L, m, zchunk, cp, d_err, s, resident);     \
+            return rows_variant<TXV, float>(variant, query, src, dst, L, m, zchunk, cp, d_err, s, resident);     \
         if (prec == kFP16Dev)                                                                                   \
-            return rows_variant<TXV, Dev<__half>>(staged, query, src, dst, L, m, zchunk, cp, d_err, s, resident); \
+            return rows_variant<TXV, Dev<__half>>(variant, query, src, dst, L, m, zchunk, cp, d_err, s, resident); \
         if (prec == kBF16Dev)                                                                                   \
-            return rows_variant<TXV, Dev<__nv_bfloat16>>(staged, query, src, dst, L, m, zchunk, cp, d_err, s,   \
+            return rows_variant<TXV, Dev<__nv_bfloat16>>(variant, query, src, dst, L, m, zchunk, cp, d_err, s,   \
                                                          resident);                                             \
     }
     LBM_ROWS_TX(32)
@@ -808,19 +1153,19 @@ bool rows_kernel_applies(const Layout& L, int prec, int periodic) {
     return L.Ly % kRowCluster == 0 && L.Lz >= 2;
 }
 
-int rows_kernel_resident_ctas(const Layout& L, int prec, bool staged) {
+int rows_kernel_resident_ctas(const Layout& L, int prec, int variant) {
     int n = 0;
     Model m = {};
     CentreParts cp = {};
-    if (rows_dispatch(prec, staged, true, nullptr, nullptr, L, m, 1, cp, nullptr, 0, &n) != cudaSuccess) return 0;
+    if (rows_dispatch(prec, variant, true, nullptr, nullptr, L, m, 1, cp, nullptr, 0, &n) != cudaSuccess) return 0;
     return n;
 }
 
-cudaError_t launch_stream_collide_rows(int prec, bool staged, const void* src, void* dst, const Layout& L,
+cudaError_t launch_stream_collide_rows(int prec, int variant, const void* src, void* dst, const Layout& L,
                                        const Model& m, const Grad& A, int zchunk, CentreParts cp, int* d_err,
                                        cudaStream_t s) {
     (void)A;  // this kernel reads the ghost shell written by the ghost kernel
-    return rows_dispatch(prec, staged, false, src, dst, L, m, zchunk, cp, d_err, s, nullptr);
+    return rows_dispatch(prec, variant, false, src, dst, L, m, zchunk, cp, d_err, s, nullptr);
 }
 
 }  // namespace lbmgb

@@ -95,16 +95,23 @@ struct Shape {
     int rows;       // 1: the row-tiled cluster kernel (lbm_fast.cu), 0: the generic tile kernel
     int tx, ty;     // tile of the x-y plane per CTA
     int zchunk;     // z planes marched per CTA
-    int staged;     // row kernel: 1 the bulk-copy staged variant, 0 direct loads
+    int variant;    // row kernel: kRowDirect, kRowStaged or kRowWs
     dim3 grid;
     int threads;
     size_t smem;
 };
 
+// Variants of the row kernel: per-thread loads of the pulled populations
+// (each plane read twice, the second time from L2), whole pulled rows staged
+// in shared memory by bulk copies, or loader and collider threads per row
+// (warp-specialised, each population read once).
+enum { kRowDirect = 0, kRowStaged = 1, kRowWs = 2 };
+
 // ---- launchers (lbm_step.cu) ----
-// staged_req: 1 direct loads, 2 staged, 0 automatic; mrt: the MRT collision
-// (generic kernel only)
-Shape choose_shape(const Layout& L, int prec, int periodic, int mrt, int ty_req, int zchunk_req, int staged_req,
+// variant_req: the row_variant of lbm_opts (1 direct loads, 2 staged,
+// 3 warp-specialised, 0 automatic); mrt: the MRT collision (generic kernel
+// only)
+Shape choose_shape(const Layout& L, int prec, int periodic, int mrt, int ty_req, int zchunk_req, int variant_req,
                    int num_sms);
 cudaError_t launch_init(int prec, void* f, const Layout& L, double R, double xi, double rho_hi, double rho_lo,
                         Grad A0, cudaStream_t s);
@@ -119,11 +126,10 @@ cudaError_t launch_centre(int prec, const void* f, const Layout& L, CentreParts 
 
 // ---- row-tiled cluster kernel (lbm_fast.cu): fp32 or 16-bit deviations, ghost boundary,
 //      Lx in {32, 64, 128, 256}, Ly % 8 == 0 ----
-// staged: the variant that stages whole pulled rows in shared memory with
-// bulk copies (cp.async.bulk) instead of per-thread loads.
+// variant: kRowDirect, kRowStaged or kRowWs.
 bool rows_kernel_applies(const Layout& L, int prec, int periodic);
-int rows_kernel_resident_ctas(const Layout& L, int prec, bool staged);
-cudaError_t launch_stream_collide_rows(int prec, bool staged, const void* src, void* dst, const Layout& L,
+int rows_kernel_resident_ctas(const Layout& L, int prec, int variant);
+cudaError_t launch_stream_collide_rows(int prec, int variant, const void* src, void* dst, const Layout& L,
                                        const Model& m, const Grad& A, int zchunk, CentreParts cp, int* d_err,
                                        cudaStream_t s);
 

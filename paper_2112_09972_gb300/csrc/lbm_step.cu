@@ -242,15 +242,15 @@ Layout make_layout(int Lx, int Ly, int Lz, int prec) {
     return L;
 }
 
-Shape choose_shape(const Layout& L, int prec, int periodic, int mrt, int ty_req, int zchunk_req, int staged_req,
+Shape choose_shape(const Layout& L, int prec, int periodic, int mrt, int ty_req, int zchunk_req, int variant_req,
                    int num_sms) {
     Shape sh;
     sh.rows = 0;
-    sh.staged = 0;
+    sh.variant = kRowDirect;
     if (ty_req <= 0 && !mrt && rows_kernel_applies(L, prec, periodic)) {
         // one CTA per row
-        const bool staged = staged_req == 2;
-        const int resident = rows_kernel_resident_ctas(L, prec, staged);
+        const int variant = variant_req == 2 ? kRowStaged : (variant_req == 3 ? kRowWs : kRowDirect);
+        const int resident = rows_kernel_resident_ctas(L, prec, variant);
         if (resident > 0) {
             // Chunks of about 32 planes (each chunk re-reads two planes) when
             // that gives at least half as many CTAs as fit on the GPU at
@@ -258,7 +258,12 @@ Shape choose_shape(const Layout& L, int prec, int periodic, int mrt, int ty_req,
             // the kernel faster at 128^3 and 256^3.  Small boxes take more
             // chunks (down to 8 planes) to reach the resident CTA count.
             int chunks = (L.Lz + 31) / 32;
-            if (2 * chunks * L.Ly < resident) {
+            if (variant == kRowWs) {
+                // long chunks, all CTAs resident at once when the rows fit
+                // (a second, partial wave would leave SMs idle)
+                if (resident >= L.Ly) chunks = resident / L.Ly;
+                if (chunks > L.Lz / 8) chunks = L.Lz / 8;
+            } else if (2 * chunks * L.Ly < resident) {
                 chunks = resident / L.Ly;
                 if (chunks > L.Lz / 8) chunks = L.Lz / 8;
             }
@@ -266,7 +271,7 @@ Shape choose_shape(const Layout& L, int prec, int periodic, int mrt, int ty_req,
             if (chunks < 1) chunks = 1;
             if (chunks > L.Lz) chunks = L.Lz;
             sh.rows = 1;
-            sh.staged = staged ? 1 : 0;
+            sh.variant = variant;
             sh.tx = L.Lx;
             sh.ty = 1;
             sh.zchunk = (L.Lz + chunks - 1) / chunks;
@@ -339,7 +344,7 @@ cudaError_t launch_centre(int prec, const void* f, const Layout& L, CentreParts 
 
 cudaError_t launch_stream_collide(int prec, const void* src, void* dst, const Layout& L, const Model& m,
                                   const Shape& sh, const Grad& A, CentreParts cp, int* d_err, cudaStream_t s) {
-    if (sh.rows) return launch_stream_collide_rows(prec, sh.staged != 0, src, dst, L, m, A, sh.zchunk, cp, d_err, s);
+    if (sh.rows) return launch_stream_collide_rows(prec, sh.variant, src, dst, L, m, A, sh.zchunk, cp, d_err, s);
     if (prec == kFP64) return stream_collide_t<double, double, kMaxThreadsF64>(src, dst, L, m, sh, cp, d_err, s);
     if (prec == kFP32) return stream_collide_t<float, float, kMaxThreadsF32>(src, dst, L, m, sh, cp, d_err, s);
     if (prec == kFP16Dev) return stream_collide_t<Dev<__half>, float, kMaxThreadsF32>(src, dst, L, m, sh, cp, d_err, s);

@@ -112,13 +112,12 @@ def test_initial_state_matches_storage_model(built, oracle_mod, storage):
     assert_within_one_spacing(g.populations(), o.populations(), box, False, (workloads.RHO_LO, 1.0), storage)
 
 
-# (box, periodic, tile_y): the row-tiled cluster kernel (widths 64 and 256,
-# automatic) and the generic tile kernel (tile_y > 0, and the periodic mode)
 # (box, periodic, tile_y, row variant): the row-tiled cluster kernel (widths
-# 64 and 256, per-thread loads and bulk-copy staging) and the generic tile
-# kernel (tile_y > 0, and the periodic mode)
+# 64 and 256; per-thread loads, bulk-copy staging, loader and collider
+# threads) and the generic tile kernel (tile_y > 0, and the periodic mode)
 CASES = [((64, 24, 20), False, 0, 1), ((256, 16, 12), False, 0, 1), ((64, 24, 20), False, 0, 2),
-         ((256, 16, 12), False, 0, 2), ((37, 29, 23), False, 3, 0), ((30, 26, 22), True, 4, 0)]
+         ((256, 16, 12), False, 0, 2), ((64, 24, 20), False, 0, 3), ((256, 16, 12), False, 0, 3),
+         ((37, 29, 23), False, 3, 0), ((30, 26, 22), True, 4, 0)]
 
 
 @pytest.mark.parametrize("storage", ["fp16dev", "bf16dev"])

@@ -56,11 +56,12 @@ def c1_reference(oracle_mod):
 
 @pytest.mark.parametrize("precision,tile_y,variant,tol_field,tol_D",
                          [("fp64", 0, 0, 1e-10, 1e-9), ("fp32", 0, 1, 1e-4, 1e-3), ("fp32", 0, 2, 1e-4, 1e-3),
-                          ("fp32", 8, 0, 1e-4, 1e-3)])
+                          ("fp32", 0, 3, 1e-4, 1e-3), ("fp32", 8, 0, 1e-4, 1e-3)])
 def test_config1_parity_after_2000_steps(built, c1_reference, precision, tile_y, variant, tol_field, tol_D):
     """fp32 runs every stream-collide kernel: the row-tiled cluster kernel
-    (a 32-wide box) with per-thread loads (variant 1) and with bulk-copy
-    staging (variant 2), and the generic tile kernel (tile_y = 8)."""
+    (a 32-wide box) with per-thread loads (variant 1), with bulk-copy staging
+    (variant 2) and with loader and collider threads (variant 3), and the
+    generic tile kernel (tile_y = 8)."""
     w = workloads.C1_PARITY
     g = DropletLBM((w.box,) * 3, w.R, w.visc, w.G, precision=precision, rho_hi=w.rho_hi, rho_lo=w.rho_lo, xi=w.xi,
                    tile_y=tile_y, row_variant=variant)
@@ -115,7 +116,8 @@ def test_interpolated_gradient_knots(built, oracle_mod):
 
 
 @pytest.mark.parametrize("precision,tile_y,variant,tol", [("fp64", 0, 0, 1e-12), ("fp32", 0, 1, 1e-5),
-                                                          ("fp32", 0, 2, 1e-5), ("fp32", 4, 0, 1e-5)])
+                                                          ("fp32", 0, 2, 1e-5), ("fp32", 0, 3, 1e-5),
+                                                          ("fp32", 4, 0, 1e-5)])
 def test_full_size_single_step_128(built, oracle_mod, precision, tile_y, variant, tol):
     """128^3 with the benchmark's launch shape (fp32, automatic: the row-tiled
     cluster kernel) and the generic tile kernel: one step from an oracle state."""
@@ -244,10 +246,10 @@ def test_box_frame_short_run(built, oracle_mod):
     assert rel_linf(g.populations(), o.populations()) <= 1e-12
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("box", [(64, 24, 20), (128, 16, 9), (32, 40, 5), (256, 8, 6)])
 def test_row_cluster_kernel_shapes(built, oracle_mod, box, variant):
-    """The row-tiled cluster kernel (both variants) on other widths, cluster
+    """The row-tiled cluster kernel (all variants) on other widths, cluster
     counts and short z extents (ragged last z chunk), fp32, 12 steps from a
     perturbed state."""
     tau = (1.0, 1.0)
@@ -261,3 +263,26 @@ def test_row_cluster_kernel_shapes(built, oracle_mod, box, variant):
     o.run(12, np.arange(12), hist)
     g.step(12)
     assert rel_linf(g.populations(), o.populations()) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16dev", "bf16dev"])
+@pytest.mark.parametrize("box,z_chunk", [((128, 32, 40), 8), ((64, 16, 13), 5), ((32, 8, 6), 1)])
+def test_warp_specialised_variant_bit_identical(built, oracle_mod, precision, box, z_chunk):
+    """Loader and collider threads (variant 3) compute the same node updates
+    as per-thread loads (variant 1) in the same order: with the same z chunks
+    (hence the same centre-of-mass partials and frame origin) the stored
+    states agree bit for bit after 25 steps of an OU-driven droplet, including
+    chunks of one plane and ragged last chunks."""
+    hist = inputs.ou_gradient_history(25, 20.0, 600.0, seed=11)
+    R = min(box) / 4.0
+    states = []
+    for variant in (1, 3):
+        g = DropletLBM(box, R, (0.5 / 3, 0.5 / 3), 3.5, precision=precision, rho_hi=1.0, rho_lo=workloads.RHO_LO,
+                       z_chunk=z_chunk, row_variant=variant)
+        assert g.launch_shape()[1] == z_chunk
+        g.set_gradient_table(np.arange(25), hist)
+        g.step(25)
+        states.append((g.populations(), g.deformation()[0]))
+        g.close()
+    assert np.array_equal(states[0][0], states[1][0])
+    assert states[0][1] == states[1][1]
