@@ -105,7 +105,7 @@ def lbm_windows(hist, edge, spinup, sample_every, nsamples, window=WINDOW, strid
 class Surrogate:
     """The MLP 9 W -> 256 -> 256 -> 256 -> 6 on the GPU."""
 
-    def __init__(self, window=WINDOW, stride=STRIDE, hidden=HIDDEN, max_batch=4096, seed=0, device=None):
+    def __init__(self, window=WINDOW, stride=STRIDE, hidden=HIDDEN, max_batch=16384, seed=0, device=None):
         import torch
 
         self.torch = torch
@@ -118,6 +118,8 @@ class Surrogate:
         self.net = MLP((9 * window,) + tuple(hidden) + (N_OUT,), max_batch=max_batch, seed=seed,
                        stream=self.stream.cuda_stream, device=self.device.index)
         self.max_batch = max_batch
+        self._copy_stream = torch.cuda.Stream(device=self.device)
+        self._staging = None  # two device buffers of max_batch windows (pinned-input pipeline)
 
     def close(self):
         self.net.close()
@@ -160,18 +162,56 @@ class Surrogate:
         return hist
 
     def predict(self, X):
-        """(M [n, 6] float32, D [n] float64) of windows X [n, 9 W] (numpy or a
-        CUDA tensor), as numpy arrays."""
+        """(M [n, 6] float32, D [n] float64) of windows X [n, 9 W] (numpy, a
+        CPU tensor or a CUDA tensor), as numpy arrays.
+
+        Host windows go to the GPU in chunks of max_batch.  From pinned
+        memory the copy of one chunk (on a copy stream, into one of two
+        staging buffers) overlaps the forward pass and D of the previous
+        chunk; from pageable memory the chunks are copied in turn."""
         torch = self.torch
+        n = int(X.shape[0])
         with torch.cuda.stream(self.stream):
-            Xd = X if isinstance(X, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32))
-            Xd = Xd.to(self.device).contiguous()
-            n = Xd.shape[0]
             m6 = torch.empty((n, N_OUT), dtype=torch.float32, device=self.device)
             D = torch.empty(n, dtype=torch.float64, device=self.device)
-            self.net.deformation(Xd, m6, D)
+            if isinstance(X, torch.Tensor) and X.is_cuda:
+                self.net.deformation(X.contiguous(), m6, D)
+            else:
+                Xh = X if isinstance(X, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32))
+                self._deformation_from_host(Xh.contiguous(), m6, D)
+            m6h = torch.empty(m6.shape, dtype=m6.dtype, pin_memory=True)
+            Dh = torch.empty(D.shape, dtype=D.dtype, pin_memory=True)
+            m6h.copy_(m6, non_blocking=True)
+            Dh.copy_(D, non_blocking=True)
             self.net.sync()
-            return m6.cpu().numpy(), D.cpu().numpy()
+            self.stream.synchronize()
+        return m6h.numpy(), Dh.numpy()
+
+    def _deformation_from_host(self, Xh, m6, D):
+        torch = self.torch
+        n, chunk = Xh.shape[0], self.max_batch
+        if not Xh.is_pinned():
+            for s in range(0, n, chunk):
+                e = min(n, s + chunk)
+                self.net.deformation(Xh[s:e].to(self.device), m6[s:e], D[s:e])
+            return
+        if self._staging is None:
+            self._staging = [torch.empty((chunk, Xh.shape[1]), dtype=torch.float32, device=self.device)
+                             for _ in range(2)]
+        done = [None, None]  # the network's stream is through with staging buffer b
+        for k, s in enumerate(range(0, n, chunk)):
+            e, b = min(n, s + chunk), k % 2
+            buf = self._staging[b][:e - s]
+            with torch.cuda.stream(self._copy_stream):
+                if done[b] is not None:
+                    self._copy_stream.wait_event(done[b])
+                buf.copy_(Xh[s:e], non_blocking=True)
+                ready = torch.cuda.Event()
+                ready.record(self._copy_stream)
+            self.stream.wait_event(ready)
+            self.net.deformation(buf, m6[s:e], D[s:e])
+            done[b] = torch.cuda.Event()
+            done[b].record(self.stream)
 
 
 def trajectory_windows(hist, spinup, sample_every, nsamples, window=WINDOW, stride=STRIDE):

@@ -93,3 +93,19 @@ def test_fallback_reruns_large_deformations_on_lbm(trained):
     assert np.allclose(D, Dt, rtol=1e-5, atol=1e-7)
     D2, fb2 = surrogate.trajectories_with_fallback(sur, hist, EDGE, SPINUP, EVERY, NSAMP)
     assert not fb2.any()  # D stays far below 0.4 at u_LBM = 0.1
+
+
+def test_pinned_pipeline_matches_pageable_and_device_inputs(trained):
+    """The same windows from pinned host memory (chunked copies overlapped
+    with the network), from pageable memory and from the device give the
+    same M and D bit for bit; 2,500 windows are three chunks of 1,024 and a
+    ragged one."""
+    import torch
+
+    sur = trained["sur"]
+    X = np.ascontiguousarray(trained["Xt"][:2500])
+    M0, D0 = sur.predict(X)
+    M1, D1 = sur.predict(torch.from_numpy(X).pin_memory())
+    M2, D2 = sur.predict(torch.from_numpy(X).cuda())
+    assert np.array_equal(M0, M1) and np.array_equal(D0, D1)
+    assert np.array_equal(M0, M2) and np.array_equal(D0, D2)
