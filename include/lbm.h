@@ -187,6 +187,8 @@ int lbm_sync(lbm_ctx* ctx);
  * unit principal axes as columns, axes[3*a + k] = component a of axis k, each
  * signed so its largest-magnitude component is positive; lambda (may be NULL)
  * receives l1, l2, l3; centre (may be NULL) the centre of mass of w.
+ * When no node has phi > 0 (no droplet phase) the tensor is undefined: D,
+ * axes, lambda and centre are NaN and the call still returns LBM_OK.
  * Synchronises.
  */
 int lbm_deformation(lbm_ctx* ctx, double* D, double axes[9], double lambda[3], double centre[3]);
@@ -442,12 +444,14 @@ int lbm_mlp_get_params(lbm_mlp* mlp, float* params);
 int lbm_mlp_set_params(lbm_mlp* mlp, const float* params);
 
 /* Outputs y [n, sizes[nlayers]] (device, float32) of inputs x [n, sizes[0]]
- * (device, float32), any n >= 0 (processed in chunks of max_batch).  Async. */
+ * (device, float32), any n >= 0 (processed in chunks of max_batch; x and y
+ * may be NULL when n = 0).  Async. */
 int lbm_mlp_forward(lbm_mlp* mlp, const float* x, float* y, int64_t n);
 
 /* For a network with 6 outputs read as M (xx, xy, xz, yy, yz, zz): the
  * outputs into m6 [n, 6] and D of Eq. 4 of each predicted M into D [n]
- * (device float64).  Async. */
+ * (device float64), any n >= 0 (n = 0 launches nothing and accepts NULL
+ * buffers).  Async. */
 int lbm_mlp_deformation(lbm_mlp* mlp, const float* x, int64_t n, float* m6, double* D);
 
 /* Loss and gradients of n samples (32 <= n <= max_batch, n % 32 == 0;

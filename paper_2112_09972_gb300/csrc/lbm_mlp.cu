@@ -1156,7 +1156,7 @@ int lbm_mlp_set_params(lbm_mlp* c, const float* params) {
 }
 
 int lbm_mlp_forward(lbm_mlp* c, const float* x, float* y, int64_t n) {
-    if (!c || !x || !y || n < 0) return LBM_EINVAL;
+    if (!c || n < 0 || (n > 0 && (!x || !y))) return LBM_EINVAL;
     cudaSetDevice(c->device);
     const int d0 = c->d[0], dL = c->d[c->L];
     for (int64_t s = 0; s < n; s += c->max_batch) {
@@ -1170,9 +1170,9 @@ int lbm_mlp_forward(lbm_mlp* c, const float* x, float* y, int64_t n) {
 }
 
 int lbm_mlp_deformation(lbm_mlp* c, const float* x, int64_t n, float* m6, double* D) {
-    if (!c || !x || !m6 || !D || n < 0 || c->d[c->L] != 6) return LBM_EINVAL;
+    if (!c || n < 0 || (n > 0 && (!x || !m6 || !D)) || c->d[c->L] != 6) return LBM_EINVAL;
     int st = lbm_mlp_forward(c, x, m6, n);
-    if (st) return st;
+    if (st || n == 0) return st;  // no launch for an empty batch
     k_deform_from_m<<<blocks_for(n, 128), 128, 0, c->stream>>>(m6, n, D);
     MLP_TRY(cudaGetLastError());
     return LBM_OK;
