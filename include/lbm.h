@@ -383,6 +383,22 @@ void lbm_destroy(lbm_ctx* ctx);
 const char* lbm_strerror(int code);
 
 /*
+ * Diagnostic of the failure path of the device-side waits (the paper has no
+ * counterpart).  Every kernel that waits on an mbarrier (the row kernels'
+ * density exchange and plane staging, the tensor-core GEMM's pipeline) bounds
+ * each wait by wall time; a wait that gives up raises a flag that the next
+ * synchronising call reports as LBM_ETIMEOUT, and the kernel returns without
+ * blocking.  This call runs one warp on `device` (< 0: the current device)
+ * that waits, with the same bounded wait as the row kernels, on an mbarrier
+ * with limit limit_ns (1e3 .. 1e10 ns): with arrive = 0 nothing arrives, the
+ * wait gives up after limit_ns and the call returns LBM_ETIMEOUT; with
+ * arrive = 1 the barrier completes first and the call returns LBM_OK.  Either
+ * way the device stays usable.  LBM_EINVAL for other arguments.
+ * Synchronises (its own stream).
+ */
+int lbm_selftest_wait(int64_t limit_ns, int32_t arrive, int32_t device);
+
+/*
  * Maffettone-Minale model (Sec. 2, Eqs. 1, 2, 4, 5) for n gradient histories
  * at once, one GPU thread per trajectory: the morphology tensor M starts at the
  * identity (a sphere) and follows

@@ -204,6 +204,18 @@ const char* lbm_strerror(int code) {
     }
 }
 
+int lbm_selftest_wait(int64_t limit_ns, int32_t arrive, int32_t device) {
+    if (limit_ns < 1000 || limit_ns > 10000000000LL || (arrive != 0 && arrive != 1)) return LBM_EINVAL;
+    if (device >= 0 && cudaSetDevice(device) != cudaSuccess) return LBM_ECUDA;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return LBM_ECUDA;
+    int gave_up = 0;
+    const cudaError_t e = launch_wait_selftest((unsigned long long)limit_ns, arrive, s, &gave_up);
+    cudaStreamDestroy(s);
+    if (e != cudaSuccess) return LBM_ECUDA;
+    return gave_up ? LBM_ETIMEOUT : LBM_OK;
+}
+
 int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[2], double G, const lbm_opts* opts) {
     if (!out) return LBM_EINVAL;
     *out = nullptr;

@@ -75,9 +75,31 @@ __device__ __forceinline__ void st_async_f2(unsigned raddr, float a, float b, un
                  : "memory");
 }
 
-// Upper bound on mbarrier polls before a wait gives up (the kernel then sets
-// error bit 4, reported as LBM_ETIMEOUT, and carries on without blocking).
-constexpr unsigned kWaitPolls = 1u << 20;
+// Wall-time bound of one mbarrier wait (%globaltimer, ns).  A wait that gives
+// up sets error bit 4, reported as LBM_ETIMEOUT, and the kernel carries on
+// without blocking.  The bound is on time, not on polls: try_wait may
+// suspend the thread for a while.
+constexpr unsigned long long kWaitNs = 2000000000ull;
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mbar_try_wait_cta(unsigned mbar, unsigned parity);
+// Bounded wait for the phase of the given parity (cluster scope when remote
+// st.async bytes count on the barrier); false when it gave up.
+__device__ __forceinline__ bool wait_bounded(unsigned mbar, unsigned parity, bool cluster_scope,
+                                             unsigned long long limit_ns) {
+    auto poll = [&]() { return cluster_scope ? mbar_try_wait(mbar, parity) : mbar_try_wait_cta(mbar, parity); };
+    if (poll()) return true;
+    const unsigned long long t0 = now_ns();
+    while (!poll())
+        if (now_ns() - t0 > limit_ns) return false;
+    return true;
+}
+__device__ __forceinline__ void mbar_arrive(unsigned mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
 
 template <int TX, int CY>
 struct FastLayout {
@@ -583,16 +605,8 @@ __global__ void __launch_bounds__(TX, MINB)
     auto stage_wait = [&](int p) {
         const int k = stage_of(p);
         const unsigned par = (sphase >> k) & 1u;
-        unsigned polls = 0;
-        bool ok = true;
-        while (!mbar_try_wait_cta(smbar_s + 8u * k, par)) {
-            if (++polls == kWaitPolls) {
-                atomicOr(d_err, 4);
-                ok = false;
-                break;
-            }
-        }
-        if (ok) pending &= ~(1u << k);
+        if (wait_bounded(smbar_s + 8u * k, par, false, kWaitNs)) pending &= ~(1u << k);
+        else atomicOr(d_err, 4);
         sphase ^= 1u << k;
     };
     auto stage_ptr = [&](int p) { return stage + (size_t)stage_of(p) * (SP::BYTES / 4); };
@@ -633,13 +647,7 @@ __global__ void __launch_bounds__(TX, MINB)
     auto wait_rows = [&](int p) {
         const int slot = slot_of(p);
         const unsigned par = (phase >> slot) & 1u;
-        unsigned polls = 0;
-        while (!mbar_try_wait(mbar_s + 8u * slot, par)) {
-            if (++polls == kWaitPolls) {
-                atomicOr(d_err, 4);
-                break;
-            }
-        }
+        if (!wait_bounded(mbar_s + 8u * slot, par, true, kWaitNs)) atomicOr(d_err, 4);
         phase ^= 1u << slot;
     };
 
@@ -686,9 +694,7 @@ __global__ void __launch_bounds__(TX, MINB)
         if (x == 0) {
             for (int k = 0; k < NST; ++k) {
                 if (!((pending >> k) & 1u)) continue;
-                unsigned polls = 0;
-                while (!mbar_try_wait_cta(smbar_s + 8u * k, ((sphase >> k) & 1u) ^ 1u) && ++polls < kWaitPolls) {
-                }
+                wait_bounded(smbar_s + 8u * k, ((sphase >> k) & 1u) ^ 1u, false, kWaitNs);
             }
         }
     }
@@ -783,25 +789,8 @@ struct WsLayout {
     static constexpr size_t bytes = sizeof(float) * (RING + POPS) + sizeof(unsigned long long) * NBAR;
 };
 
-__device__ __forceinline__ void mbar_arrive(unsigned mbar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
-}
-__device__ __forceinline__ unsigned long long now_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Wall-time bound of one wait of the warp-specialised kernel.
-constexpr unsigned long long kWsWaitNs = 2000000000ull;
-// Bounded wait for the phase of the given parity (cluster scope: remote
-// st.async bytes count on the ring barriers); false when it gave up.
 __device__ __forceinline__ bool ws_wait(unsigned mbar, unsigned parity, bool cluster_scope) {
-    auto poll = [&]() { return cluster_scope ? mbar_try_wait(mbar, parity) : mbar_try_wait_cta(mbar, parity); };
-    if (poll()) return true;
-    const unsigned long long t0 = now_ns();
-    while (!poll())
-        if (now_ns() - t0 > kWsWaitNs) return false;
-    return true;
+    return wait_bounded(mbar, parity, cluster_scope, kWaitNs);
 }
 
 template <int TX, int CY, int MINB, typename ST>
@@ -1145,6 +1134,24 @@ cudaError_t rows_dispatch(int prec, int variant, bool query, const void* src, vo
     return cudaErrorInvalidValue;
 }
 
+// Self-test of the bounded wait: one warp waits on an mbarrier that nothing
+// arrives on (arrive = 0), or that thread 0 completes first (arrive = 1),
+// with the helper every kernel of this file uses.
+__device__ int g_wait_selftest;
+__global__ void k_wait_selftest(unsigned long long limit_ns, int arrive) {
+    __shared__ __align__(8) unsigned long long bar;
+    const unsigned b = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b, 1u);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (arrive && threadIdx.x == 0) mbar_arrive(b);
+    __syncthreads();
+    const bool ok = wait_bounded(b, 0u, false, limit_ns);
+    if (threadIdx.x == 0) g_wait_selftest = ok ? 1 : 0;
+}
+
 }  // namespace
 
 bool rows_kernel_applies(const Layout& L, int prec, int periodic) {
@@ -1159,6 +1166,21 @@ int rows_kernel_resident_ctas(const Layout& L, int prec, int variant) {
     CentreParts cp = {};
     if (rows_dispatch(prec, variant, true, nullptr, nullptr, L, m, 1, cp, nullptr, 0, &n) != cudaSuccess) return 0;
     return n;
+}
+
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, int arrive, cudaStream_t s, int* gave_up) {
+    const int unset = -1;
+    cudaError_t e = cudaMemcpyToSymbolAsync(g_wait_selftest, &unset, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    k_wait_selftest<<<1, 32, 0, s>>>(limit_ns, arrive);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int r = unset;
+    if ((e = cudaMemcpyFromSymbolAsync(&r, g_wait_selftest, sizeof(int), 0, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if (r < 0) return cudaErrorUnknown;
+    *gave_up = r == 0 ? 1 : 0;
+    return cudaSuccess;
 }
 
 cudaError_t launch_stream_collide_rows(int prec, int variant, const void* src, void* dst, const Layout& L,

@@ -128,6 +128,10 @@ cudaError_t launch_centre(int prec, const void* f, const Layout& L, CentreParts 
 //      Lx in {32, 64, 128, 256}, Ly % 8 == 0 ----
 // variant: kRowDirect, kRowStaged or kRowWs.
 bool rows_kernel_applies(const Layout& L, int prec, int periodic);
+// One warp waits on an mbarrier with the kernels' bounded wait (limit_ns of
+// wall time); nothing arrives unless arrive.  *gave_up = 1 when the wait gave
+// up.  Synchronises s.
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, int arrive, cudaStream_t s, int* gave_up);
 int rows_kernel_resident_ctas(const Layout& L, int prec, int variant);
 cudaError_t launch_stream_collide_rows(int prec, int variant, const void* src, void* dst, const Layout& L,
                                        const Model& m, const Grad& A, int zchunk, CentreParts cp, int* d_err,

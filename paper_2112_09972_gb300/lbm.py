@@ -36,7 +36,7 @@ ABI_FUNCTIONS = [
     "lbm_mlp_create", "lbm_mlp_set_normalisation", "lbm_mlp_param_count", "lbm_mlp_get_params",
     "lbm_mlp_set_params", "lbm_mlp_forward", "lbm_mlp_deformation", "lbm_mlp_gradients", "lbm_mlp_train_step",
     "lbm_mlp_sync", "lbm_mlp_destroy", "lbm_mlp_set_tensor_path", "lbm_mm_integrate", "lbm_components", "lbm_surface_deformation",
-    "lbm_reinject_mass",
+    "lbm_reinject_mass", "lbm_selftest_wait",
 ]
 
 
@@ -131,6 +131,7 @@ def load_library(path=LIB_PATH):
         "lbm_mlp_set_tensor_path": (ctypes.c_int, [vp, ctypes.c_int32]),
         "lbm_surface_deformation": (ctypes.c_int, [vp, _DP, _DP, _DP]),
         "lbm_reinject_mass": (ctypes.c_int, [vp, ctypes.c_double, _DP]),
+        "lbm_selftest_wait": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]),
         "lbm_components": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int64, _I32P, _I64P, ctypes.c_int32]),
         "lbm_mm_integrate": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp, vp]),
@@ -526,6 +527,12 @@ class MLP:
     def set_tensor_path(self, path):
         """0: tcgen05 tensor cores where the shape allows (default); 1: mma.sync only."""
         _check(self._lib.lbm_mlp_set_tensor_path(self._h, int(path)), "lbm_mlp_set_tensor_path")
+
+
+def selftest_wait(limit_ns, arrive=False, device=-1):
+    """Status of lbm_selftest_wait: LBM_ETIMEOUT (-6) when nothing arrives and
+    the bounded device-side wait gives up after limit_ns, 0 when it completes."""
+    return int(load_library().lbm_selftest_wait(int(limit_ns), 1 if arrive else 0, int(device)))
 
 
 def mm_integrate(A, tau_d, chi, substeps=10, record_every=1, precision="fp64", want_M=False, stream=None):

@@ -70,3 +70,23 @@ def test_empty_batches_of_the_network(built):
     M, Dp = sur.predict(np.zeros((0, 576), dtype=np.float32))
     assert M.shape == (0, 6) and Dp.shape == (0,)
     sur.close()
+
+
+def test_bounded_wait_gives_up_and_the_device_stays_usable(built):
+    """Failure path of the device-side waits without a GPU fault: a warp waits
+    on an mbarrier that nothing arrives on; the bounded wait gives up after
+    its limit, the call reports LBM_ETIMEOUT, and the device then runs a
+    normal step.  A barrier that does complete reports success."""
+    import time
+
+    from paper_2112_09972_gb300.lbm import selftest_wait
+
+    t0 = time.perf_counter()
+    assert selftest_wait(5_000_000) == -6  # LBM_ETIMEOUT after 5 ms
+    assert time.perf_counter() - t0 < 5.0
+    assert selftest_wait(5_000_000, arrive=True) == 0
+    assert selftest_wait(10) == -1  # limit below 1 us: LBM_EINVAL
+    g = DropletLBM((32, 16, 12), 3.0, (0.5 / 3, 0.5 / 3), 3.5, precision="fp32", rho_hi=1.0, rho_lo=workloads.RHO_LO)
+    g.step(2)
+    g.sync()
+    assert np.isfinite(g.deformation()[0])
