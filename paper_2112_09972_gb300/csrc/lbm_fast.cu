@@ -30,6 +30,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include "lbm_centre.cuh"
 #include "lbm_dev.cuh"
 #include "lbm_internal.h"
 #include "lbm_lattice.cuh"
@@ -702,53 +703,8 @@ __global__ void __launch_bounds__(TX, MINB)
     cluster.sync();
 
     // centre-of-mass partials of the written state (fixed-order reduction)
-    const int lane = x & 31, warp = x >> 5;
-    constexpr int nwarps = (TX + 31) / 32;
     double cmd[4] = {(double)cm[0], (double)cm[1], (double)cm[2], (double)cm[3]};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        double a = cmd[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) red[4 * warp + q] = a;
-    }
-    __syncthreads();
-    __shared__ unsigned last;
-    const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    const unsigned total = gridDim.x * gridDim.y * gridDim.z;
-    if (warp == 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            double a = lane < nwarps ? red[4 * lane + q] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-            if (lane == 0) cp.p[4 * cta + q] = a;
-        }
-        if (lane == 0) {
-            __threadfence();
-            last = atomicAdd(cp.counter, 1u) == total - 1 ? 1u : 0u;
-        }
-    }
-    __syncthreads();
-    if (last && warp == 0) {
-        __threadfence();
-        double s4[4] = {0.0, 0.0, 0.0, 0.0};
-        for (unsigned bb = lane; bb < total; bb += 32)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) s4[q] += __ldcg(cp.p + 4LL * bb + q);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s4[q] += __shfl_down_sync(0xffffffffu, s4[q], o);
-        if (lane == 0) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) cp.sum[q] = s4[q];
-            // frame origin x_c = sum w x / sum w (box centre when there is no droplet)
-            const bool have = s4[0] > 0.0;
-            for (int q = 0; q < 3; ++q) cp.sum[4 + q] = have ? s4[1 + q] / s4[0] : 0.0;
-            *cp.counter = 0u;
-        }
-    }
+    centre_epilogue(cmd, cp, red);
 }
 
 // ---- Warp-specialised variant: loader and collider threads per row ----
@@ -919,52 +875,8 @@ __global__ void __launch_bounds__(2 * TX, MINB)
     cluster.sync();
 
     // centre-of-mass partials of the written state (fixed-order reduction)
-    const int lane = t & 31, warp = t >> 5;
-    constexpr int nwarps = (2 * TX + 31) / 32;
     double cmd[4] = {(double)cm[0], (double)cm[1], (double)cm[2], (double)cm[3]};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        double a = cmd[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) red[4 * warp + q] = a;
-    }
-    __syncthreads();
-    __shared__ unsigned last;
-    const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    const unsigned total = gridDim.x * gridDim.y * gridDim.z;
-    if (warp == 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            double a = lane < nwarps ? red[4 * lane + q] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-            if (lane == 0) cp.p[4 * cta + q] = a;
-        }
-        if (lane == 0) {
-            __threadfence();
-            last = atomicAdd(cp.counter, 1u) == total - 1 ? 1u : 0u;
-        }
-    }
-    __syncthreads();
-    if (last && warp == 0) {
-        __threadfence();
-        double s4[4] = {0.0, 0.0, 0.0, 0.0};
-        for (unsigned bb = lane; bb < total; bb += 32)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) s4[q] += __ldcg(cp.p + 4LL * bb + q);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s4[q] += __shfl_down_sync(0xffffffffu, s4[q], o);
-        if (lane == 0) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) cp.sum[q] = s4[q];
-            const bool have = s4[0] > 0.0;
-            for (int q = 0; q < 3; ++q) cp.sum[4 + q] = have ? s4[1 + q] / s4[0] : 0.0;
-            *cp.counter = 0u;
-        }
-    }
+    centre_epilogue(cmd, cp, red);
 }
 
 constexpr int kRowMinBlocks = 6;

@@ -7,6 +7,7 @@
 
 #include "lbm_dev.cuh"
 #include "lbm_internal.h"
+#include "lbm_centre.cuh"
 #include "lbm_lattice.cuh"
 
 namespace lbmgb {
@@ -97,58 +98,6 @@ struct Puller<Dev<T>, C, PER> {
     }
 };
 
-// Fixed-order reduction of the per-CTA centre partials by the last CTA to
-// finish (threadfence-reduction pattern); every thread of the CTA calls it.
-// `scratch` holds 4 doubles per warp of shared memory.
-__device__ void centre_epilogue(double (&cm)[4], CentreParts cp, double* scratch) {
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = (blockDim.x + 31) >> 5;
-    const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    const unsigned total = gridDim.x * gridDim.y * gridDim.z;
-    __shared__ unsigned last;
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        double a = cm[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) scratch[4 * warp + q] = a;
-    }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            double a = lane < nwarps ? scratch[4 * lane + q] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-            if (lane == 0) cp.p[4 * cta + q] = a;
-        }
-        if (lane == 0) {
-            __threadfence();
-            last = atomicAdd(cp.counter, 1u) == total - 1 ? 1u : 0u;
-        }
-    }
-    __syncthreads();
-    if (last && warp == 0) {
-        __threadfence();
-        double s4[4] = {0.0, 0.0, 0.0, 0.0};
-        for (unsigned b = lane; b < total; b += 32)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) s4[q] += __ldcg(cp.p + 4LL * b + q);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s4[q] += __shfl_down_sync(0xffffffffu, s4[q], o);
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) cp.sum[q] = s4[q];
-            // frame origin x_c = sum w x / sum w (box centre when there is no droplet)
-            const bool have = s4[0] > 0.0;
-            for (int q = 0; q < 3; ++q) cp.sum[4 + q] = have ? s4[1 + q] / s4[0] : 0.0;
-            *cp.counter = 0u;
-        }
-    }
-}
 
 // One CTA's share of the stream-collide step: the TX x TY tile at (x0, y0)
 // of the x-y plane, marched over planes [zc0, zc1).  blockDim.x may exceed
