@@ -204,15 +204,17 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_nt(GemmArgs g) {
 //                M 128, N BN, K 16) for each chunk, releases the stage with
 //                tcgen05.commit, and commits a finished tile to its
 //                accumulator's "full" mbarrier;
-//   warps 2-5 -- the epilogue: each warp reads its 32 TMEM lanes (rows) with
-//                tcgen05.ld, applies the fused epilogue, stores 16-byte
+//   warps 2-9 -- the epilogue: two warps per 32 TMEM lanes (rows), each
+//                taking every other 32-column block; a warp reads its block
+//                with tcgen05.ld, applies the fused epilogue, stores 16-byte
 //                vectors and hands the accumulator back (its "empty"
 //                mbarrier), while the tensor core fills the other one.
 // Every wait is bounded.  A wait that gives up sets bit 1 of *err and stops
 // every role; before the CTA exits, the copies and products it issued are
 // waited for (bounded) and the tensor memory is released.
 constexpr int TC_M = 128, TC_K = 64;
-constexpr int kTcThreads = 192;
+constexpr int kTcThreads = 320;
+constexpr int kTcEpiWarps = 8;  // warps 2 .. 9
 constexpr int kTcStages = 6;
 constexpr unsigned kTcTileA = TC_M * TC_K * 2;               // 16 KB
 constexpr unsigned kTcStageBytes = 2 * kTcTileA;             // A tile + B tile (BN <= 128 rows)
@@ -379,7 +381,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         for (int b = 0; b < 2; ++b) {
             tc_mbar_init(accf_bar(b), 1);
-            tc_mbar_init(acce_bar(b), 4);  // one arrival per epilogue warp
+            tc_mbar_init(acce_bar(b), kTcEpiWarps);  // one arrival per epilogue warp
         }
         tc_mbar_init(drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -478,7 +480,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             tc_commit(drain_bar);  // completes when every product issued above has
         }
     } else {
-        const int q = warp & 3;  // a warp reads TMEM lanes 32 (warp % 4) .. + 31
+        const int q = warp & 3;             // a warp reads TMEM lanes 32 (warp % 4) .. + 31
+        const int first = ((warp - 2) >> 2) * 32;  // and column blocks first, first + 64, ...
         unsigned tc = 0;
         for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++tc) {
             const int buf = (int)(tc & 1u);
@@ -494,7 +497,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             float* Cf = g.Cf ? g.Cf + (long long)(tile / tiles_mn) * g.c_split : nullptr;
             const int m = m0 + q * 32 + lane;
 #pragma unroll 1
-            for (int cb = 0; cb < sh.bn; cb += 32) {
+            for (int cb = first; cb < sh.bn; cb += 64) {
                 unsigned v[32];
                 const unsigned addr = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(buf * 128 + cb);
                 asm volatile(
