@@ -881,12 +881,17 @@ __global__ void __launch_bounds__(2 * TX, MINB)
 
 constexpr int kRowMinBlocks = 6;
 
-// Resident CTAs per SM asked of the compiler: 6 x 128 threads for the
-// direct-load variant; the staged variant is bounded by its shared memory
-// (about 2 x 128-thread CTAs per SM).
+// Resident CTAs per SM asked of the compiler (it sets the register budget).
+// Direct-load variant: 6 x 128 threads' worth (80 registers), except at
+// Lx = 128, where 4 CTAs (128 registers) step 1.7 % (fp32) and 2.8 % (fp16
+// deviations) faster at 128^3 -- the 512-CTA grid fills only 3.4 per SM, so
+// the bound costs no occupancy; at Lx = 256, 3 CTAs (80 registers) beat 2
+// (128 registers) by 2 % (fp32) and 13 % (fp16 deviations), measured on
+// GB300.  The staged variant is bounded by its shared memory (about 2 x
+// 128-thread CTAs per SM).
 template <int TX, bool STAGED>
 constexpr int row_min_blocks() {
-    return STAGED ? (256 / TX > 0 ? 256 / TX : 1) : kRowMinBlocks * 128 / TX;
+    return STAGED ? (256 / TX > 0 ? 256 / TX : 1) : (TX == 128 ? 4 : kRowMinBlocks * 128 / TX);
 }
 
 template <int TX, int CY, typename S, bool STAGED>
