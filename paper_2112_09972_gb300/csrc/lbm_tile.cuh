@@ -259,6 +259,27 @@ __device__ __forceinline__ void tile_march(const S* __restrict__ src, S* __restr
     }
 }
 
+// One 32-byte sector (8 floats or 4 doubles, 32-byte aligned) holding v at
+// position `lane` and zeros elsewhere, in two 16-byte stores.
+template <typename S>
+__device__ __forceinline__ void store_sector(S* p, int lane, S v);
+template <>
+__device__ __forceinline__ void store_sector<float>(float* p, int lane, float v) {
+    float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) e[k] = k == lane ? v : 0.f;
+    reinterpret_cast<float4*>(p)[0] = make_float4(e[0], e[1], e[2], e[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(e[4], e[5], e[6], e[7]);
+}
+template <>
+__device__ __forceinline__ void store_sector<double>(double* p, int lane, double v) {
+    double e[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) e[k] = k == lane ? v : 0.0;
+    reinterpret_cast<double2*>(p)[0] = make_double2(e[0], e[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(e[2], e[3]);
+}
+
 // Ghost populations of shell node (x, y, z) of box L (Eq. 8 at the boundary
 // density and the flow A (p - x_c), p measured from the box centre; Eq. 14):
 // written only for the directions that stream into the box.  Sets error
@@ -273,6 +294,13 @@ __device__ __forceinline__ void ghost_node(S* __restrict__ f, const Layout& L, c
     const C uz = A[6] * px + A[7] * py + A[8] * pz;
     const C usq = ux * ux + uy * uy + uz * uz;
     const C u2x = C(1.5) * usq;
+    // An x-face ghost sits alone in a 32-byte sector of row padding (x0 is
+    // one sector; when Lx fills whole sectors, so is the stretch after the
+    // row).  That sector is written whole -- the value and zero padding,
+    // which nothing reads -- so that no partial sector is merged with DRAM.
+    constexpr int SEC = 32 / (int)sizeof(S);
+    const bool whole = (x == -1 || x == L.Lx) && L.x0 == SEC && L.Lx % SEC == 0;
+    const int lane = x == -1 ? SEC - 1 : 0;  // the ghost's place in its sector
     bool any = false;
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
@@ -280,7 +308,11 @@ __device__ __forceinline__ void ghost_node(S* __restrict__ f, const Layout& L, c
         if (xi < 0 || xi >= L.Lx || yi < 0 || yi >= L.Ly || zi < 0 || zi >= L.Lz) continue;
         any = true;
 #pragma unroll
-        for (int s = 0; s < 2; ++s) f[L.at(s, i, x, y, z)] = (S)feq<C>(i, (C)m.rho_b[s], ux, uy, uz, u2x);
+        for (int s = 0; s < 2; ++s) {
+            const S v = (S)feq<C>(i, (C)m.rho_b[s], ux, uy, uz, u2x);
+            if (whole) store_sector<S>(f + L.at(s, i, x, y, z) - lane, lane, v);
+            else f[L.at(s, i, x, y, z)] = v;
+        }
     }
     if (any && (double)usq > m.mach2) atomicOr(d_err, 2);
 }
