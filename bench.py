@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--no-precision", action="store_true")
     p.add_argument("--no-surrogate", action="store_true")
     p.add_argument("--precision-steps", type=int, default=400)
+    p.add_argument("--no-variants", action="store_true")
     return p.parse_args()
 
 
@@ -404,6 +405,82 @@ def surrogate_bench(stream, dev, n_infer=65536, n_ref=512, n_train=1536, train_s
     }
 
 
+def variants_bench(stream, dev, steps=200):
+    """The method variants on the throughput case (128^3, fp32): MRT collision
+    (generic tile kernel) against BGK (row kernel) in MLUPS; the GPU
+    Maffettone-Minale model (Eqs. 1, 2, 5) in trajectories per second, fp32
+    and fp64; and the per-call cost of breakup detection, the surface-area
+    deformation of Eq. 17 and mass reinjection on the droplet state (median
+    of five synchronising calls)."""
+    import numpy as np
+    import torch
+
+    from paper_2112_09972_gb300 import inputs, workloads
+    from paper_2112_09972_gb300.lbm import DropletLBM, mm_integrate
+
+    w = workloads.C2_THROUGHPUT
+    hist = w.gradient_history(steps + 30)
+
+    def per_step(g, n):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.step(n)
+        b.record(stream)
+        g.sync()
+        return a.elapsed_time(b) / 1e3 / n
+
+    def median_call(fn):
+        ts = []
+        for _ in range(5):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return float(np.median(ts))
+
+    out = {"workload": w.name, "timed_steps": steps}
+    for name, mrt in (("bgk", None), ("mrt", True)):
+        g = DropletLBM((w.box,) * 3, w.R, w.visc, w.G, precision="fp32", rho_hi=w.rho_hi, rho_lo=w.rho_lo, xi=w.xi,
+                       stream=stream.cuda_stream, device=dev, mrt=mrt)
+        g.set_gradient_table(np.arange(hist.shape[0]), hist)
+        g.step(20)
+        g.sync()
+        s = per_step(g, steps)
+        out[name] = {"mlups": round(w.nodes / s / 1e6, 1), "us_per_step": round(s * 1e6, 1),
+                     "achieved_gbs_whole_step": round(BYTES_PER_LUP_FP32 * w.nodes / s / 1e9, 1),
+                     "kernel": "k_stream_collide_rows" if mrt is None else "k_stream_collide (generic tile, MRT)",
+                     "D": g.deformation()[0]}
+        if mrt is None:
+            # target: the current total mass of component A, a factor of one,
+            # so that the timed reinjections leave the state as it is
+            m_a = g.checksums()[0][0]
+            out["per_call_ms"] = {
+                "components": round(1e3 * median_call(lambda: g.components(0.0, 10)), 3),
+                "surface_deformation": round(1e3 * median_call(g.surface_deformation), 3),
+                "reinject_mass": round(1e3 * median_call(lambda: g.reinject_mass(m_a)), 3),
+                "deformation": round(1e3 * median_call(g.deformation), 3)}
+        g.close()
+    out["mrt_over_bgk_time"] = round(out["bgk"]["mlups"] / out["mrt"]["mlups"], 3)
+    # Maffettone-Minale: n OU gradient histories of T LBM steps (one seeded
+    # history per trajectory block, cycled), RK4 with 10 substeps per step
+    n, T = 16384, 1000
+    base = np.stack([inputs.ou_gradient_history(T, 200.0, 1000.0, seed=100 + k) for k in range(16)], axis=1)
+    A = torch.from_numpy(np.ascontiguousarray(np.tile(base, (1, n // 16, 1)))).to(dev)
+    mm = {"trajectories": n, "steps": T, "substeps": 10}
+    for prec in ("fp32", "fp64"):
+        with torch.cuda.stream(stream):
+            mm_integrate(A[:50], 30.0, 1.0, precision=prec, record_every=8, stream=stream.cuda_stream)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mm_integrate(A, 30.0, 1.0, precision=prec, record_every=8, stream=stream.cuda_stream)
+            b.record(stream)
+        b.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        mm[prec] = {"seconds": round(t, 4), "trajectories_per_s": round(n / t, 1)}
+    out["mm_model"] = mm
+    return out
+
+
 def run_reference(args, w):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -527,6 +604,9 @@ def main():
     sur = None
     if not args.no_surrogate and world == 1:
         sur = surrogate_bench(stream, dev)
+    var = None
+    if not args.no_variants and world == 1:
+        var = variants_bench(stream, dev)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -570,6 +650,7 @@ def main():
         "ensemble": ens,
         "precision": prec,
         "surrogate": sur,
+        "variants": var,
         "D_last": samples[-1] if samples else None,
     }
     print(json.dumps(line))
