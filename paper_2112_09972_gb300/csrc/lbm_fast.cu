@@ -30,6 +30,8 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "lbm_centre.cuh"
 #include "lbm_dev.cuh"
 #include "lbm_internal.h"
@@ -42,6 +44,7 @@ namespace {
 
 struct FastModel {
     float inv_tau[2], tau[2], G, rho_b[2];
+    float mrt[5];  // MRT free rates (s_e, s_eps, s_q, s_pi, s_m) when the kernel relaxes moments
 };
 
 // Shared-memory, cluster-address and mbarrier helpers (inline PTX).
@@ -387,13 +390,14 @@ struct StagedLayout {
 // density ring (slots s0, s1, s2 hold planes z - 1, z, z + 1; row 0 is this
 // CTA's row, rows -1 / +1 its neighbours, columns -1 and TX the x halo):
 // momentum (Eq. 6), Shan-Chen force (Eq. 7), common velocity with the force
-// shift, BGK relaxation to the equilibrium of Eq. 8 (Eqs. 9, 10), and the
-// store of the post-collision state (float32 populations with the rest
+// shift, BGK relaxation to the equilibrium of Eq. 8 (Eqs. 9, 10) -- or, with
+// MRT (float32 storage), the moment relaxation of the generic kernel -- and
+// the store of the post-collision state (float32 populations with the rest
 // population closing the mass balance, or 16-bit deviations).  Also
 // accumulates the centre-of-mass partials of the droplet phase and flags
 // non-finite densities.  Shared by the row kernels so that every variant
 // computes bit-identical states.
-template <int TX, typename ST>
+template <int TX, typename ST, bool MRT = false>
 __device__ __forceinline__ void collide_node(const float* ring, int s0, int s1, int s2, int x, int y, int z,
                                              const float (&f)[2][19], const FastModel& m, const Layout& L,
                                              ST* __restrict__ dst, int* __restrict__ d_err, float (&cm)[4], float px,
@@ -504,25 +508,40 @@ __device__ __forceinline__ void collide_node(const float* ring, int s0, int s1, 
             // rounding from drifting the interface
             const long long b = L.at(s, 0, x, y, z);
             float others = 0.f;
+            if constexpr (MRT) {
+                // MRT: relax the moments of the deviation from equilibrium
+                // (d'Humieres basis; momentum and stress at 1/tau)
+                float dv[19], out[19];
 #pragma unroll
-            for (int i = 1; i < 19; i += 2) {
-                const float cu = (float)cx_(i) * ux + (float)cy_(i) * uy + (float)cz_(i) * uz;
-                const float rw = r * wgt<float>(i);
-                const float even = rw * (1.f + 4.5f * cu * cu - u2x);
-                const float odd = rw * (3.f * cu);
-                const float fa = f[s][i], fb = f[s][i + 1];
-                const float oa = fa - (fa - (even + odd)) * it;
-                const float ob = fb - (fb - (even - odd)) * it;
-                __stcs(dst + b + (long long)i * L.array, oa);
-                __stcs(dst + b + (long long)(i + 1) * L.array, ob);
-                others += oa + ob;
+                for (int i = 0; i < 19; ++i) dv[i] = f[s][i] - feq<float>(i, r, ux, uy, uz, u2x);
+                mrt_relax<float>(f[s], dv, it, m.mrt, out);
+#pragma unroll
+                for (int i = 1; i < 19; i += 2) {
+                    __stcs(dst + b + (long long)i * L.array, out[i]);
+                    __stcs(dst + b + (long long)(i + 1) * L.array, out[i + 1]);
+                    others += out[i] + out[i + 1];
+                }
+            } else {
+#pragma unroll
+                for (int i = 1; i < 19; i += 2) {
+                    const float cu = (float)cx_(i) * ux + (float)cy_(i) * uy + (float)cz_(i) * uz;
+                    const float rw = r * wgt<float>(i);
+                    const float even = rw * (1.f + 4.5f * cu * cu - u2x);
+                    const float odd = rw * (3.f * cu);
+                    const float fa = f[s][i], fb = f[s][i + 1];
+                    const float oa = fa - (fa - (even + odd)) * it;
+                    const float ob = fb - (fb - (even - odd)) * it;
+                    __stcs(dst + b + (long long)i * L.array, oa);
+                    __stcs(dst + b + (long long)(i + 1) * L.array, ob);
+                    others += oa + ob;
+                }
             }
             __stcs(dst + b, r - others);
         }
     }
 }
 
-template <int TX, int CY, int MINB, typename ST, bool STAGED>
+template <int TX, int CY, int MINB, typename ST, bool STAGED, bool MRT = false>
 __global__ void __launch_bounds__(TX, MINB)
     k_stream_collide_rows(const ST* __restrict__ src, ST* __restrict__ dst, Layout L, FastModel m, int zchunk,
                           CentreParts cp, int* __restrict__ d_err) {
@@ -683,8 +702,8 @@ __global__ void __launch_bounds__(TX, MINB)
         }
         wait_rows(z + 1);
 
-        collide_node<TX, ST>(ring, slot_of(z - 1), slot_of(z), slot_of(z + 1), x, y, z, f, m, L, dst, d_err, cm, px,
-                             py);
+        collide_node<TX, ST, MRT>(ring, slot_of(z - 1), slot_of(z), slot_of(z + 1), x, y, z, f, m, L, dst, d_err, cm,
+                                  px, py);
         // Before a later plane reuses this plane's own-row slot, all threads
         // must be done reading it: the __syncthreads of the next iterations
         // (S > 3 planes apart) order that.
@@ -899,10 +918,10 @@ constexpr size_t row_smem() {
     return STAGED ? StagedLayout<TX, CY, S>::bytes : FastLayout<TX, CY>::bytes;
 }
 
-template <int TX, int CY, typename S, bool STAGED>
+template <int TX, int CY, typename S, bool STAGED, bool MRT>
 cudaError_t launch_rows(const void* src, void* dst, const Layout& L, const Model& m, int zchunk, int nchunks,
                         CentreParts cp, int* d_err, cudaStream_t s) {
-    auto k = k_stream_collide_rows<TX, CY, row_min_blocks<TX, STAGED>(), S, STAGED>;
+    auto k = k_stream_collide_rows<TX, CY, row_min_blocks<TX, STAGED>(), S, STAGED, MRT>;
     const size_t smem = row_smem<TX, CY, S, STAGED>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -913,6 +932,7 @@ cudaError_t launch_rows(const void* src, void* dst, const Layout& L, const Model
         fm.rho_b[q] = (float)m.rho_b[q];
     }
     fm.G = (float)m.G;
+    for (int k = 0; k < 5; ++k) fm.mrt[k] = (float)m.mrt_rates[k];
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(1, L.Ly, nchunks);
     cfg.blockDim = dim3(TX, 1, 1);
@@ -928,9 +948,9 @@ cudaError_t launch_rows(const void* src, void* dst, const Layout& L, const Model
     return cudaLaunchKernelEx(&cfg, k, (const S*)src, (S*)dst, L, fm, zchunk, cp, d_err);
 }
 
-template <int TX, int CY, typename S, bool STAGED>
+template <int TX, int CY, typename S, bool STAGED, bool MRT>
 int max_clusters() {
-    auto k = k_stream_collide_rows<TX, CY, row_min_blocks<TX, STAGED>(), S, STAGED>;
+    auto k = k_stream_collide_rows<TX, CY, row_min_blocks<TX, STAGED>(), S, STAGED, MRT>;
     const size_t smem = row_smem<TX, CY, S, STAGED>();
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
@@ -957,15 +977,15 @@ int max_clusters() {
 
 constexpr int kRowCluster = 8;
 
-template <int TX, typename S, bool STAGED>
+template <int TX, typename S, bool STAGED, bool MRT = false>
 cudaError_t rows_for(bool query, const void* src, void* dst, const Layout& L, const Model& m, int zchunk,
                      CentreParts cp, int* d_err, cudaStream_t s, int* resident) {
     if (query) {
-        *resident = max_clusters<TX, kRowCluster, S, STAGED>() * kRowCluster;
+        *resident = max_clusters<TX, kRowCluster, S, STAGED, MRT>() * kRowCluster;
         return cudaSuccess;
     }
     const int nchunks = (L.Lz + zchunk - 1) / zchunk;
-    return launch_rows<TX, kRowCluster, S, STAGED>(src, dst, L, m, zchunk, nchunks, cp, d_err, s);
+    return launch_rows<TX, kRowCluster, S, STAGED, MRT>(src, dst, L, m, zchunk, nchunks, cp, d_err, s);
 }
 
 // Resident CTAs per SM asked of the compiler for the warp-specialised
@@ -1025,6 +1045,11 @@ cudaError_t ws_for(bool query, const void* src, void* dst, const Layout& L, cons
 template <int TX, typename S>
 cudaError_t rows_variant(int variant, bool query, const void* src, void* dst, const Layout& L, const Model& m,
                          int zchunk, CentreParts cp, int* d_err, cudaStream_t s, int* resident) {
+    if (m.mrt) {  // MRT: float32 storage, direct loads only
+        if constexpr (std::is_same<S, float>::value)
+            return rows_for<TX, S, false, true>(query, src, dst, L, m, zchunk, cp, d_err, s, resident);
+        return cudaErrorInvalidValue;
+    }
     if (variant == kRowWs) return ws_for<TX, kRowCluster, S>(query, src, dst, L, m, zchunk, cp, d_err, s, resident);
     if (variant == kRowStaged) return rows_for<TX, S, true>(query, src, dst, L, m, zchunk, cp, d_err, s, resident);
     return rows_for<TX, S, false>(query, src, dst, L, m, zchunk, cp, d_err, s, resident);
@@ -1077,9 +1102,10 @@ bool rows_kernel_applies(const Layout& L, int prec, int periodic) {
     return L.Ly % kRowCluster == 0 && L.Lz >= 2;
 }
 
-int rows_kernel_resident_ctas(const Layout& L, int prec, int variant) {
+int rows_kernel_resident_ctas(const Layout& L, int prec, int variant, int mrt) {
     int n = 0;
     Model m = {};
+    m.mrt = mrt;
     CentreParts cp = {};
     if (rows_dispatch(prec, variant, true, nullptr, nullptr, L, m, 1, cp, nullptr, 0, &n) != cudaSuccess) return 0;
     return n;

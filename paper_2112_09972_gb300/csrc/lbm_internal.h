@@ -69,7 +69,7 @@ struct Model {
     int periodic;      // 1: periodic test mode, no ghosts
     double mach2;      // guard on |u_ghost|^2 (lattice units)
     int droplet_frame; // 1: ghost flow A (x - x_c), x_c the droplet's centre of mass
-    int mrt;           // 1: MRT collision (generic kernel) with the free rates below
+    int mrt;           // 1: MRT collision with the free rates below (row kernel for float32 storage, else generic)
     double mrt_rates[5];  // s_e, s_eps, s_q, s_pi, s_m
 };
 
@@ -109,8 +109,8 @@ enum { kRowDirect = 0, kRowStaged = 1, kRowWs = 2 };
 
 // ---- launchers (lbm_step.cu) ----
 // variant_req: the row_variant of lbm_opts (1 direct loads, 2 staged,
-// 3 warp-specialised, 0 automatic); mrt: the MRT collision (generic kernel
-// only)
+// 3 warp-specialised, 0 automatic); mrt: the MRT collision (the row kernel's
+// direct variant for float32 storage, the generic kernel otherwise)
 Shape choose_shape(const Layout& L, int prec, int periodic, int mrt, int ty_req, int zchunk_req, int variant_req,
                    int num_sms);
 cudaError_t launch_init(int prec, void* f, const Layout& L, double R, double xi, double rho_hi, double rho_lo,
@@ -132,7 +132,7 @@ bool rows_kernel_applies(const Layout& L, int prec, int periodic);
 // wall time); nothing arrives unless arrive.  *gave_up = 1 when the wait gave
 // up.  Synchronises s.
 cudaError_t launch_wait_selftest(unsigned long long limit_ns, int arrive, cudaStream_t s, int* gave_up);
-int rows_kernel_resident_ctas(const Layout& L, int prec, int variant);
+int rows_kernel_resident_ctas(const Layout& L, int prec, int variant, int mrt);
 cudaError_t launch_stream_collide_rows(int prec, int variant, const void* src, void* dst, const Layout& L,
                                        const Model& m, const Grad& A, int zchunk, CentreParts cp, int* d_err,
                                        cudaStream_t s);

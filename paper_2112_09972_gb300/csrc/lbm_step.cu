@@ -247,10 +247,11 @@ Shape choose_shape(const Layout& L, int prec, int periodic, int mrt, int ty_req,
     Shape sh;
     sh.rows = 0;
     sh.variant = kRowDirect;
-    if (ty_req <= 0 && !mrt && rows_kernel_applies(L, prec, periodic)) {
+    if (ty_req <= 0 && (!mrt || prec == kFP32) && rows_kernel_applies(L, prec, periodic)) {
         // one CTA per row
-        const int variant = variant_req == 2 ? kRowStaged : (variant_req == 3 ? kRowWs : kRowDirect);
-        const int resident = rows_kernel_resident_ctas(L, prec, variant);
+        // MRT rows: direct loads only
+        const int variant = mrt ? kRowDirect : (variant_req == 2 ? kRowStaged : (variant_req == 3 ? kRowWs : kRowDirect));
+        const int resident = rows_kernel_resident_ctas(L, prec, variant, mrt);
         if (resident > 0) {
             // Chunks of about 32 planes (each chunk re-reads two planes) when
             // that gives at least half as many CTAs as fit on the GPU at

@@ -1,4 +1,5 @@
-"""The MRT collision on the GPU (generic kernel) against the oracle's MRT
+"""The MRT collision on the GPU (the row kernel for float32 storage on
+row-tiled shapes, the generic kernel otherwise) against the oracle's MRT
 operator (oracle/lbm_oracle.cpp, pinned in tests/test_oracle_mrt.py).
 
 Tolerances as for BGK (tests/test_gpu_parity.py): float64 differs by the
@@ -27,10 +28,12 @@ def rel_linf(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
-@pytest.mark.parametrize("periodic", [False, True])
-def test_mrt_matches_oracle(built, oracle_mod, precision, tol, periodic):
-    box = (37, 29, 23)
+@pytest.mark.parametrize("precision,tol,periodic,box", [
+    ("fp64", 1e-12, False, (37, 29, 23)), ("fp64", 1e-12, True, (37, 29, 23)),
+    ("fp32", 2e-5, False, (37, 29, 23)), ("fp32", 2e-5, True, (37, 29, 23)),
+    ("fp32", 2e-5, False, (64, 24, 20)),    # the row kernel (64-wide rows, 3 clusters)
+    ("fp32", 2e-5, False, (128, 16, 14))])  # the row kernel, 128-wide rows, one short z chunk
+def test_mrt_matches_oracle(built, oracle_mod, precision, tol, periodic, box):
     tau = (0.9, 1.3)
     o = oracle_mod.OracleLBM(box, tau, 3.5, (workloads.RHO_LO, 1.0), periodic=periodic, mrt=RATES)
     g = DropletLBM(box, 5.0, ((tau[0] - 0.5) / 3, (tau[1] - 0.5) / 3), 3.5, precision=precision, periodic=periodic,
@@ -48,12 +51,16 @@ def test_mrt_matches_oracle(built, oracle_mod, precision, tol, periodic):
 
 
 def test_mrt_default_rates_and_shape(built):
-    """mrt=True takes the default free rates; MRT runs on the generic kernel
-    (tile_y > 0 in the launch shape)."""
+    """mrt=True takes the default free rates; with float32 storage on a
+    row-tiled shape MRT runs on the row kernel (tile_y = 1 in the launch
+    shape), with float64 storage on the generic kernel (tile_y > 1)."""
     w = workloads.C1_PARITY
+    g64 = DropletLBM((32, 32, 32), w.R, w.visc, w.G, precision="fp64", rho_lo=w.rho_lo, mrt=True)
+    assert g64.launch_shape()[0] > 1
+    g64.close()
     g = DropletLBM((32, 32, 32), w.R, w.visc, w.G, precision="fp32", rho_lo=w.rho_lo, mrt=True)
     ty, _, _ = g.launch_shape()
-    assert ty > 1
+    assert ty == 1
     g.set_gradient(inputs.simple_shear(w.shear_rate()), 0)
     g.step(200)
     D = g.deformation()[0]
