@@ -407,7 +407,7 @@ def surrogate_bench(stream, dev, n_infer=65536, n_ref=512, n_train=1536, train_s
 
 def variants_bench(stream, dev, steps=200):
     """The method variants on the throughput case (128^3, fp32): MRT collision
-    (generic tile kernel) against BGK (row kernel) in MLUPS; the GPU
+    against BGK in MLUPS (the kernel each runs on is named); the GPU
     Maffettone-Minale model (Eqs. 1, 2, 5) in trajectories per second, fp32
     and fp64; and the per-call cost of breakup detection, the surface-area
     deformation of Eq. 17 and mass reinjection on the droplet state (median
@@ -448,7 +448,7 @@ def variants_bench(stream, dev, steps=200):
         s = per_step(g, steps)
         out[name] = {"mlups": round(w.nodes / s / 1e6, 1), "us_per_step": round(s * 1e6, 1),
                      "achieved_gbs_whole_step": round(BYTES_PER_LUP_FP32 * w.nodes / s / 1e9, 1),
-                     "kernel": "k_stream_collide_rows" if mrt is None else "k_stream_collide (generic tile, MRT)",
+                     "kernel": "k_stream_collide_rows" if g.launch_shape()[0] == 1 else "k_stream_collide (generic tile)",
                      "D": g.deformation()[0]}
         if mrt is None:
             # target: the current total mass of component A, a factor of one,
