@@ -189,8 +189,21 @@ def cpu_baseline(w, hist, steps=None):
         if (n is not None and done >= n) or (n is None and (el > 12.0 or done >= 60)):
             break
     mlups = w.nodes * done / el / 1e6
+    # the same oracle on one thread, a shorter sample (one to three steps)
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    done1 = 0
+    while True:
+        o.step(hist[done + done1 + 1])
+        done1 += 1
+        el1 = time.perf_counter() - t1
+        if el1 > 6.0 or done1 >= 3:
+            break
+    oracle.set_threads(cores)
     return {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{done} steps of the full {w.box}^3 box (FP64, all host cores), {el:.1f} s"}
+            "sample": f"{done} steps of the full {w.box}^3 box (FP64, all host cores), {el:.1f} s",
+            "single_thread": {"value": round(w.nodes * done1 / el1 / 1e6, 4), "unit": "MLUPS",
+                              "sample": f"{done1} further steps on one thread, {el1:.1f} s"}}
 
 
 def ensemble_bench(steps, stream, dev):
