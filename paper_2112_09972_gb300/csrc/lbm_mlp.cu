@@ -5,14 +5,17 @@
 // Sec. 2, Eq. 4; M = identity for a sphere, the Maffettone-Minale tensor of
 // Eqs. 1, 2).  Forward pass, backward pass and Adam run on the GPU:
 //
-//   k_gemm_tc   -- C = A B^T on the 5th-generation tensor cores (tcgen05.mma,
-//                  accumulator in tensor memory) for 128 x 128 tiles, A [M, K]
-//                  and B [N, K] with K contiguous, fused epilogues (bias +
-//                  ReLU to bfloat16, ReLU-derivative mask to bfloat16,
-//                  float32 output)
+//   k_gemm_tc   -- C = A B^T on the 5th-generation tensor cores: a
+//                  persistent, warp-specialised kernel (TMA loads into a
+//                  shared-memory ring, tcgen05.mma into a double-buffered
+//                  tensor-memory accumulator, eight epilogue warps) over
+//                  128 x BN tiles (BN 128, 64 or 32) and split-K slices; A
+//                  [M, K] and B [N, K] with K contiguous; fused epilogues
+//                  (bias + ReLU to bfloat16, ReLU-derivative mask to
+//                  bfloat16, float32 output)
 //   k_gemm_nt   -- the same on warp-level tensor cores (mma.sync m16n8k16,
 //                  float32 accumulation) for the shapes k_gemm_tc does not
-//                  tile (ragged M or N, the 32-wide output layer)
+//                  tile (M not a multiple of 128, N not of 32, K not of 64)
 //   k_transpose -- bfloat16 tile transpose (operands of the weight gradients)
 //   k_prep, k_loss_grad, k_colsum_*, k_splitsum, k_adam, k_weights, k_output,
 //   k_deform_from_m -- input normalisation, mean-square loss and its
