@@ -8,8 +8,8 @@
 // marches a chunk of z planes; CY consecutive rows form a thread-block
 // cluster.  Per plane and thread (one node x):
 //   * the 38 populations pulled into the node (x - c_i) are read and summed
-//     into the node's post-streaming densities, which go into a four-slot
-//     ring of density planes in shared memory; one plane later the same 38
+//     into the node's post-streaming densities, which go into a ring of
+//     density planes in shared memory (CY + 2 slots); one plane later the same 38
 //     values are read again for the collision (that second read is served by
 //     L1/L2).  Holding no populations on chip keeps each CTA at a few KB of
 //     shared memory and few registers, so many CTAs per SM hide the latency;
@@ -26,6 +26,13 @@
 //
 // Sums over opposite velocity pairs are differenced first (c_{2k} = -c_{2k-1}),
 // and the equilibria of a pair share their even part.
+//
+// Variants (lbm_opts.row_variant): the direct loads above (the automatic
+// choice); whole pulled rows staged in shared memory by bulk copies
+// (k_stream_collide_rows<..., STAGED = true>); and loader and collider
+// threads per row (k_stream_collide_ws).  All three share collide_node and
+// store bit-identical states.  The direct variant also has an MRT instance
+// for float32 storage (collide_node<..., MRT = true>).
 
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
