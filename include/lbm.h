@@ -98,7 +98,9 @@ typedef enum {
     /* multi-relaxation-time collision (Sec. 2), d'Humieres et al. (2002)
        D3Q19 moment basis: g* = g - M^-1 S M (g - g_eq); stress and momentum
        moments relax at 1/tau (Eq. 10; the velocity-shift forcing), the others
-       at opts->mrt_rates.  Runs on the generic kernel. */
+       at opts->mrt_rates.  Runs in the row kernel for LBM_FP32 storage on
+       boxes with box[0] in {32, 64, 128, 256} and box[1] a multiple of 8
+       (ghost boundary), on the generic kernel otherwise. */
     LBM_COLLISION_MRT = 1
 } lbm_collision;
 
