@@ -306,9 +306,13 @@ int lbm_launch_shape(lbm_ctx* ctx, int32_t* tile_y, int32_t* z_chunk, int32_t* c
  * (1024 blocks x 10 doubles), held by every GPU that loads the library until
  * the process exits.  Its device address is looked up on the first call on
  * each device (with that device current): make that first call before any
- * stream capture starts.  All calls share the array, so calls whose kernels
- * may run concurrently on the GPU (unordered streams) race and give wrong
- * results; calls ordered on one stream are safe.
+ * stream capture starts.  After cudaDeviceReset of a device the cached
+ * address is stale: do not call this entry point on that device again in the
+ * same process.  All calls share the array, so calls whose kernels may run
+ * concurrently on the GPU (unordered streams) race and give wrong results;
+ * calls ordered on one stream are safe.  Returns LBM_ECUDA when one of the
+ * call's own two launches fails (an error left by an earlier, unrelated call
+ * is neither reported nor cleared).
  */
 int lbm_moments_static(const void* f, int32_t precision, const int32_t box[3], double* out, void* cuda_stream);
 

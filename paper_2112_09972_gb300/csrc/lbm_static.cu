@@ -15,11 +15,20 @@
 // exits.  In host code its name is only a host-side stand-in, so its device
 // address is looked up with cudaGetSymbolAddress, once per device, on the
 // first call made while that device is current.  Make that first call before
-// any stream capture begins.  All calls share the one array: two calls whose
-// kernels overlap on the GPU (different streams, no ordering between them)
-// race on it and give wrong results; calls on one stream are ordered and safe.
-// Every block overwrites its own slot of partial sums before the final
-// reduction reads it, so no part of the array has to start at zero.
+// any stream capture begins.  The cached address belongs to the device's
+// current primary context: after cudaDeviceReset (which discards that
+// context and the array with it) the cache is stale, so a process that resets
+// a device must not call this entry point on it again.  A launch that fails
+// drops the cached address of the device, so the next call looks it up anew.
+// All calls share the one array: two calls whose kernels overlap on the GPU
+// (different streams, no ordering between them) race on it and give wrong
+// results; calls on one stream are ordered and safe.  Every block overwrites
+// its own slot of partial sums before the final reduction reads it, so no
+// part of the array has to start at zero.
+//
+// The call's status is that of its own two launches (the return codes of
+// cudaLaunchKernel), not the thread's last-error state, so an error left by
+// an earlier, unrelated call is neither reported here nor cleared.
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -27,6 +36,7 @@
 #include <mutex>
 
 #include "../../include/lbm.h"
+#include "lbm_eigen.cuh"
 
 namespace {
 
@@ -38,8 +48,9 @@ static __device__ __align__(256) double g_moment_scratch[kStaticBlocks * 10];
 std::mutex g_scratch_mutex;
 double* g_scratch_ptr[128] = {nullptr};
 
-// Device address of the scratch array on the current device (looked up once).
-int scratch_for_current_device(double** out) {
+// Device address of the scratch array on the current device (looked up once
+// per device; *dev_out receives the device index).
+int scratch_for_current_device(double** out, int* dev_out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ECUDA;
     if (dev < 0 || dev >= 128) return LBM_ECUDA;
@@ -50,7 +61,14 @@ int scratch_for_current_device(double** out) {
         g_scratch_ptr[dev] = (double*)p;
     }
     *out = g_scratch_ptr[dev];
+    *dev_out = dev;
     return LBM_OK;
+}
+
+// Forget the cached address of device dev (after a failed launch).
+void drop_scratch(int dev) {
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    g_scratch_ptr[dev] = nullptr;
 }
 
 // Per-block sums of the ten moments of w = max(phi, 0) over a dense
@@ -101,42 +119,10 @@ __global__ void __launch_bounds__(kStaticThreads) k_moments_dense(const S* __res
     }
 }
 
-// Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations.
-__device__ void jacobi3_static(double a[3][3], double lam[3], double v[3][3]) {
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) v[i][j] = (i == j) ? 1.0 : 0.0;
-    for (int sweep = 0; sweep < 64; ++sweep) {
-        const double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
-        const double scale = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]);
-        if (off <= 1e-300 || off <= 1e-17 * scale) break;
-        for (int p = 0; p < 2; ++p)
-            for (int q = p + 1; q < 3; ++q) {
-                if (a[p][q] == 0.0) continue;
-                const double theta = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
-                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < 3; ++k) {
-                    const double akp = a[k][p], akq = a[k][q];
-                    a[k][p] = c * akp - s * akq;
-                    a[k][q] = s * akp + c * akq;
-                }
-                for (int k = 0; k < 3; ++k) {
-                    const double apk = a[p][k], aqk = a[q][k];
-                    a[p][k] = c * apk - s * aqk;
-                    a[q][k] = s * apk + c * aqk;
-                }
-                for (int k = 0; k < 3; ++k) {
-                    const double vkp = v[k][p], vkq = v[k][q];
-                    v[k][p] = c * vkp - s * vkq;
-                    v[k][q] = s * vkp + c * vkq;
-                }
-            }
-    }
-    for (int k = 0; k < 3; ++k) lam[k] = a[k][k];
-}
-
-// Sum the partials in block order; moments, D, axes, eigenvalues and centre
-// in the result layout of lbm_moments_static.
+// Sum the partials (each lane a strided subset of the blocks, then a warp
+// shuffle tree: a fixed order, so the result is deterministic) and derive the
+// moments, D, axes, eigenvalues and centre in the result layout of
+// lbm_deformation, with the same eigen-solver as the context-based path.
 __global__ void k_moments_dense_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
     const int lane = threadIdx.x;
     double m[10];
@@ -148,35 +134,7 @@ __global__ void k_moments_dense_final(const double* __restrict__ partials, int n
         for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
         m[k] = a;
     }
-    if (lane != 0) return;
-    for (int k = 0; k < 10; ++k) out[k] = m[k];
-    const double mass = m[0];
-    const double c[3] = {m[1] / mass, m[2] / mass, m[3] / mass};
-    double I[3][3];
-    I[0][0] = m[4] / mass - c[0] * c[0];
-    I[0][1] = I[1][0] = m[5] / mass - c[0] * c[1];
-    I[0][2] = I[2][0] = m[6] / mass - c[0] * c[2];
-    I[1][1] = m[7] / mass - c[1] * c[1];
-    I[1][2] = I[2][1] = m[8] / mass - c[1] * c[2];
-    I[2][2] = m[9] / mass - c[2] * c[2];
-    double lam[3], v[3][3];
-    jacobi3_static(I, lam, v);
-    int ord[3] = {0, 1, 2};
-    for (int i = 0; i < 3; ++i)
-        for (int j = i + 1; j < 3; ++j)
-            if (lam[ord[j]] > lam[ord[i]]) { const int tmp = ord[i]; ord[i] = ord[j]; ord[j] = tmp; }
-    for (int k = 0; k < 3; ++k) {
-        const int col = ord[k];
-        int big = 0;
-        for (int a = 1; a < 3; ++a)
-            if (fabs(v[a][col]) > fabs(v[big][col])) big = a;
-        const double sgn = v[big][col] < 0.0 ? -1.0 : 1.0;
-        for (int a = 0; a < 3; ++a) out[11 + 3 * a + k] = sgn * v[a][col];
-        out[20 + k] = lam[col];
-        out[23 + k] = c[k];
-    }
-    const double a1 = sqrt(fmax(lam[ord[0]], 0.0)), a3 = sqrt(fmax(lam[ord[2]], 0.0));
-    out[10] = (a1 - a3) / (a1 + a3);
+    if (lane == 0) lbmgb::deformation_from_moments(m, out);
 }
 
 }  // namespace
@@ -193,15 +151,23 @@ extern "C" int lbm_moments_static(const void* f, int32_t precision, const int32_
     // the scratch array whatever N is
     if (N > (1LL << 31) / 38) return LBM_EINVAL;
     double* scratch = nullptr;
-    int st = scratch_for_current_device(&scratch);
+    int dev = 0;
+    int st = scratch_for_current_device(&scratch, &dev);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     long long nb = (N + kStaticThreads - 1) / kStaticThreads;
-    const int blocks = (int)(nb < kStaticBlocks ? nb : kStaticBlocks);
-    if (precision == LBM_FP64)
-        k_moments_dense<double><<<blocks, kStaticThreads, 0, s>>>((const double*)f, box[0], box[1], box[2], scratch);
-    else
-        k_moments_dense<float><<<blocks, kStaticThreads, 0, s>>>((const float*)f, box[0], box[1], box[2], scratch);
-    k_moments_dense_final<<<1, 32, 0, s>>>(scratch, blocks, out);
-    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+    int blocks = (int)(nb < kStaticBlocks ? nb : kStaticBlocks);
+    int Lx = box[0], Ly = box[1], Lz = box[2];
+    void* args[] = {(void*)&f, &Lx, &Ly, &Lz, &scratch};
+    const void* k = precision == LBM_FP64 ? (const void*)k_moments_dense<double> : (const void*)k_moments_dense<float>;
+    cudaError_t e = cudaLaunchKernel(k, dim3(blocks), dim3(kStaticThreads), args, 0, s);
+    if (e == cudaSuccess) {
+        void* fargs[] = {&scratch, &blocks, &out};
+        e = cudaLaunchKernel((const void*)k_moments_dense_final, dim3(1), dim3(32), fargs, 0, s);
+    }
+    if (e != cudaSuccess) {
+        drop_scratch(dev);
+        return LBM_ECUDA;
+    }
+    return LBM_OK;
 }
