@@ -618,7 +618,7 @@ int lbm_save(lbm_ctx* c, const char* path) {
     CkptHeader h;
     memset(&h, 0, sizeof(h));
     memcpy(h.magic, "LBMGB300", 8);
-    h.version = 1;
+    h.version = 2;  // 2: row-interleaved device layout (raw buffers of deviation storage)
     for (int a = 0; a < 3; ++a) h.box[a] = c->box[a];
     h.prec = c->prec;
     h.bc = c->model.periodic;
@@ -652,7 +652,7 @@ int lbm_load(lbm_ctx* c, const char* path) {
     FILE* fp = fopen(path, "rb");
     if (!fp) return LBM_EIO;
     CkptHeader h;
-    if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 1) {
+    if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 2) {
         fclose(fp);
         return LBM_EIO;
     }

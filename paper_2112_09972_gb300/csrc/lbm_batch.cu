@@ -43,7 +43,7 @@ namespace lbmgb_batch {
 
 struct BatchBox {
     Layout L;
-    float* f[2];  // ping-pong population buffers (padded plane-major layout)
+    float* f[2];  // ping-pong population buffers (padded row-interleaved layout)
 };
 
 struct BatchItem {
@@ -176,8 +176,8 @@ __global__ void __launch_bounds__(256) k_batch_moments(const BatchBox* __restric
         float ra = 0.f, rb = 0.f;
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            ra += f[base + (long long)i * L.array];
-            rb += f[base + (long long)(19 + i) * L.array];
+            ra += f[base + (long long)i * L.pitch];
+            rb += f[base + (long long)(19 + i) * L.pitch];
         }
         const float phi = (ra - rb) / (ra + rb);
         const double w = phi > 0.f ? (double)phi : 0.0;

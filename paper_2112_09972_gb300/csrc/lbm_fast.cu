@@ -9,20 +9,37 @@
 // cluster.  Per plane and thread (one node x):
 //   * the 38 populations pulled into the node (x - c_i) are read and summed
 //     into the node's post-streaming densities, which go into a ring of
-//     density planes in shared memory (CY + 2 slots); one plane later the same 38
+//     density planes in shared memory (4 slots); one plane later the same 38
 //     values are read again for the collision (that second read is served by
-//     L1/L2).  Holding no populations on chip keeps each CTA at a few KB of
-//     shared memory and few registers, so many CTAs per SM hide the latency;
+//     L2).  Holding no populations on chip keeps each CTA at a few KB of
+//     shared memory, so many CTAs per SM hide the latency;
 //   * each CTA pushes its row of densities into the rings of the CTAs that
 //     own rows y -/+ 1 with st.async, which counts the bytes on the
 //     receiving CTA's mbarrier for that plane; the force (Eq. 7) then reads
 //     all 18 neighbour densities from local shared memory after a bounded
-//     mbarrier wait.  Only the two rows just outside the cluster are pulled
-//     a second time (ratio 2/CY); that work is split evenly over the CTAs of
-//     the cluster, which push those densities into the edge CTAs' rings.
+//     mbarrier wait.  The two rows just outside the cluster are pulled a
+//     second time by the two CTAs nearest each edge (half a row each), which
+//     push them into the edge CTA's ring.  Every CTA's ring is written only by
+//     itself and by the CTAs next to it, so no CTA runs more than one plane
+//     ahead of its neighbours and four ring slots suffice (proof at
+//     FastLayout).
 // There is no cluster-wide barrier and no memory fence per plane: a CTA waits
 // only for the two rows it reads.  DRAM sees about one read and one write of
 // every population; L2 serves the second read and the outer-halo reads.
+//
+// Addressing.  In the row-interleaved layout (lbm_internal.h) every
+// population a node pulls, and every population it writes, lies at a
+// compile-time byte offset (fixed by Lx) from one of three pointers to the
+// node's own element in planes z - 1, z, z + 1; the loads and stores carry
+// those offsets as immediates, so the per-node address arithmetic is three
+// pointer increments per plane.
+//
+// March direction.  Chunks with odd index march down in z, the others up, so
+// the two chunks that meet at a chunk boundary read the planes on either side
+// of it (each chunk's halo plane is the other's last plane) at the same time,
+// at the end or at the start of both marches, and L2 serves the second of
+// the two reads.  Every variant marches in the same order, so all three
+// store bit-identical states.
 //
 // Sums over opposite velocity pairs are differenced first (c_{2k} = -c_{2k-1}),
 // and the equilibria of a pair share their even part.
@@ -30,14 +47,15 @@
 // Variants (lbm_opts.row_variant): the direct loads above (the automatic
 // choice); whole pulled rows staged in shared memory by bulk copies
 // (k_stream_collide_rows<..., STAGED = true>); and loader and collider
-// threads per row (k_stream_collide_ws).  All three share collide_node and
-// store bit-identical states.  The direct variant also has an MRT instance
-// for float32 storage (collide_node<..., MRT = true>).
+// threads per row (k_stream_collide_ws).  All three share collide_node.  The
+// direct variant also has an MRT instance for float32 storage
+// (collide_node<..., MRT = true>).
 
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <type_traits>
+#include <utility>
 
 #include "lbm_centre.cuh"
 #include "lbm_dev.cuh"
@@ -46,13 +64,58 @@
 
 namespace cg = cooperative_groups;
 
+// Build-time launch parameters of the direct row kernel: resident CTAs per SM
+// asked of the compiler (its register budget) at each row width, and whether
+// odd chunks march down in z.
+#ifndef LBM_ROWS_MINB_32
+#define LBM_ROWS_MINB_32 24
+#endif
+#ifndef LBM_ROWS_MINB_64
+#define LBM_ROWS_MINB_64 12
+#endif
+#ifndef LBM_ROWS_MINB_128
+#define LBM_ROWS_MINB_128 5
+#endif
+#ifndef LBM_ROWS_MINB_256
+#define LBM_ROWS_MINB_256 3
+#endif
+#ifndef LBM_ROWS_ALTERNATE
+#define LBM_ROWS_ALTERNATE 1
+#endif
+
 namespace lbmgb {
 namespace {
 
 struct FastModel {
     float inv_tau[2], tau[2], G, rho_b[2];
-    float mrt[5];  // MRT free rates (s_e, s_eps, s_q, s_pi, s_m) when the kernel relaxes moments
+    float omit[2];  // 1 - 1/tau
+    float sh[2];    // -G tau: the velocity shift tau_s F^s / rho_s per unit of the other component's force sum
+    float mrt[5];   // MRT free rates (s_e, s_eps, s_q, s_pi, s_m) when the kernel relaxes moments
 };
+
+FastModel fast_model(const Model& m) {
+    FastModel fm;
+    for (int q = 0; q < 2; ++q) {
+        fm.inv_tau[q] = (float)(1.0 / m.tau[q]);
+        fm.tau[q] = (float)m.tau[q];
+        fm.rho_b[q] = (float)m.rho_b[q];
+        fm.omit[q] = (float)(1.0 - 1.0 / m.tau[q]);
+        fm.sh[q] = (float)(-m.G * m.tau[q]);
+    }
+    fm.G = (float)m.G;
+    for (int k = 0; k < 5; ++k) fm.mrt[k] = (float)m.mrt_rates[k];
+    return fm;
+}
+
+// Compile-time loop: f(std::integral_constant<int, 0>) ... f(..., N - 1).
+template <typename F, int... I>
+__device__ __forceinline__ void sfor_(F& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void sfor(F&& f) {
+    sfor_(f, std::make_integer_sequence<int, N>{});
+}
 
 // Shared-memory, cluster-address and mbarrier helpers (inline PTX).
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -78,6 +141,17 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned mbar, unsigned parity) {
         : "memory");
     return ok != 0u;
 }
+__device__ __forceinline__ bool mbar_try_wait_cta(unsigned mbar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
 // Store two floats into (possibly another CTA's) shared memory and count
 // 8 bytes on that CTA's mbarrier when they land.
 __device__ __forceinline__ void st_async_f2(unsigned raddr, float a, float b, unsigned rmbar) {
@@ -96,7 +170,6 @@ __device__ __forceinline__ unsigned long long now_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-__device__ __forceinline__ bool mbar_try_wait_cta(unsigned mbar, unsigned parity);
 // Bounded wait for the phase of the given parity (cluster scope when remote
 // st.async bytes count on the barrier); false when it gave up.
 __device__ __forceinline__ bool wait_bounded(unsigned mbar, unsigned parity, bool cluster_scope,
@@ -111,63 +184,6 @@ __device__ __forceinline__ bool wait_bounded(unsigned mbar, unsigned parity, boo
 __device__ __forceinline__ void mbar_arrive(unsigned mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
-
-template <int TX, int CY>
-struct FastLayout {
-    static constexpr int RW = TX + 2;            // ring row width (x halo columns -1, TX)
-    static constexpr int HN = 2 * TX / CY;       // outer-halo nodes pulled per CTA
-    // Density ring slots.  Plane p lives in slot p mod S.  The rows beyond
-    // the cluster are written by every CTA of the cluster, and a CTA can run
-    // at most CY - 1 planes ahead of the edge CTA it writes to, so S = CY + 2
-    // slots keep a slot's next plane from landing before its last reader.
-    static constexpr int S = CY + 2;
-    static constexpr int RING = S * 3 * RW * 2;  // [slot][row -1..1][col][component]
-    static constexpr unsigned TX_BYTES = 2u * TX * 2u * 4u;  // rows -1 and +1, both components
-    static constexpr size_t bytes = sizeof(float) * RING + sizeof(unsigned long long) * S;
-};
-
-// Pulled population (s, i) of the node whose (s=0, i=0) element index is b.
-// The first read of a plane keeps its lines in L2 (evict_last policy) for the
-// second read one plane later, which marks them last-use.
-__device__ __forceinline__ const float* pulled_ptr(const float* src, const Layout& L, long long b, int s, int i) {
-    return src + b + (long long)(s * 19 + i) * L.array -
-           ((long long)cz_(i) * L.plane + (long long)cy_(i) * L.pitch + cx_(i));
-}
-__device__ __forceinline__ float ld_keep(const float* p, unsigned long long pol) {
-    float v;
-    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
-    return v;
-}
-__device__ __forceinline__ float pulled(const float* __restrict__ src, const Layout& L, long long b, int s, int i,
-                                        unsigned long long pol) {
-    return ld_keep(pulled_ptr(src, L, b, s, i), pol);
-}
-__device__ __forceinline__ float pulled_last(const float* __restrict__ src, const Layout& L, long long b, int s, int i) {
-    return __ldlu(pulled_ptr(src, L, b, s, i));
-}
-
-// 16-bit deviation storage: the word of the deviation pair {A, B} of
-// direction i pulled into the node whose first word (i = 1) has index b, and
-// the node's own float4 block {rho*_A, rho*_B, f*_0A, f*_0B}.
-__device__ __forceinline__ const unsigned* dev_ptr(const unsigned* src, const Layout& L, long long b, int i) {
-    return src + b + (long long)(i - 1) * L.array -
-           ((long long)cz_(i) * (L.plane >> 1) + (long long)cy_(i) * L.pitch + cx_(i));
-}
-__device__ __forceinline__ unsigned ld_keep_u32(const unsigned* p, unsigned long long pol) {
-    unsigned v;
-    asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
-    return v;
-}
-__device__ __forceinline__ float4 ld_keep_f4(const float4* p, unsigned long long pol) {
-    float4 v;
-    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p), "l"(pol));
-    return v;
-}
-
-// ---- TMA-staged variant: bulk copies of whole pulled rows into shared memory ----
-
 // Bulk copy of `bytes` (a multiple of 16) from a 16-byte aligned global
 // address to this CTA's shared memory, counted on the CTA's mbarrier.
 __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned mbar) {
@@ -178,23 +194,254 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
 // Order this thread's earlier generic-proxy accesses to shared memory before
 // later async-proxy (bulk copy) writes to it.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ bool mbar_try_wait_cta(unsigned mbar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    return ok != 0u;
+
+// Global loads and stores at a pointer plus an immediate byte offset.  The
+// first read of a plane keeps its lines in L2 (evict_last policy) for the
+// second read one plane later, which marks them last-use; the written state
+// is streamed out.  The populations read are never written by the kernel, so
+// the loads may be scheduled freely.
+template <int OFF>
+__device__ __forceinline__ float ld_keep(const void* p, unsigned long long pol) {
+    float v;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1+%3], %2;" : "=f"(v) : "l"(p), "l"(pol), "n"(OFF));
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ float ld_last(const void* p) {
+    float v;
+    asm("ld.global.lu.f32 %0, [%1+%2];" : "=f"(v) : "l"(p), "n"(OFF));
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ unsigned ld_keep_u32(const void* p, unsigned long long pol) {
+    unsigned v;
+    asm("ld.global.nc.L2::cache_hint.b32 %0, [%1+%3], %2;" : "=r"(v) : "l"(p), "l"(pol), "n"(OFF));
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ unsigned ld_last_u32(const void* p) {
+    unsigned v;
+    asm("ld.global.lu.b32 %0, [%1+%2];" : "=r"(v) : "l"(p), "n"(OFF));
+    return v;
+}
+__device__ __forceinline__ float4 ld_keep_f4(const void* p, unsigned long long pol) {
+    float4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float4 ld_last_f4(const void* p) {
+    float4 v;
+    asm("ld.global.lu.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ void st_cs(void* p, float v) {
+    asm volatile("st.global.cs.f32 [%0+%2], %1;" ::"l"(p), "f"(v), "n"(OFF));
+}
+template <int OFF>
+__device__ __forceinline__ void st_cs_u32(void* p, unsigned v) {
+    asm volatile("st.global.cs.b32 [%0+%2], %1;" ::"l"(p), "r"(v), "n"(OFF));
+}
+__device__ __forceinline__ void st_cs_f4(void* p, float4 v) {
+    asm volatile("st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w));
 }
 
+// Compile-time geometry of the row-interleaved layout for row width TX (the
+// values make_layout computes): entries before x = 0, entries per population
+// row and layout units per row block (elements of 4 bytes for float32, units
+// of 2 bytes for deviations).
+template <int TX, typename ST>
+struct RowGeo;
+template <int TX>
+struct RowGeo<TX, float> {
+    static constexpr int X0 = 8, PITCH = TX + 16, ROW = 38 * PITCH;
+};
+template <int TX, typename T>
+struct RowGeo<TX, Dev<T>> {
+    static constexpr int X0 = 16, PITCH = TX + 32, ROW = 44 * PITCH;
+};
+
+// Storage-specific reads and writes of the row kernels.  A node's accesses
+// go through its pointer `base` (the node in plane -1) and, per plane p, the
+// three pointers P3 of planes p - 1, p, p + 1.
+template <int TX, typename ST>
+struct RowIO;
+
+template <int TX>
+struct RowIO<TX, float> {
+    using G = RowGeo<TX, float>;
+    struct P3 {
+        const char* m;
+        const char* o;
+        const char* p;
+    };
+    using Out = float*;  // element (s = 0, i = 0) of the node in the written plane
+    // element (s = 0, i = 0) of node (x, y) in plane -1
+    static __device__ __forceinline__ const char* base(const float* src, int x, int y) {
+        return reinterpret_cast<const char*>(src + (long long)(y + 1) * G::ROW + G::X0 + x);
+    }
+    // the same node, component s (the halo threads sum one component each)
+    static __device__ __forceinline__ const char* base_c(const float* src, int x, int y, int s) {
+        return base(src, x, y) + 4 * s * 19 * G::PITCH;
+    }
+    static __device__ __forceinline__ P3 planes(const char* b, const Layout& L, int p) {
+        const long long pl = 4 * L.plane;
+        const char* o = b + (long long)(p + 1) * pl;
+        return {o - pl, o, o + pl};
+    }
+    static __device__ __forceinline__ Out out(float* dst, const Layout& L, int x, int y, int z) {
+        return dst + (long long)(z + 1) * L.plane + (long long)(y + 1) * G::ROW + G::X0 + x;
+    }
+    // byte offset of population (s, i) pulled into the node (it comes from
+    // x - c_i, which lies in plane p - c_iz: the pointer src_plane picks)
+    template <int S, int I>
+    static constexpr int poff() {
+        return 4 * ((S * 19 + I) * G::PITCH - cy_(I) * G::ROW - cx_(I));
+    }
+    template <int I>
+    static __device__ __forceinline__ const char* src_plane(const P3& q) {
+        return cz_(I) > 0 ? q.m : (cz_(I) < 0 ? q.p : q.o);
+    }
+    // component S's post-streaming density (first read, kept in L2)
+    template <int S>
+    static __device__ __forceinline__ float density(const P3& q, unsigned long long pol) {
+        float r = ld_keep<poff<S, 0>()>(q.o, pol);
+        sfor<9>([&](auto K) {
+            constexpr int i = 2 * decltype(K)::value + 1;
+            r += ld_keep<poff<S, i>()>(src_plane<i>(q), pol) + ld_keep<poff<S, i + 1>()>(src_plane<i + 1>(q), pol);
+        });
+        return r;
+    }
+    static __device__ __forceinline__ void densities(const P3& q, unsigned long long pol, float& ra, float& rb) {
+        ra = density<0>(q, pol);
+        rb = density<1>(q, pol);
+    }
+    // the node's 38 pulled populations (second read, last use)
+    static __device__ __forceinline__ void populations(const P3& q, float (&f)[2][19]) {
+        sfor<19>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            f[0][i] = ld_last<poff<0, i>()>(src_plane<i>(q));
+            f[1][i] = ld_last<poff<1, i>()>(src_plane<i>(q));
+        });
+    }
+    // one read of the 38 pulled populations and the densities summed from
+    // them in the order of density() (the warp-specialised kernel)
+    static __device__ __forceinline__ void load_all(const P3& q, float (&f)[2][19], float& ra, float& rb) {
+        populations(q, f);
+        ra = f[0][0];
+        rb = f[1][0];
+#pragma unroll
+        for (int i = 1; i < 19; i += 2) {
+            ra += f[0][i] + f[0][i + 1];
+            rb += f[1][i] + f[1][i + 1];
+        }
+    }
+    template <int S, int I>
+    static __device__ __forceinline__ void store(Out o, float v) {
+        st_cs<4 * (S * 19 + I) * G::PITCH>(o, v);
+    }
+};
+
+// 16-bit deviation storage: per node the float4 block {rho*_A, rho*_B, f*_0A,
+// f*_0B} and the 18 words of deviation pairs {A, B}.  The plane pointers
+// point at the node's word slot (x0 + x) of its row block; the node's own
+// block lies a per-thread constant further (12 (x0 + x) bytes), and the word
+// of direction i at the immediate 4 (3 + i) pitch.
+template <int TX, typename T>
+struct RowIO<TX, Dev<T>> {
+    using G = RowGeo<TX, Dev<T>>;
+    struct P3 {
+        const char* m;
+        const char* o;
+        const char* p;
+        int blk;  // byte offset of the node's float4 block from o
+    };
+    struct Out {
+        unsigned* w;  // word slot of the node in the written plane
+        float4* b;    // the node's float4 block
+    };
+    static __device__ __forceinline__ const char* base(const Dev<T>* src, int x, int y) {
+        return reinterpret_cast<const char*>(src) + 2LL * (long long)(y + 1) * G::ROW + 4 * (G::X0 + x);
+    }
+    static __device__ __forceinline__ P3 planes(const char* b, const Layout& L, int p, int x) {
+        const long long pl = 2 * L.plane;
+        const char* o = b + (long long)(p + 1) * pl;
+        return {o - pl, o, o + pl, 12 * (G::X0 + x)};
+    }
+    static __device__ __forceinline__ Out out(Dev<T>* dst, const Layout& L, int x, int y, int z) {
+        char* o = reinterpret_cast<char*>(dst) + 2LL * ((long long)(z + 1) * L.plane + (long long)(y + 1) * G::ROW) +
+                  4 * (G::X0 + x);
+        return {reinterpret_cast<unsigned*>(o), reinterpret_cast<float4*>(o + 12 * (G::X0 + x))};
+    }
+    template <int I>
+    static constexpr int woff() {  // byte offset of the word of direction I pulled into the node
+        return 4 * (3 + I) * G::PITCH - 2 * cy_(I) * G::ROW - 4 * cx_(I);
+    }
+    template <int I>
+    static __device__ __forceinline__ const char* src_plane(const P3& q) {
+        return cz_(I) > 0 ? q.m : (cz_(I) < 0 ? q.p : q.o);
+    }
+    // sum_i (w_i rho* + d_i) + f*_0 = f*_0 + (1 - w_0) rho* + sum_i d_i
+    static __device__ __forceinline__ void densities(const P3& q, unsigned long long pol, float& ra, float& rb) {
+        const float4 o = ld_keep_f4(q.o + q.blk, pol);
+        float da = 0.f, db = 0.f;
+        sfor<9>([&](auto K) {
+            constexpr int i = 2 * decltype(K)::value + 1;
+            const float2 u = dev_unpack2<T>(ld_keep_u32<woff<i>()>(src_plane<i>(q), pol));
+            const float2 v = dev_unpack2<T>(ld_keep_u32<woff<i + 1>()>(src_plane<i + 1>(q), pol));
+            da += u.x + v.x;
+            db += u.y + v.y;
+        });
+        ra = o.z + (1.f - wgt<float>(0)) * o.x + da;
+        rb = o.w + (1.f - wgt<float>(0)) * o.y + db;
+    }
+    static __device__ __forceinline__ void populations(const P3& q, float (&f)[2][19]) {
+        const float4 o = ld_last_f4(q.o + q.blk);
+        f[0][0] = o.z;
+        f[1][0] = o.w;
+        sfor<18>([&](auto K) {
+            constexpr int i = decltype(K)::value + 1;
+            const float2 v = dev_unpack2<T>(ld_last_u32<woff<i>()>(src_plane<i>(q)));
+            f[0][i] = wgt<float>(i) * o.x + v.x;
+            f[1][i] = wgt<float>(i) * o.y + v.y;
+        });
+    }
+    // one read of the block and the 18 pulled words: the populations of
+    // populations() and the densities of densities(), with their arithmetic
+    static __device__ __forceinline__ void load_all(const P3& q, float (&f)[2][19], float& ra, float& rb) {
+        const float4 o = ld_last_f4(q.o + q.blk);
+        f[0][0] = o.z;
+        f[1][0] = o.w;
+        float da = 0.f, db = 0.f;
+        sfor<9>([&](auto K) {
+            constexpr int i = 2 * decltype(K)::value + 1;
+            const float2 u = dev_unpack2<T>(ld_last_u32<woff<i>()>(src_plane<i>(q)));
+            const float2 v = dev_unpack2<T>(ld_last_u32<woff<i + 1>()>(src_plane<i + 1>(q)));
+            da += u.x + v.x;
+            db += u.y + v.y;
+            f[0][i] = wgt<float>(i) * o.x + u.x;
+            f[1][i] = wgt<float>(i) * o.y + u.y;
+            f[0][i + 1] = wgt<float>(i + 1) * o.x + v.x;
+            f[1][i + 1] = wgt<float>(i + 1) * o.y + v.y;
+        });
+        ra = o.z + (1.f - wgt<float>(0)) * o.x + da;
+        rb = o.w + (1.f - wgt<float>(0)) * o.y + db;
+    }
+    template <int I>
+    static __device__ __forceinline__ void store_word(Out o, unsigned v) {
+        st_cs_u32<4 * (3 + I) * G::PITCH>(o.w, v);
+    }
+};
+
+// ---- TMA-staged variant: bulk copies of whole pulled rows into shared memory ----
+
 // Shared-memory image of one plane of one row for the staged variant: every
-// array the row's pulled populations come from, as a row segment that starts
-// at x = -4 (16-byte aligned) and covers x - c_ix for every x of the row.
-// Each source row is y - c_iy of plane p - c_iz, so over the grid every
-// population row is copied exactly once.
+// population row the row's pulled populations come from, as a row segment
+// that starts at x = -4 (16-byte aligned) and covers x - c_ix for every x of
+// the row.  Each source row is y - c_iy of plane p - c_iz, so over the grid
+// every population row is copied exactly once.
 template <int TX, typename ST>
 struct StagePlane;
 
@@ -272,151 +519,70 @@ struct StagePlane<TX, Dev<T>> {
     }
 };
 
-// Storage-specific reads and writes of the row kernel.  A node is named by
-// its plane-0 indices (NodeIx); plane p adds p planes.
-struct NodeIx {
-    long long a;  // float32: element of (s=0, i=0); deviations: float4 block index
-    long long b;  // deviations: 2-byte index of deviation (s=0, i=1)
-};
-
-template <typename S>
-struct RowIO;
-
-template <>
-struct RowIO<float> {
-    static __device__ __forceinline__ NodeIx node(const Layout& L, int x, int y) { return {L.at(0, 0, x, y, 0), 0}; }
-    // post-streaming densities of the node at plane p (first read, kept in L2)
-    static __device__ __forceinline__ void densities(const float* __restrict__ src, const Layout& L, NodeIx n, int p,
-                                                     unsigned long long keep, float& ra, float& rb) {
-        const long long b = n.a + (long long)p * L.plane;
-        ra = pulled(src, L, b, 0, 0, keep);
-        rb = pulled(src, L, b, 1, 0, keep);
-#pragma unroll
-        for (int i = 1; i < 19; i += 2) {
-            ra += pulled(src, L, b, 0, i, keep) + pulled(src, L, b, 0, i + 1, keep);
-            rb += pulled(src, L, b, 1, i, keep) + pulled(src, L, b, 1, i + 1, keep);
-        }
-    }
-    // the node's 38 pulled populations at plane p (second read, last use)
-    static __device__ __forceinline__ void populations(const float* __restrict__ src, const Layout& L, NodeIx n, int p,
-                                                       float (&f)[2][19]) {
-        const long long b = n.a + (long long)p * L.plane;
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int i = 0; i < 19; ++i) f[s][i] = pulled_last(src, L, b, s, i);
-    }
-    // one read of the 38 pulled populations and the densities summed from
-    // them in the order of densities() (the warp-specialised kernel)
-    static __device__ __forceinline__ void load_all(const float* __restrict__ src, const Layout& L, NodeIx n, int p,
-                                                    float (&f)[2][19], float& ra, float& rb) {
-        populations(src, L, n, p, f);
-        ra = f[0][0];
-        rb = f[1][0];
-#pragma unroll
-        for (int i = 1; i < 19; i += 2) {
-            ra += f[0][i] + f[0][i + 1];
-            rb += f[1][i] + f[1][i + 1];
-        }
-    }
-};
-
-template <typename T>
-struct RowIO<Dev<T>> {
-    static __device__ __forceinline__ NodeIx node(const Layout& L, int x, int y) {
-        return {L.dev_node(x, y, 0), L.dev_word(1, x, y, 0)};
-    }
-    static __device__ __forceinline__ void densities(const Dev<T>* __restrict__ src, const Layout& L, NodeIx n, int p,
-                                                     unsigned long long keep, float& ra, float& rb) {
-        const float4 o = ld_keep_f4(reinterpret_cast<const float4*>(src) + n.a + (long long)p * (L.plane >> 3), keep);
-        const unsigned* d = reinterpret_cast<const unsigned*>(src);
-        const long long b = n.b + (long long)p * (L.plane >> 1);
-        // sum_i (w_i rho* + d_i) + f*_0 = f*_0 + (1 - w_0) rho* + sum_i d_i
-        float da = 0.f, db = 0.f;
-#pragma unroll
-        for (int i = 1; i < 19; i += 2) {
-            const float2 u = dev_unpack2<T>(ld_keep_u32(dev_ptr(d, L, b, i), keep));
-            const float2 v = dev_unpack2<T>(ld_keep_u32(dev_ptr(d, L, b, i + 1), keep));
-            da += u.x + v.x;
-            db += u.y + v.y;
-        }
-        ra = o.z + (1.f - wgt<float>(0)) * o.x + da;
-        rb = o.w + (1.f - wgt<float>(0)) * o.y + db;
-    }
-    static __device__ __forceinline__ void populations(const Dev<T>* __restrict__ src, const Layout& L, NodeIx n, int p,
-                                                       float (&f)[2][19]) {
-        const float4 o = __ldlu(reinterpret_cast<const float4*>(src) + n.a + (long long)p * (L.plane >> 3));
-        const unsigned* d = reinterpret_cast<const unsigned*>(src);
-        const long long b = n.b + (long long)p * (L.plane >> 1);
-        f[0][0] = o.z;
-        f[1][0] = o.w;
-#pragma unroll
-        for (int i = 1; i < 19; ++i) {
-            const float2 v = dev_unpack2<T>(__ldlu(dev_ptr(d, L, b, i)));
-            f[0][i] = wgt<float>(i) * o.x + v.x;
-            f[1][i] = wgt<float>(i) * o.y + v.y;
-        }
-    }
-    // one read of the block and the 18 pulled words: the populations of
-    // populations() and the densities of densities(), with their arithmetic
-    static __device__ __forceinline__ void load_all(const Dev<T>* __restrict__ src, const Layout& L, NodeIx n, int p,
-                                                    float (&f)[2][19], float& ra, float& rb) {
-        const float4 o = __ldlu(reinterpret_cast<const float4*>(src) + n.a + (long long)p * (L.plane >> 3));
-        const unsigned* d = reinterpret_cast<const unsigned*>(src);
-        const long long b = n.b + (long long)p * (L.plane >> 1);
-        f[0][0] = o.z;
-        f[1][0] = o.w;
-        float da = 0.f, db = 0.f;
-#pragma unroll
-        for (int i = 1; i < 19; i += 2) {
-            const float2 u = dev_unpack2<T>(__ldlu(dev_ptr(d, L, b, i)));
-            const float2 v = dev_unpack2<T>(__ldlu(dev_ptr(d, L, b, i + 1)));
-            da += u.x + v.x;
-            db += u.y + v.y;
-            f[0][i] = wgt<float>(i) * o.x + u.x;
-            f[1][i] = wgt<float>(i) * o.y + u.y;
-            f[0][i + 1] = wgt<float>(i + 1) * o.x + v.x;
-            f[1][i + 1] = wgt<float>(i + 1) * o.y + v.y;
-        }
-        ra = o.z + (1.f - wgt<float>(0)) * o.x + da;
-        rb = o.w + (1.f - wgt<float>(0)) * o.y + db;
-    }
+// Density ring of the direct and staged row kernels: S slots, each three
+// rows (-1, 0, +1: the neighbour row below, this CTA's row, the neighbour row
+// above) of RW = TX + 2 columns (x = -1 .. TX) of float2 {rho_A, rho_B},
+// then S mbarriers.  Plane number k of the march (k = 0 .. n + 1) lives in
+// slot k mod S.
+//
+// Why S = 4 slots suffice.  The writers of a CTA b's ring are b itself and
+// the CTAs next to b in the cluster (its neighbour rows; the outer-halo rows
+// of an edge CTA come from the edge CTA and its neighbour).  Each writer a of
+// b is in turn written by b.  A CTA pushes plane k (march order) only after
+// it waited for plane k - 1 of its ring, i.e. after b pushed plane k - 1,
+// which b did only after it had collided plane k - 3.  Slot k mod S last held
+// plane k - S, whose last reader is the collision of plane k - S + 1 (it reads
+// planes k - S .. k - S + 2).  So b is done with the slot when a pushes into
+// it if k - S + 1 <= k - 3, i.e. S >= 4.  b's own threads write row 0 of the
+// slot only after the __syncthreads of the previous march step, which every
+// thread reaches after colliding plane k - 3: the same bound.  The barrier of
+// a slot therefore completes once per use, and the wait for plane k uses
+// parity (k / S) mod 2.
+template <int TX, int CY>
+struct FastLayout {
+    static constexpr int RW = TX + 2;
+    static constexpr int S = 4;
+    static constexpr int SLOT = 3 * RW;                  // float2 per slot
+    static constexpr unsigned TX_BYTES = 2u * TX * 8u;  // rows -1 and +1 of a slot land by st.async
+    static constexpr size_t ring_bytes = sizeof(float2) * S * SLOT;
+    static constexpr size_t bytes = ring_bytes + sizeof(unsigned long long) * S;
 };
 
 // Shared memory of the staged variant beyond the density ring: NST stage
 // mbarriers, then (128-byte aligned) NST plane images.
 template <int TX, int CY, typename ST>
 struct StagedLayout {
-    static constexpr int NST = 3;  // planes z+1 (resident), z+2 and z+3 (in flight)
+    static constexpr int NST = 3;  // march planes k (resident), k + 1 and k + 2 (in flight)
     static constexpr size_t mbar_off = FastLayout<TX, CY>::bytes;
     static constexpr size_t stage_off = ((mbar_off + 8 * NST + 127) / 128) * 128;
     static constexpr size_t bytes = stage_off + (size_t)NST * StagePlane<TX, ST>::BYTES;
 };
 
-// Collision of node (x, y, z) from its 38 pulled populations f and the
-// density ring (slots s0, s1, s2 hold planes z - 1, z, z + 1; row 0 is this
-// CTA's row, rows -1 / +1 its neighbours, columns -1 and TX the x halo):
-// momentum (Eq. 6), Shan-Chen force (Eq. 7), common velocity with the force
-// shift, BGK relaxation to the equilibrium of Eq. 8 (Eqs. 9, 10) -- or, with
-// MRT (float32 storage), the moment relaxation of the generic kernel -- and
-// the store of the post-collision state (float32 populations with the rest
-// population closing the mass balance, or 16-bit deviations).  Also
-// accumulates the centre-of-mass partials of the droplet phase and flags
-// non-finite densities.  Shared by the row kernels so that every variant
-// computes bit-identical states.
+// Collision of one node from its 38 pulled populations f and the density
+// ring (rzm, rz0, rzp: this node's column in the slots of planes z - 1, z,
+// z + 1; row r of a slot is r * RW further): momentum (Eq. 6), Shan-Chen
+// force (Eq. 7), common velocity with the force shift, BGK relaxation to the
+// equilibrium of Eq. 8 (Eqs. 9, 10) -- or, with MRT (float32 storage), the
+// moment relaxation of the generic kernel -- and the store of the
+// post-collision state (float32 populations with the rest population closing
+// the mass balance, or 16-bit deviations).  Also accumulates the
+// centre-of-mass partials of the droplet phase and flags non-finite
+// densities.  Shared by the row kernels so that every variant computes
+// bit-identical states.
 template <int TX, typename ST, bool MRT = false>
-__device__ __forceinline__ void collide_node(const float* ring, int s0, int s1, int s2, int x, int y, int z,
-                                             const float (&f)[2][19], const FastModel& m, const Layout& L,
-                                             ST* __restrict__ dst, int* __restrict__ d_err, float (&cm)[4], float px,
-                                             float py) {
+__device__ __forceinline__ void collide_node(const float2* rzm, const float2* rz0, const float2* rzp,
+                                             const float (&f)[2][19], const FastModel& m,
+                                             typename RowIO<TX, ST>::Out out, float (&cm)[4], int& bad, float px,
+                                             float py, float pz) {
+    using IO = RowIO<TX, ST>;
     constexpr int RW = TX + 2;
-    auto ridx = [&](int slot, int row, int col) { return ((slot * 3 + row + 1) * RW + col + 1) * 2; };
-    // neighbour density of component s at offset (dx, dy, dz)
-    auto nb = [&](int s, int dx, int dy, int dz) -> float {
-        const int slot = dz == 0 ? s1 : (dz > 0 ? s2 : s0);
-        return ring[ridx(slot, dy, x + dx) + s];
+    // neighbour densities {A, B} at offset (dx, dy, dz)
+    auto nb = [&](int dx, int dy, int dz) -> float2 {
+        const float2* r = dz == 0 ? rz0 : (dz > 0 ? rzp : rzm);
+        return r[(dy + 1) * RW + dx];
     };
-    const float rho[2] = {ring[ridx(s1, 0, x)], ring[ridx(s1, 0, x) + 1]};
+    const float2 rho2 = rz0[RW];
+    const float rho[2] = {rho2.x, rho2.y};
     // momentum (Eq. 6), opposite pairs differenced first
     float j[2][3];
 #pragma unroll
@@ -431,134 +597,185 @@ __device__ __forceinline__ void collide_node(const float* ring, int s0, int s1, 
         }
         j[s][0] = jx; j[s][1] = jy; j[s][2] = jz;
     }
-    // Shan-Chen force (Eq. 7) sums, neighbour pairs differenced first
+    // Shan-Chen force (Eq. 7) sums sum_i w_i rho_s(x + c_i) c_i, neighbour
+    // pairs differenced first; the weight folds into the multiplier
     float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
 #pragma unroll
     for (int i = 1; i < 19; i += 2) {
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const float d = wgt<float>(i) * (nb(s, cx_(i), cy_(i), cz_(i)) - nb(s, -cx_(i), -cy_(i), -cz_(i)));
-            if (cx_(i)) acc[s][0] += (float)cx_(i) * d;
-            if (cy_(i)) acc[s][1] += (float)cy_(i) * d;
-            if (cz_(i)) acc[s][2] += (float)cz_(i) * d;
-        }
+        const float2 np = nb(cx_(i), cy_(i), cz_(i)), nm = nb(-cx_(i), -cy_(i), -cz_(i));
+        const float dA = np.x - nm.x, dB = np.y - nm.y;
+        if (cx_(i)) { acc[0][0] += (wgt<float>(i) * cx_(i)) * dA; acc[1][0] += (wgt<float>(i) * cx_(i)) * dB; }
+        if (cy_(i)) { acc[0][1] += (wgt<float>(i) * cy_(i)) * dA; acc[1][1] += (wgt<float>(i) * cy_(i)) * dB; }
+        if (cz_(i)) { acc[0][2] += (wgt<float>(i) * cz_(i)) * dA; acc[1][2] += (wgt<float>(i) * cz_(i)) * dB; }
     }
     const float den = rho[0] * m.inv_tau[0] + rho[1] * m.inv_tau[1];
+    const float rden = __frcp_rn(den);
     float up[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) up[a] = (j[0][a] * m.inv_tau[0] + j[1][a] * m.inv_tau[1]) / den;
-    if (!(isfinite(rho[0]) && isfinite(rho[1]))) atomicOr(d_err, 1);
+    for (int a = 0; a < 3; ++a) up[a] = (j[0][a] * m.inv_tau[0] + j[1][a] * m.inv_tau[1]) * rden;
+    if (!(isfinite(rho[0]) && isfinite(rho[1]))) bad |= 1;
     {
-        const float phi = (rho[0] - rho[1]) / (rho[0] + rho[1]);
-        const float w = phi > 0.f ? phi : 0.f;
+        const float phi = __fdividef(rho[0] - rho[1], rho[0] + rho[1]);
+        const float w = fmaxf(phi, 0.f);
         cm[0] += w;
-        cm[1] += w * px;
-        cm[2] += w * py;
-        cm[3] += w * ((float)z - 0.5f * (float)(L.Lz - 1));
+        cm[1] = fmaf(w, px, cm[1]);
+        cm[2] = fmaf(w, py, cm[2]);
+        cm[3] = fmaf(w, pz, cm[3]);
     }
     if constexpr (is_dev_t<ST>::value) {
         // 16-bit deviations from w_i times the density of the node each
         // population streams to (this CTA's density planes), the pair of
         // components of one direction in one word
         using T = decltype(dev_tag(ST{}));
-        float ux[2], uy[2], uz[2], u2x[2];
+        float ux[2], uy[2], uz[2], base[2], e1[2], e2[2];
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            const float sh = -m.G * m.tau[s];  // tau_s F^s / rho_s per unit of the other sum
-            ux[s] = up[0] + sh * acc[1 - s][0];
-            uy[s] = up[1] + sh * acc[1 - s][1];
-            uz[s] = up[2] + sh * acc[1 - s][2];
-            u2x[s] = 1.5f * (ux[s] * ux[s] + uy[s] * uy[s] + uz[s] * uz[s]);
+            ux[s] = fmaf(m.sh[s], acc[1 - s][0], up[0]);
+            uy[s] = fmaf(m.sh[s], acc[1 - s][1], up[1]);
+            uz[s] = fmaf(m.sh[s], acc[1 - s][2], up[2]);
+            base[s] = 1.f - 1.5f * (ux[s] * ux[s] + uy[s] * uy[s] + uz[s] * uz[s]);
+            const float ir = m.inv_tau[s] * rho[s];
+            e1[s] = ir * wgt<float>(1);  // axis directions
+            e2[s] = ir * wgt<float>(7);  // edge directions
         }
-        unsigned* d = reinterpret_cast<unsigned*>(dst);
-        const long long db = L.dev_word(1, x, y, z);
         float others[2] = {0.f, 0.f};
-#pragma unroll
-        for (int i = 1; i < 19; i += 2) {
+        sfor<9>([&](auto K) {
+            constexpr int i = 2 * decltype(K)::value + 1;
+            // densities of the destinations x + c_i and x - c_i (read again
+            // from shared memory rather than held since the force)
+            const float2 np = nb(cx_(i), cy_(i), cz_(i)), nm = nb(-cx_(i), -cy_(i), -cz_(i));
             float da[2], dbv[2], refa[2], refb[2];
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 const float cu = (float)cx_(i) * ux[s] + (float)cy_(i) * uy[s] + (float)cz_(i) * uz[s];
-                const float rw = rho[s] * wgt<float>(i);
-                const float even = rw * (1.f + 4.5f * cu * cu - u2x[s]);
-                const float odd = rw * (3.f * cu);
-                const float fa = f[s][i], fb = f[s][i + 1];
-                const float oa = fa - (fa - (even + odd)) * m.inv_tau[s];
-                const float ob = fb - (fb - (even - odd)) * m.inv_tau[s];
-                refa[s] = wgt<float>(i) * nb(s, cx_(i), cy_(i), cz_(i));
-                refb[s] = wgt<float>(i) * nb(s, -cx_(i), -cy_(i), -cz_(i));
+                const float e = i < 7 ? e1[s] : e2[s];
+                const float ev = e * fmaf(4.5f * cu, cu, base[s]);
+                const float od = (3.f * e) * cu;
+                const float oa = fmaf(m.omit[s], f[s][i], ev + od);
+                const float ob = fmaf(m.omit[s], f[s][i + 1], ev - od);
+                refa[s] = wgt<float>(i) * (s ? np.y : np.x);
+                refb[s] = wgt<float>(i) * (s ? nm.y : nm.x);
                 da[s] = oa - refa[s];
                 dbv[s] = ob - refb[s];
             }
             const unsigned wa = dev_pack2<T>(da[0], da[1]), wb = dev_pack2<T>(dbv[0], dbv[1]);
-            __stcs(d + db + (long long)(i - 1) * L.array, wa);
-            __stcs(d + db + (long long)i * L.array, wb);
+            IO::template store_word<i>(out, wa);
+            IO::template store_word<i + 1>(out, wb);
             // the values the readers will rebuild, for the mass balance
             const float2 qa = dev_unpack2<T>(wa), qb = dev_unpack2<T>(wb);
             others[0] += (refa[0] + qa.x) + (refb[0] + qb.x);
             others[1] += (refa[1] + qa.y) + (refb[1] + qb.y);
-        }
-        __stcs(reinterpret_cast<float4*>(dst) + L.dev_node(x, y, z),
-               make_float4(rho[0], rho[1], rho[0] - others[0], rho[1] - others[1]));
+        });
+        st_cs_f4(out.b, make_float4(rho[0], rho[1], rho[0] - others[0], rho[1] - others[1]));
     } else {
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            const float sh = -m.G * m.tau[s];  // tau_s F^s / rho_s per unit of the other sum
-            const float ux = up[0] + sh * acc[1 - s][0];
-            const float uy = up[1] + sh * acc[1 - s][1];
-            const float uz = up[2] + sh * acc[1 - s][2];
-            const float u2x = 1.5f * (ux * ux + uy * uy + uz * uz);
-            const float it = m.inv_tau[s];
+            const float ux = fmaf(m.sh[s], acc[1 - s][0], up[0]);
+            const float uy = fmaf(m.sh[s], acc[1 - s][1], up[1]);
+            const float uz = fmaf(m.sh[s], acc[1 - s][2], up[2]);
             const float r = rho[s];
             // moving populations; the rest population then closes the mass
             // balance exactly (sum of outputs = rho), which keeps fp32
             // rounding from drifting the interface
-            const long long b = L.at(s, 0, x, y, z);
             float others = 0.f;
             if constexpr (MRT) {
                 // MRT: relax the moments of the deviation from equilibrium
                 // (d'Humieres basis; momentum and stress at 1/tau)
-                float dv[19], out[19];
+                const float u2x = 1.5f * (ux * ux + uy * uy + uz * uz);
+                float dv[19], o[19];
 #pragma unroll
                 for (int i = 0; i < 19; ++i) dv[i] = f[s][i] - feq<float>(i, r, ux, uy, uz, u2x);
-                mrt_relax<float>(f[s], dv, it, m.mrt, out);
-#pragma unroll
-                for (int i = 1; i < 19; i += 2) {
-                    __stcs(dst + b + (long long)i * L.array, out[i]);
-                    __stcs(dst + b + (long long)(i + 1) * L.array, out[i + 1]);
-                    others += out[i] + out[i + 1];
-                }
+                mrt_relax<float>(f[s], dv, m.inv_tau[s], m.mrt, o);
+                sfor<9>([&](auto K) {
+                    constexpr int i = 2 * decltype(K)::value + 1;
+                    if (s == 0) {
+                        IO::template store<0, i>(out, o[i]);
+                        IO::template store<0, i + 1>(out, o[i + 1]);
+                    } else {
+                        IO::template store<1, i>(out, o[i]);
+                        IO::template store<1, i + 1>(out, o[i + 1]);
+                    }
+                    others += o[i] + o[i + 1];
+                });
             } else {
-#pragma unroll
-                for (int i = 1; i < 19; i += 2) {
+                const float base = 1.f - 1.5f * (ux * ux + uy * uy + uz * uz);
+                const float ir = m.inv_tau[s] * r;
+                const float e1 = ir * wgt<float>(1), e2 = ir * wgt<float>(7);
+                const float om = m.omit[s];
+                sfor<9>([&](auto K) {
+                    constexpr int i = 2 * decltype(K)::value + 1;
                     const float cu = (float)cx_(i) * ux + (float)cy_(i) * uy + (float)cz_(i) * uz;
-                    const float rw = r * wgt<float>(i);
-                    const float even = rw * (1.f + 4.5f * cu * cu - u2x);
-                    const float odd = rw * (3.f * cu);
-                    const float fa = f[s][i], fb = f[s][i + 1];
-                    const float oa = fa - (fa - (even + odd)) * it;
-                    const float ob = fb - (fb - (even - odd)) * it;
-                    __stcs(dst + b + (long long)i * L.array, oa);
-                    __stcs(dst + b + (long long)(i + 1) * L.array, ob);
+                    const float e = i < 7 ? e1 : e2;
+                    const float ev = e * fmaf(4.5f * cu, cu, base);
+                    const float od = (3.f * e) * cu;
+                    const float oa = fmaf(om, f[s][i], ev + od);
+                    const float ob = fmaf(om, f[s][i + 1], ev - od);
+                    if (s == 0) {
+                        IO::template store<0, i>(out, oa);
+                        IO::template store<0, i + 1>(out, ob);
+                    } else {
+                        IO::template store<1, i>(out, oa);
+                        IO::template store<1, i + 1>(out, ob);
+                    }
                     others += oa + ob;
-                }
+                });
             }
-            __stcs(dst + b, r - others);
+            if (s == 0) IO::template store<0, 0>(out, r - others);
+            else IO::template store<1, 0>(out, r - others);
         }
     }
 }
 
+// Outer-halo share of a CTA of the direct and staged kernels: the rows just
+// outside the cluster (y0 - 1 below, y0 + CY above) are pulled by the two
+// CTAs nearest each edge, half a row each, and pushed into the edge CTA's
+// ring (row -1 of rank 0, row +1 of rank CY - 1).  Float32: thread x sums
+// component x & 1 of halo node x / 2 of the CTA's half; deviations (both
+// components in one word): threads x < TX / 2 sum a whole node each.
+template <int TX, int CY, typename ST>
+struct HaloShare {
+    bool cta;   // this CTA pulls outer-halo nodes
+    bool thr;   // this thread pushes one (float32: the even thread of a pair)
+    bool in;    // the halo row lies in the box
+    int col;    // the halo node's column
+    int comp;   // float32: the component this thread sums
+    int row;    // ring row of the edge CTA it lands in (-1 or +1)
+    int rank;   // the edge CTA
+    int y;      // the halo row
+    __device__ __forceinline__ HaloShare(int x, int r, int Y0, int Ly) {
+        static_assert(CY >= 4, "the two halo pairs of CTAs must not overlap");
+        const bool lo = r < 2, hi = r >= CY - 2;
+        cta = lo || hi;
+        const int half = lo ? r : r - (CY - 2);
+        y = lo ? Y0 - 1 : Y0 + CY;
+        in = y >= 0 && y < Ly;
+        row = lo ? -1 : 1;
+        rank = lo ? 0 : CY - 1;
+        if constexpr (is_dev_t<ST>::value) {
+            thr = cta && x < TX / 2;
+            col = half * (TX / 2) + x;
+            comp = 0;
+        } else {
+            thr = cta && (x & 1) == 0;
+            col = half * (TX / 2) + (x >> 1);
+            comp = x & 1;
+        }
+    }
+};
+
 template <int TX, int CY, int MINB, typename ST, bool STAGED, bool MRT = false>
 __global__ void __launch_bounds__(TX, MINB)
     k_stream_collide_rows(const ST* __restrict__ src, ST* __restrict__ dst, Layout L, FastModel m, int zchunk,
-                          CentreParts cp, int* __restrict__ d_err) {
-    using IO = RowIO<ST>;
+                          int alt, CentreParts cp, int* __restrict__ d_err) {
+    using IO = RowIO<TX, ST>;
     using FL = FastLayout<TX, CY>;
     using SP = StagePlane<TX, ST>;
     using SL = StagedLayout<TX, CY, ST>;
-    constexpr int RW = FL::RW, HN = FL::HN, S = FL::S, NST = SL::NST;
-    extern __shared__ __align__(128) float ring[];  // [S][3][RW][2], then S mbarriers (staged: see StagedLayout)
-    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(ring + FL::RING);
+    using HS = HaloShare<TX, CY, ST>;
+    constexpr int RW = FL::RW, S = FL::S, NST = SL::NST;
+    constexpr bool DEV = is_dev_t<ST>::value;
+    extern __shared__ __align__(128) float2 ring[];  // [S][3][RW], then S mbarriers (staged: see StagedLayout)
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(ring + S * FL::SLOT);
     __shared__ double red[4 * ((TX + 31) / 32)];
 
     cg::cluster_group cluster = cg::this_cluster();
@@ -568,18 +785,13 @@ __global__ void __launch_bounds__(TX, MINB)
     const int Y0 = y - rank;
     const int zc0 = blockIdx.z * zchunk;
     const int zc1 = min(zc0 + zchunk, L.Lz);
+    const int n = zc1 - zc0;
+    // k-th plane of the march (k = 0 and n + 1 are the halo planes)
+    const bool down = alt && (blockIdx.z & 1);
+    auto plane_of = [&](int k) { return down ? zc1 - k : zc0 - 1 + k; };
 
-    // Outer-halo node handled by this thread (threads x < HN): the first half
-    // of them cover row Y0 - 1 (kept in rank 0's ring row -1), the second half
-    // row Y0 + CY (kept in rank CY-1's ring row +1), TX/CY columns per CTA.
-    const bool hthr = x < HN;
-    const int hside = x < HN / 2 ? 0 : 1;
-    const int hcol = rank * (HN / 2) + (x % (HN / 2));
-    const int hy = hside ? Y0 + CY : Y0 - 1;
-    const bool hin = hy >= 0 && hy < L.Ly;
+    const HS hs(x, rank, Y0, L.Ly);
 
-    // ring index of (slot, row in -1..1, col in -1..TX), component 0
-    auto ridx = [&](int slot, int row, int col) { return ((slot * 3 + row + 1) * RW + col + 1) * 2; };
     const unsigned ring_s = smem_u32(ring);
     const unsigned mbar_s = smem_u32(mbar);
     // Where this CTA's own row goes in the neighbours' rings, and where its
@@ -588,8 +800,8 @@ __global__ void __launch_bounds__(TX, MINB)
     const unsigned below_mbar = rank > 0 ? cluster_addr(mbar_s, rank - 1) : 0u;
     const unsigned above_ring = rank < CY - 1 ? cluster_addr(ring_s, rank + 1) : 0u;  // their row -1
     const unsigned above_mbar = rank < CY - 1 ? cluster_addr(mbar_s, rank + 1) : 0u;
-    const unsigned halo_ring = cluster_addr(ring_s, hside ? CY - 1 : 0);
-    const unsigned halo_mbar = cluster_addr(mbar_s, hside ? CY - 1 : 0);
+    const unsigned halo_ring = cluster_addr(ring_s, hs.rank);
+    const unsigned halo_mbar = cluster_addr(mbar_s, hs.rank);
 
     // staged variant: plane images and their mbarriers (one arrival, by
     // thread 0, plus the bytes of the copies)
@@ -598,7 +810,7 @@ __global__ void __launch_bounds__(TX, MINB)
     const float* stage = reinterpret_cast<const float*>(reinterpret_cast<const char*>(ring) + SL::stage_off);
 
     // ghost density in every slot (x halo columns keep it for good), barriers
-    for (int e = x; e < FL::RING; e += TX) ring[e] = m.rho_b[e & 1];
+    for (int e = x; e < S * FL::SLOT; e += TX) ring[e] = make_float2(m.rho_b[0], m.rho_b[1]);
     if (x == 0) {
         for (int k = 0; k < S; ++k) mbar_init(mbar_s + 8u * k, 1u);
         if constexpr (STAGED)
@@ -607,121 +819,142 @@ __global__ void __launch_bounds__(TX, MINB)
     }
     cluster.sync();  // barriers initialised before any remote store arrives
 
-    const NodeIx node0 = IO::node(L, x, y);
-    const NodeIx hnode0 = IO::node(L, hcol, hin ? hy : 0);
+    const char* nbase = IO::base(src, x, y);
+    const char* hbase;
+    if constexpr (DEV) hbase = IO::base(src, hs.col, hs.in ? hs.y : 0);
+    else hbase = IO::base_c(src, hs.col, hs.in ? hs.y : 0, hs.comp);
+    auto planes = [&](const char* b, int p, int col) {
+        if constexpr (DEV) return IO::planes(b, L, p, col);
+        else return IO::planes(b, L, p);
+    };
     unsigned long long keep;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
 
-    auto slot_of = [&](int p) { return (p - (zc0 - 1)) % S; };
-
-    // Staged variant: plane p of this row lives in stage (p - zc0 + 1) mod NST.
-    // Thread 0 fills a stage (expect_tx, then the copies); every thread waits
-    // on the stage's mbarrier (bounded) before its first read of the plane.
-    // Only the planes this chunk reads and that lie in the box are copied.
-    auto stage_of = [&](int p) { return (p - zc0 + 1) % NST; };
-    auto plane_wanted = [&](int p) { return p >= 0 && p < L.Lz && p >= zc0 - 1 && p <= zc1; };
-    unsigned sphase = 0u;   // bit k: parity of stage k's next completion (every thread)
+    // Staged variant: march plane k lives in stage k mod NST.  Thread 0 fills
+    // a stage (expect_tx, then the copies); every thread waits on the stage's
+    // mbarrier (bounded) before its first read of the plane.  Only the planes
+    // this chunk reads and that lie in the box are copied.
+    auto plane_wanted = [&](int k) {
+        const int p = plane_of(k);
+        return k <= n + 1 && p >= 0 && p < L.Lz;
+    };
+    unsigned sphase = 0u;   // bit s: parity of stage s's next completion (every thread)
     unsigned pending = 0u;  // thread 0: stages with copies it has not seen complete
-    auto fill = [&](int p) {
-        if (!plane_wanted(p)) return;
-        const int k = stage_of(p);
-        mbar_expect_tx(smbar_s + 8u * k, SP::BYTES);
-        SP::issue(src, L, y, p, stage_s + (unsigned)(k * SP::BYTES), smbar_s + 8u * k);
-        pending |= 1u << k;
+    auto fill = [&](int k) {
+        if (!plane_wanted(k)) return;
+        const int st = k % NST;
+        mbar_expect_tx(smbar_s + 8u * st, SP::BYTES);
+        SP::issue(src, L, y, plane_of(k), stage_s + (unsigned)(st * SP::BYTES), smbar_s + 8u * st);
+        pending |= 1u << st;
     };
-    auto stage_wait = [&](int p) {
-        const int k = stage_of(p);
-        const unsigned par = (sphase >> k) & 1u;
-        if (wait_bounded(smbar_s + 8u * k, par, false, kWaitNs)) pending &= ~(1u << k);
+    auto stage_wait = [&](int k) {
+        const int st = k % NST;
+        const unsigned par = (sphase >> st) & 1u;
+        if (wait_bounded(smbar_s + 8u * st, par, false, kWaitNs)) pending &= ~(1u << st);
         else atomicOr(d_err, 4);
-        sphase ^= 1u << k;
+        sphase ^= 1u << st;
     };
-    auto stage_ptr = [&](int p) { return stage + (size_t)stage_of(p) * (SP::BYTES / 4); };
+    auto stage_ptr = [&](int k) { return stage + (size_t)(k % NST) * (SP::BYTES / 4); };
     if constexpr (STAGED) {
         if (x == 0)
-            for (int q = -1; q <= 1; ++q) fill(zc0 + q);
+            for (int k = 0; k < 3; ++k) fill(k);
     }
 
-    // Post-streaming densities of plane p: the own node into row 0 of this
-    // CTA's ring and into the neighbours' rows -1 / +1; the outer-halo node
-    // (threads x < HN) into the edge CTA's row -1 / +1.  Ghost densities
-    // outside the box.  Every CTA then expects TX_BYTES on its slot barrier.
-    auto densities = [&](int p) {
-        const int slot = slot_of(p);
+    // Post-streaming densities of march plane k: the own node into row 0 of
+    // this CTA's ring and into the neighbours' rows -1 / +1; the outer-halo
+    // share into the edge CTA's ring.  Ghost densities outside the box.
+    // Every CTA then expects TX_BYTES on its slot barrier.
+    auto densities = [&](int k) {
+        const int p = plane_of(k);
+        const int sl = k & (S - 1);
         const bool in = p >= 0 && p < L.Lz;
         float ra = m.rho_b[0], rb = m.rho_b[1];
         if (in) {
             if constexpr (STAGED) {
-                stage_wait(p);
-                SP::densities(stage_ptr(p), x, ra, rb);
+                stage_wait(k);
+                SP::densities(stage_ptr(k), x, ra, rb);
             } else {
-                IO::densities(src, L, node0, p, keep, ra, rb);
+                IO::densities(planes(nbase, p, x), keep, ra, rb);
             }
         }
-        *reinterpret_cast<float2*>(ring + ridx(slot, 0, x)) = make_float2(ra, rb);
-        const unsigned mb = 8u * slot;
-        if (rank > 0) st_async_f2(below_ring + 4u * ridx(slot, 1, x), ra, rb, below_mbar + mb);
-        if (rank < CY - 1) st_async_f2(above_ring + 4u * ridx(slot, -1, x), ra, rb, above_mbar + mb);
-        if (hthr) {
-            float ha = m.rho_b[0], hb = m.rho_b[1];
-            if (in && hin) IO::densities(src, L, hnode0, p, keep, ha, hb);
-            st_async_f2(halo_ring + 4u * ridx(slot, hside ? 1 : -1, hcol), ha, hb, halo_mbar + mb);
+        ring[sl * FL::SLOT + RW + x + 1] = make_float2(ra, rb);
+        const unsigned col = 8u * (unsigned)(sl * FL::SLOT + x + 1);  // row -1 of the slot, this column
+        const unsigned mb = 8u * sl;
+        if (rank > 0) st_async_f2(below_ring + col + 16u * RW, ra, rb, below_mbar + mb);
+        if (rank < CY - 1) st_async_f2(above_ring + col, ra, rb, above_mbar + mb);
+        if (hs.cta) {
+            const unsigned hoff = 8u * (unsigned)(sl * FL::SLOT + (hs.row + 1) * RW + hs.col + 1);
+            if constexpr (DEV) {
+                if (hs.thr) {
+                    float ha = m.rho_b[0], hb = m.rho_b[1];
+                    if (in && hs.in) IO::densities(planes(hbase, p, hs.col), keep, ha, hb);
+                    st_async_f2(halo_ring + hoff, ha, hb, halo_mbar + mb);
+                }
+            } else {
+                float v = m.rho_b[hs.comp];
+                if (in && hs.in) v = IO::template density<0>(planes(hbase, p, 0), keep);
+                const float other = __shfl_xor_sync(0xffffffffu, v, 1);
+                if (hs.thr) st_async_f2(halo_ring + hoff, v, other, halo_mbar + mb);
+            }
         }
         if (x == 0) mbar_expect_tx(mbar_s + mb, FL::TX_BYTES);
     };
-    // Wait (bounded) until the neighbour rows of plane p have landed.
-    unsigned phase = 0u;  // bit k: parity of slot k's next phase
-    auto wait_rows = [&](int p) {
-        const int slot = slot_of(p);
-        const unsigned par = (phase >> slot) & 1u;
-        if (!wait_bounded(mbar_s + 8u * slot, par, true, kWaitNs)) atomicOr(d_err, 4);
-        phase ^= 1u << slot;
+    // Wait (bounded) until the neighbour rows of march plane k have landed.
+    auto wait_rows = [&](int k) {
+        const unsigned par = (unsigned)(k / S) & 1u;
+        if (!wait_bounded(mbar_s + 8u * (k & (S - 1)), par, true, kWaitNs)) atomicOr(d_err, 4);
     };
 
     float cm[4] = {0.f, 0.f, 0.f, 0.f};
+    int bad = 0;
     const float px = (float)x - 0.5f * (float)(L.Lx - 1), py = (float)y - 0.5f * (float)(L.Ly - 1);
 
-    densities(zc0 - 1);
-    densities(zc0);
-    wait_rows(zc0 - 1);
-    wait_rows(zc0);
+    densities(0);
+    densities(1);
+    wait_rows(0);
+    wait_rows(1);
     if constexpr (STAGED) {
-        __syncthreads();  // plane zc0 - 1 read by all: its stage takes plane zc0 + 2
+        __syncthreads();  // march plane 0 read by all: its stage takes plane 3
         if (x == 0) {
             fence_proxy_async();
-            fill(zc0 + 2);
+            fill(3);
         }
     }
-    for (int z = zc0; z < zc1; ++z) {
-        densities(z + 1);
+    for (int k = 1; k <= n; ++k) {
+        densities(k + 1);
+        const int z = plane_of(k);
         // this node's populations for the collision, read while the
-        // neighbour rows of plane z + 1 are in flight
+        // neighbour rows of plane k + 1 are in flight
         float f[2][19];
-        if constexpr (STAGED) SP::populations(stage_ptr(z), x, f);
-        else IO::populations(src, L, node0, z, f);
-        __syncthreads();  // own row of plane z + 1 complete
+        if constexpr (STAGED) SP::populations(stage_ptr(k), x, f);
+        else IO::populations(planes(nbase, z, x), f);
+        __syncthreads();  // own row of plane k + 1 complete
         if constexpr (STAGED) {
-            // plane z has been read by every thread: its stage takes plane z + 3
+            // plane k has been read by every thread: its stage takes plane k + 3
             if (x == 0) {
                 fence_proxy_async();
-                fill(z + 3);
+                fill(k + 3);
             }
         }
-        wait_rows(z + 1);
+        wait_rows(k + 1);
 
-        collide_node<TX, ST, MRT>(ring, slot_of(z - 1), slot_of(z), slot_of(z + 1), x, y, z, f, m, L, dst, d_err, cm,
-                                  px, py);
+        const float2* rprev = ring + ((k - 1) & (S - 1)) * FL::SLOT + x + 1;
+        const float2* rcur = ring + (k & (S - 1)) * FL::SLOT + x + 1;
+        const float2* rnext = ring + ((k + 1) & (S - 1)) * FL::SLOT + x + 1;
+        collide_node<TX, ST, MRT>(down ? rnext : rprev, rcur, down ? rprev : rnext, f, m, IO::out(dst, L, x, y, z),
+                                  cm, bad, px, py, (float)z - 0.5f * (float)(L.Lz - 1));
         // Before a later plane reuses this plane's own-row slot, all threads
         // must be done reading it: the __syncthreads of the next iterations
-        // (S > 3 planes apart) order that.
+        // (S - 1 march planes apart) order that.
     }
+    if (bad) atomicOr(d_err, bad);
     // staged variant: copies whose completion thread 0 did not observe (a
     // wait that gave up) are waited for again, bounded, before the CTA exits
     if constexpr (STAGED) {
         if (x == 0) {
-            for (int k = 0; k < NST; ++k) {
-                if (!((pending >> k) & 1u)) continue;
-                wait_bounded(smbar_s + 8u * k, ((sphase >> k) & 1u) ^ 1u, false, kWaitNs);
+            for (int st = 0; st < NST; ++st) {
+                if (!((pending >> st) & 1u)) continue;
+                wait_bounded(smbar_s + 8u * st, ((sphase >> st) & 1u) ^ 1u, false, kWaitNs);
             }
         }
     }
@@ -736,24 +969,24 @@ __global__ void __launch_bounds__(TX, MINB)
 // ---- Warp-specialised variant: loader and collider threads per row ----
 //
 // A CTA of 2 TX threads owns one row: threads 0 .. TX-1 (loaders) and
-// TX .. 2 TX-1 (colliders) each take node x = t mod TX.  Per plane p a loader
-// reads the node's 38 pulled populations once, sums its densities into the
-// ring (own row, the neighbour CTAs' rows by st.async, the outer-halo node as
-// in the direct variant) and stages the populations in shared memory (NP
-// planes in flight); the colliders collide plane z from shared memory once
-// the densities of plane z + 1 have landed.  Loads of later planes are in
-// flight while earlier planes are collided, on other warps, and no
-// population is read twice.
+// TX .. 2 TX-1 (colliders) each take node x = t mod TX.  Per march plane k a
+// loader reads the node's 38 pulled populations once, sums its densities into
+// the ring (own row, the neighbour CTAs' rows by st.async, and its share of
+// the rows outside the cluster, which every CTA of the cluster helps pull)
+// and stages the populations in shared memory (NP planes in flight); the
+// colliders collide plane k from shared memory once the densities of plane
+// k + 1 have landed.  Loads of later planes are in flight while earlier
+// planes are collided, on other warps, and no population is read twice.
 //
-// Barriers (all waits bounded): ring slot k completes when this CTA's TX
+// Barriers (all waits bounded): ring slot s completes when this CTA's TX
 // loaders have written their own row of the slot's plane and the 2 TX x 8
 // bytes of the rows -1 / +1 have landed; full[b] when the loaders have staged
 // a plane in buffer b; empty[b] when the colliders are done with it.
 //
-// Ring slots: a loader pushes plane p's densities only after it has staged
-// plane p - 1, which waited for its colliders to be done with plane
-// p - 1 - NP = p - 3; those colliders finished plane p - 3 only after the CTAs
-// next to them had pushed plane p - 2.  So a loader is at most two planes
+// Ring slots: a loader pushes plane k's densities only after it has staged
+// plane k - 1, which waited for its colliders to be done with plane
+// k - 1 - NP = k - 3; those colliders finished plane k - 3 only after the CTAs
+// next to them had pushed plane k - 2.  So a loader is at most two planes
 // ahead of the loaders of the CTAs next to it in the cluster and at most
 // 2 (CY - 1) planes ahead of any CTA of the cluster (the outer-halo rows go
 // from every CTA to the edge CTAs), whose colliders may still be reading
@@ -764,11 +997,11 @@ struct WsLayout {
     static constexpr int HN = 2 * TX / CY;
     static constexpr int S = 2 * CY + 2;
     static constexpr int NP = 2;
-    static constexpr int RING = S * 3 * RW * 2;  // [slot][row -1..1][col][component] floats
-    static constexpr int POPS = NP * 38 * TX;    // [buffer][s * 19 + i][x] floats
-    static constexpr unsigned TX_BYTES = 2u * TX * 2u * 4u;
+    static constexpr int SLOT = 3 * RW;           // float2 per slot
+    static constexpr int POPS = NP * 38 * TX;     // [buffer][s * 19 + i][x] floats
+    static constexpr unsigned TX_BYTES = 2u * TX * 8u;
     static constexpr int NBAR = S + 2 * NP;
-    static constexpr size_t bytes = sizeof(float) * (RING + POPS) + sizeof(unsigned long long) * NBAR;
+    static constexpr size_t bytes = sizeof(float2) * S * SLOT + sizeof(float) * POPS + sizeof(unsigned long long) * NBAR;
 };
 
 __device__ __forceinline__ bool ws_wait(unsigned mbar, unsigned parity, bool cluster_scope) {
@@ -777,13 +1010,14 @@ __device__ __forceinline__ bool ws_wait(unsigned mbar, unsigned parity, bool clu
 
 template <int TX, int CY, int MINB, typename ST>
 __global__ void __launch_bounds__(2 * TX, MINB)
-    k_stream_collide_ws(const ST* __restrict__ src, ST* __restrict__ dst, Layout L, FastModel m, int zchunk,
+    k_stream_collide_ws(const ST* __restrict__ src, ST* __restrict__ dst, Layout L, FastModel m, int zchunk, int alt,
                         CentreParts cp, int* __restrict__ d_err) {
-    using IO = RowIO<ST>;
+    using IO = RowIO<TX, ST>;
     using WL = WsLayout<TX, CY>;
     constexpr int RW = WL::RW, HN = WL::HN, S = WL::S, NP = WL::NP;
-    extern __shared__ __align__(128) float ring[];  // [S][3][RW][2], then [NP][38][TX], then NBAR mbarriers
-    float* pops = ring + WL::RING;
+    constexpr bool DEV = is_dev_t<ST>::value;
+    extern __shared__ __align__(128) float2 ring[];  // [S][3][RW], then [NP][38][TX] floats, then NBAR mbarriers
+    float* pops = reinterpret_cast<float*>(ring + S * WL::SLOT);
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(pops + WL::POPS);
     __shared__ double red[4 * ((2 * TX + 31) / 32)];
 
@@ -796,15 +1030,19 @@ __global__ void __launch_bounds__(2 * TX, MINB)
     const int Y0 = y - rank;
     const int zc0 = blockIdx.z * zchunk;
     const int zc1 = min(zc0 + zchunk, L.Lz);
+    const int n = zc1 - zc0;
+    const bool down = alt && (blockIdx.z & 1);
+    auto plane_of = [&](int k) { return down ? zc1 - k : zc0 - 1 + k; };
 
-    // outer-halo node of loader threads x < HN (as in the direct variant)
+    // outer-halo node of loader threads x < HN: the first half of them cover
+    // row Y0 - 1 (kept in rank 0's ring row -1), the second half row Y0 + CY
+    // (kept in rank CY - 1's ring row +1), TX / CY columns per CTA
     const bool hthr = loader && x < HN;
     const int hside = x < HN / 2 ? 0 : 1;
     const int hcol = rank * (HN / 2) + (x % (HN / 2));
     const int hy = hside ? Y0 + CY : Y0 - 1;
     const bool hin = hy >= 0 && hy < L.Ly;
 
-    auto ridx = [&](int slot, int row, int col) { return ((slot * 3 + row + 1) * RW + col + 1) * 2; };
     const unsigned ring_s = smem_u32(ring);
     const unsigned rbar_s = smem_u32(bars);        // S ring-slot barriers
     const unsigned full_s = rbar_s + 8u * S;       // NP: a plane staged
@@ -816,7 +1054,7 @@ __global__ void __launch_bounds__(2 * TX, MINB)
     const unsigned halo_ring = cluster_addr(ring_s, hside ? CY - 1 : 0);
     const unsigned halo_mbar = cluster_addr(rbar_s, hside ? CY - 1 : 0);
 
-    for (int e = t; e < WL::RING; e += 2 * TX) ring[e] = m.rho_b[e & 1];  // ghost density, x halo columns for good
+    for (int e = t; e < S * WL::SLOT; e += 2 * TX) ring[e] = make_float2(m.rho_b[0], m.rho_b[1]);
     if (t == 0) {
         for (int k = 0; k < S; ++k) mbar_init(rbar_s + 8u * k, (unsigned)TX);
         for (int b = 0; b < NP; ++b) {
@@ -827,37 +1065,45 @@ __global__ void __launch_bounds__(2 * TX, MINB)
     }
     cluster.sync();  // barriers initialised before any remote store arrives
 
-    auto slot_of = [&](int p) { return (p - (zc0 - 1)) % S; };
+    auto planes = [&](const char* b, int p, int col) {
+        if constexpr (DEV) return IO::planes(b, L, p, col);
+        else return IO::planes(b, L, p);
+    };
     float cm[4] = {0.f, 0.f, 0.f, 0.f};
+    int bad = 0;
 
     if (loader) {
-        const NodeIx node0 = IO::node(L, x, y);
-        const NodeIx hnode0 = IO::node(L, hcol, hin ? hy : 0);
+        const char* nbase = IO::base(src, x, y);
+        const char* hbase = IO::base(src, hcol, hin ? hy : 0);
         unsigned long long keep;
         asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
         unsigned ephase = 0u;  // bit b: parity of empty[b]'s next phase
-        for (int p = zc0 - 1; p <= zc1; ++p) {
+        for (int k = 0; k <= n + 1; ++k) {
+            const int p = plane_of(k);
             const bool in = p >= 0 && p < L.Lz;
-            const bool staged = p >= zc0 && p < zc1;  // a plane this CTA collides
+            const bool staged = k >= 1 && k <= n;  // a plane this CTA collides
             float f[2][19];
             float ra = m.rho_b[0], rb = m.rho_b[1];
-            if (in) IO::load_all(src, L, node0, p, f, ra, rb);
+            if (in) IO::load_all(planes(nbase, p, x), f, ra, rb);
             float ha = m.rho_b[0], hb = m.rho_b[1];
-            if (hthr && in && hin) IO::densities(src, L, hnode0, p, keep, ha, hb);  // read again by its own CTA
-            // densities first: the colliders of plane p - 1 wait for them
-            const int slot = slot_of(p);
+            if (hthr && in && hin) IO::densities(planes(hbase, p, hcol), keep, ha, hb);  // read again by its own CTA
+            // densities first: the colliders of plane k - 1 wait for them
+            const int slot = k % S;
             const unsigned mb = 8u * slot;
-            *reinterpret_cast<float2*>(ring + ridx(slot, 0, x)) = make_float2(ra, rb);
-            if (rank > 0) st_async_f2(below_ring + 4u * ridx(slot, 1, x), ra, rb, below_mbar + mb);
-            if (rank < CY - 1) st_async_f2(above_ring + 4u * ridx(slot, -1, x), ra, rb, above_mbar + mb);
-            if (hthr) st_async_f2(halo_ring + 4u * ridx(slot, hside ? 1 : -1, hcol), ha, hb, halo_mbar + mb);
+            const unsigned col = 8u * (unsigned)(slot * WL::SLOT + x + 1);
+            ring[slot * WL::SLOT + RW + x + 1] = make_float2(ra, rb);
+            if (rank > 0) st_async_f2(below_ring + col + 16u * RW, ra, rb, below_mbar + mb);
+            if (rank < CY - 1) st_async_f2(above_ring + col, ra, rb, above_mbar + mb);
+            if (hthr)
+                st_async_f2(halo_ring + 8u * (unsigned)(slot * WL::SLOT + (hside ? 2 : 0) * RW + hcol + 1), ha, hb,
+                            halo_mbar + mb);
             if (x == 0) mbar_expect_tx(rbar_s + mb, WL::TX_BYTES);  // this thread's arrival, and the bytes
             else mbar_arrive(rbar_s + mb);
             // then the populations, into a buffer the colliders are done with
-            // (plane p - NP); they wait in registers meanwhile
+            // (plane k - NP); they wait in registers meanwhile
             if (staged) {
-                const int b = (p - zc0) % NP;
-                if (p - zc0 >= NP) {
+                const int b = (k - 1) % NP;
+                if (k - 1 >= NP) {
                     if (!ws_wait(empty_s + 8u * b, (ephase >> b) & 1u, false)) atomicOr(d_err, 4);
                     ephase ^= 1u << b;
                 }
@@ -871,17 +1117,17 @@ __global__ void __launch_bounds__(2 * TX, MINB)
         }
     } else {
         const float px = (float)x - 0.5f * (float)(L.Lx - 1), py = (float)y - 0.5f * (float)(L.Ly - 1);
-        unsigned rphase = 0u, fphase = 0u;  // bit k: parity of ring slot k's / full[k]'s next phase
-        auto wait_ring = [&](int p) {
-            const int slot = slot_of(p);
+        unsigned rphase = 0u, fphase = 0u;  // bit s: parity of ring slot s's / full[s]'s next phase
+        auto wait_ring = [&](int k) {
+            const int slot = k % S;
             if (!ws_wait(rbar_s + 8u * slot, (rphase >> slot) & 1u, true)) atomicOr(d_err, 4);
             rphase ^= 1u << slot;
         };
-        wait_ring(zc0 - 1);
-        wait_ring(zc0);
-        for (int z = zc0; z < zc1; ++z) {
-            wait_ring(z + 1);
-            const int b = (z - zc0) % NP;
+        wait_ring(0);
+        wait_ring(1);
+        for (int k = 1; k <= n; ++k) {
+            wait_ring(k + 1);
+            const int b = (k - 1) % NP;
             if (!ws_wait(full_s + 8u * b, (fphase >> b) & 1u, false)) atomicOr(d_err, 4);
             fphase ^= 1u << b;
             float f[2][19];
@@ -890,13 +1136,18 @@ __global__ void __launch_bounds__(2 * TX, MINB)
             for (int s = 0; s < 2; ++s)
 #pragma unroll
                 for (int i = 0; i < 19; ++i) f[s][i] = P[(s * 19 + i) * TX + x];
-            collide_node<TX, ST>(ring, slot_of(z - 1), slot_of(z), slot_of(z + 1), x, y, z, f, m, L, dst, d_err, cm,
-                                 px, py);
-            // the buffer may take plane z + NP (released after the collision,
+            const int z = plane_of(k);
+            const float2* rprev = ring + ((k - 1) % S) * WL::SLOT + x + 1;
+            const float2* rcur = ring + (k % S) * WL::SLOT + x + 1;
+            const float2* rnext = ring + ((k + 1) % S) * WL::SLOT + x + 1;
+            collide_node<TX, ST>(down ? rnext : rprev, rcur, down ? rprev : rnext, f, m, IO::out(dst, L, x, y, z), cm,
+                                 bad, px, py, (float)z - 0.5f * (float)(L.Lz - 1));
+            // the buffer may take plane k + NP (released after the collision,
             // so that the populations can stay in shared memory until used)
             mbar_arrive(empty_s + 8u * b);
         }
     }
+    if (bad) atomicOr(d_err, bad);
     // no CTA leaves while another may still address its shared memory
     cluster.sync();
 
@@ -905,19 +1156,14 @@ __global__ void __launch_bounds__(2 * TX, MINB)
     centre_epilogue(cmd, cp, red);
 }
 
-constexpr int kRowMinBlocks = 6;
-
-// Resident CTAs per SM asked of the compiler (it sets the register budget).
-// Direct-load variant: 6 x 128 threads' worth (80 registers), except at
-// Lx = 128, where 4 CTAs (128 registers) step 1.7 % (fp32) and 2.8 % (fp16
-// deviations) faster at 128^3 -- the 512-CTA grid fills only 3.4 per SM, so
-// the bound costs no occupancy; at Lx = 256, 3 CTAs (80 registers) beat 2
-// (128 registers) by 2 % (fp32) and 13 % (fp16 deviations), measured on
-// GB300.  The staged variant is bounded by its shared memory (about 2 x
-// 128-thread CTAs per SM).
+// Resident CTAs per SM asked of the compiler (it sets the register budget)
+// for the direct-load variant, per row width; the staged variant is bounded
+// by its shared memory (about 2 x 128-thread CTAs per SM).
 template <int TX, bool STAGED>
 constexpr int row_min_blocks() {
-    return STAGED ? (256 / TX > 0 ? 256 / TX : 1) : (TX == 128 ? 4 : kRowMinBlocks * 128 / TX);
+    if (STAGED) return 256 / TX > 0 ? 256 / TX : 1;
+    return TX == 32 ? LBM_ROWS_MINB_32
+                    : (TX == 64 ? LBM_ROWS_MINB_64 : (TX == 128 ? LBM_ROWS_MINB_128 : LBM_ROWS_MINB_256));
 }
 
 template <int TX, int CY, typename S, bool STAGED>
@@ -932,14 +1178,7 @@ cudaError_t launch_rows(const void* src, void* dst, const Layout& L, const Model
     const size_t smem = row_smem<TX, CY, S, STAGED>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    FastModel fm;
-    for (int q = 0; q < 2; ++q) {
-        fm.inv_tau[q] = (float)(1.0 / m.tau[q]);
-        fm.tau[q] = (float)m.tau[q];
-        fm.rho_b[q] = (float)m.rho_b[q];
-    }
-    fm.G = (float)m.G;
-    for (int k = 0; k < 5; ++k) fm.mrt[k] = (float)m.mrt_rates[k];
+    const FastModel fm = fast_model(m);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(1, L.Ly, nchunks);
     cfg.blockDim = dim3(TX, 1, 1);
@@ -952,7 +1191,7 @@ cudaError_t launch_rows(const void* src, void* dst, const Layout& L, const Model
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, (const S*)src, (S*)dst, L, fm, zchunk, cp, d_err);
+    return cudaLaunchKernelEx(&cfg, k, (const S*)src, (S*)dst, L, fm, zchunk, (int)LBM_ROWS_ALTERNATE, cp, d_err);
 }
 
 template <int TX, int CY, typename S, bool STAGED, bool MRT>
@@ -1037,16 +1276,10 @@ cudaError_t ws_for(bool query, const void* src, void* dst, const Layout& L, cons
         *resident = n * CY;
         return cudaSuccess;
     }
-    FastModel fm;
-    for (int q = 0; q < 2; ++q) {
-        fm.inv_tau[q] = (float)(1.0 / m.tau[q]);
-        fm.tau[q] = (float)m.tau[q];
-        fm.rho_b[q] = (float)m.rho_b[q];
-    }
-    fm.G = (float)m.G;
+    const FastModel fm = fast_model(m);
     cfg.gridDim = dim3(1, L.Ly, (L.Lz + zchunk - 1) / zchunk);
     cfg.stream = s;
-    return cudaLaunchKernelEx(&cfg, k, (const S*)src, (S*)dst, L, fm, zchunk, cp, d_err);
+    return cudaLaunchKernelEx(&cfg, k, (const S*)src, (S*)dst, L, fm, zchunk, (int)LBM_ROWS_ALTERNATE, cp, d_err);
 }
 
 template <int TX, typename S>
@@ -1062,18 +1295,26 @@ cudaError_t rows_variant(int variant, bool query, const void* src, void* dst, co
     return rows_for<TX, S, false>(query, src, dst, L, m, zchunk, cp, d_err, s, resident);
 }
 
+// The kernels address the layout with the compile-time geometry of RowGeo;
+// the layout of the context must be the one make_layout gives for Lx.
+template <int TX, typename S>
+bool geometry_matches(const Layout& L) {
+    using G = RowGeo<TX, S>;
+    return L.x0 == G::X0 && L.pitch == G::PITCH && L.row == (long long)G::ROW;
+}
+
 // Dispatch on the row width, the storage type and the variant.
 cudaError_t rows_dispatch(int prec, int variant, bool query, const void* src, void* dst, const Layout& L,
                           const Model& m, int zchunk, CentreParts cp, int* d_err, cudaStream_t s, int* resident) {
-#define LBM_ROWS_TX(TXV)                                                                                        \
-    if (L.Lx == TXV) {                                                                                          \
-        if (prec == kFP32)                                                                                      \
-            return rows_variant<TXV, float>(variant, query, src, dst, L, m, zchunk, cp, d_err, s, resident);     \
-        if (prec == kFP16Dev)                                                                                   \
+#define LBM_ROWS_TX(TXV)                                                                                         \
+    if (L.Lx == TXV) {                                                                                           \
+        if (prec == kFP32 && geometry_matches<TXV, float>(L))                                                    \
+            return rows_variant<TXV, float>(variant, query, src, dst, L, m, zchunk, cp, d_err, s, resident);      \
+        if (prec == kFP16Dev && geometry_matches<TXV, Dev<__half>>(L))                                           \
             return rows_variant<TXV, Dev<__half>>(variant, query, src, dst, L, m, zchunk, cp, d_err, s, resident); \
-        if (prec == kBF16Dev)                                                                                   \
-            return rows_variant<TXV, Dev<__nv_bfloat16>>(variant, query, src, dst, L, m, zchunk, cp, d_err, s,   \
-                                                         resident);                                             \
+        if (prec == kBF16Dev && geometry_matches<TXV, Dev<__nv_bfloat16>>(L))                                    \
+            return rows_variant<TXV, Dev<__nv_bfloat16>>(variant, query, src, dst, L, m, zchunk, cp, d_err, s,    \
+                                                         resident);                                              \
     }
     LBM_ROWS_TX(32)
     LBM_ROWS_TX(64)

@@ -9,43 +9,47 @@
 
 namespace lbmgb {
 
-// Padded, plane-major structure-of-arrays population layout in device memory.
+// Padded, row-interleaved structure-of-arrays population layout in device
+// memory:
 //
-//   element (s, i, z, y, x) at  (z + 1) * plane + (s*19 + i) * array + (y + 1) * pitch + x0 + x
+//   element (s, i, z, y, x) at  (z + 1) * plane + (y + 1) * row + (s*19 + i) * pitch + x0 + x
 //
-// for fluid nodes x in [0, Lx), y in [0, Ly), z in [0, Lz), with
-// array = ny * pitch (one population's x-y plane) and plane = 38 * array.
-// All 38 populations of one z plane are contiguous, so a CTA marching along
-// z touches a few memory pages at a time rather than 38 arrays far apart.
-// One ghost layer surrounds the box: x = -1 .. Lx, y = -1 .. Ly, z = -1 .. Lz
-// all have storage.  x0 puts the first fluid node of every row on a 32-byte
-// boundary, and pitch (a multiple of 32 bytes) keeps every row on that
-// boundary.
+// for fluid nodes x in [0, Lx), y in [0, Ly), z in [0, Lz), with row = 38 *
+// pitch (all populations of one row of nodes) and plane = ny * row.  Within a
+// row block the 38 populations are rows of `pitch` elements, so the offset
+// between any two populations of one node, and between the populations a
+// node pulls from its neighbours (x - c_i), is a constant fixed by Lx alone
+// except for the z plane: the row kernels address every access as one of
+// three per-plane pointers plus a compile-time immediate.  One ghost layer
+// surrounds the box: x = -1 .. Lx, y = -1 .. Ly, z = -1 .. Lz all have
+// storage.  x0 puts the first fluid node of every row on a 32-byte boundary,
+// and pitch (a multiple of 32 bytes) keeps every row on that boundary.
 //
-// 16-bit deviation storage uses the same geometry in 2-byte units with
-// plane = 44 * array: per z plane first a float4 block of `array` nodes
-// {rho*_A, rho*_B, f*_0A, f*_0B} (8 units per node), then for each direction
-// i = 1..18 an array of 32-bit words, one per node, holding the deviations
-// of both components {A, B} (see dev_node / dev_word / dev_at).
+// 16-bit deviation storage uses the same geometry in 2-byte units with row =
+// 44 * pitch: per row block first a row of `pitch` float4 blocks
+// {rho*_A, rho*_B, f*_0A, f*_0B} (8 units per entry), then for each direction
+// i = 1..18 a row of `pitch` 32-bit words, one per node, holding the
+// deviations of both components {A, B} (see dev_node / dev_word / dev_at).
 struct Layout {
     int Lx, Ly, Lz;
     int x0;           // elements before x = 0 in a row
-    int pitch;        // elements per row
+    int pitch;        // elements per population row
     int ny, nz;       // Ly + 2, Lz + 2
-    long long plane;  // elements per z plane (all 38 populations)
-    long long array;  // elements of one population's x-y plane
+    long long row;    // elements per row block (all populations of one row of nodes)
+    long long plane;  // elements per z plane (ny row blocks)
     long long total;  // nz * plane
     __host__ __device__ long long at(int s, int i, int x, int y, int z) const {
-        return (long long)(z + 1) * plane + (long long)(s * 19 + i) * array + (long long)(y + 1) * pitch + x0 + x;
+        return (long long)(z + 1) * plane + (long long)(y + 1) * row + (long long)(s * 19 + i) * pitch + x0 + x;
     }
     // 16-bit deviation storage: float4 index of node (x, y, z)'s block
     __host__ __device__ long long dev_node(int x, int y, int z) const {
-        return (long long)(z + 1) * (plane >> 3) + (long long)(y + 1) * pitch + x0 + x;
+        return (long long)(z + 1) * (plane >> 3) + (long long)(y + 1) * (row >> 3) + x0 + x;
     }
     // 16-bit deviation storage: 32-bit word index of the deviation pair
     // {A, B} of direction i >= 1 of node (x, y, z)
     __host__ __device__ long long dev_word(int i, int x, int y, int z) const {
-        return (long long)(z + 1) * (plane >> 1) + (long long)(3 + i) * array + (long long)(y + 1) * pitch + x0 + x;
+        return (long long)(z + 1) * (plane >> 1) + (long long)(y + 1) * (row >> 1) + (long long)(3 + i) * pitch + x0 +
+               x;
     }
     // 16-bit deviation storage: 2-byte index of deviation (s, i >= 1) of node (x, y, z)
     __host__ __device__ long long dev_at(int s, int i, int x, int y, int z) const {

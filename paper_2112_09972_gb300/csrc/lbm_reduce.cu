@@ -101,8 +101,8 @@ __device__ __forceinline__ void node_rho(const S* __restrict__ f, const Layout& 
         rb = 0.0;
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            ra += (double)f[b + (long long)i * L.array];
-            rb += (double)f[b + (long long)(19 + i) * L.array];
+            ra += (double)f[b + (long long)i * L.pitch];
+            rb += (double)f[b + (long long)(19 + i) * L.pitch];
         }
     }
 }

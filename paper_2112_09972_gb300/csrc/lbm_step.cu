@@ -172,8 +172,8 @@ __global__ void __launch_bounds__(256) k_centre(const S* __restrict__ f, Layout 
             const long long b = L.at(0, 0, x, y, z);
 #pragma unroll
             for (int i = 0; i < 19; ++i) {
-                ra += (double)f[b + (long long)i * L.array];
-                rb += (double)f[b + (long long)(19 + i) * L.array];
+                ra += (double)f[b + (long long)i * L.pitch];
+                rb += (double)f[b + (long long)(19 + i) * L.pitch];
             }
         }
         const double phi = (ra - rb) / (ra + rb);
@@ -234,10 +234,11 @@ Layout make_layout(int Lx, int Ly, int Lz, int prec) {
     L.pitch = ((L.x0 + Lx + 1 + align - 1) / align) * align;
     L.ny = Ly + 2;
     L.nz = Lz + 2;
-    L.array = (long long)L.ny * L.pitch;
     // 16-bit deviation storage: 8 units of node block + 36 deviations per node
-    // (array is a multiple of 16, so every float4 block stays 16-byte aligned)
-    L.plane = (is_dev(prec) ? 44LL : 38LL) * L.array;
+    // (pitch is a multiple of 16 units, so every float4 block stays 16-byte
+    // aligned and row / 8 is whole)
+    L.row = (is_dev(prec) ? 44LL : 38LL) * L.pitch;
+    L.plane = (long long)L.ny * L.row;
     L.total = (long long)L.nz * L.plane;
     return L;
 }

@@ -30,7 +30,7 @@ struct Puller {
         if (PER) {
             return L.at(s, i, wrap(x - cx_(i), L.Lx), wrap(y - cy_(i), L.Ly), wrap(z - cz_(i), L.Lz));
         }
-        return L.at(s, i, x, y, z) - ((long long)cz_(i) * L.plane + (long long)cy_(i) * L.pitch + cx_(i));
+        return L.at(s, i, x, y, z) - ((long long)cz_(i) * L.plane + (long long)cy_(i) * L.row + cx_(i));
     }
 
     // Pull all 38 populations of fluid node (x, y, z).
