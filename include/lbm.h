@@ -120,9 +120,11 @@ typedef struct {
     int32_t frame;       /* lbm_frame, default LBM_FRAME_DROPLET */
     int32_t row_variant; /* row-tiled kernel: 1 per-thread loads of the pulled
                             populations (each plane read twice, the second
-                            time from L2), 2 whole pulled rows staged in shared
-                            memory by bulk copies (cp.async.bulk, one read),
-                            3 loader and collider threads per row (warp-
+                            time from L2), 2 the pulled rows of each plane
+                            staged in shared memory by bulk copies
+                            (cp.async.bulk, two planes ahead, one read; each
+                            node's populations carried in registers to its
+                            collision), 3 loader and collider threads per row (warp-
                             specialised: each population read once, staged in
                             shared memory for the collision); 0: automatic;
                             LBM_EINVAL outside 0..3 */

@@ -437,84 +437,138 @@ struct RowIO<TX, Dev<T>> {
 
 // ---- TMA-staged variant: bulk copies of whole pulled rows into shared memory ----
 
+// Direction i's velocity at run time (the bulk copies are spread over the
+// lanes of a warp, one population row per lane).
+__device__ __forceinline__ void dir_rt(int i, int& cx, int& cy, int& cz) {
+    // 2 bits per direction and axis: 0 -> -1, 1 -> 0, 2 -> +1
+    constexpr unsigned long long TX_ = [] {
+        unsigned long long t = 0;
+        for (int k = 0; k < 19; ++k) t |= (unsigned long long)(cx_(k) + 1) << (2 * k);
+        return t;
+    }();
+    constexpr unsigned long long TY_ = [] {
+        unsigned long long t = 0;
+        for (int k = 0; k < 19; ++k) t |= (unsigned long long)(cy_(k) + 1) << (2 * k);
+        return t;
+    }();
+    constexpr unsigned long long TZ_ = [] {
+        unsigned long long t = 0;
+        for (int k = 0; k < 19; ++k) t |= (unsigned long long)(cz_(k) + 1) << (2 * k);
+        return t;
+    }();
+    cx = (int)((TX_ >> (2 * i)) & 3ull) - 1;
+    cy = (int)((TY_ >> (2 * i)) & 3ull) - 1;
+    cz = (int)((TZ_ >> (2 * i)) & 3ull) - 1;
+}
+
 // Shared-memory image of one plane of one row for the staged variant: every
-// population row the row's pulled populations come from, as a row segment
-// that starts at x = -4 (16-byte aligned) and covers x - c_ix for every x of
-// the row.  Each source row is y - c_iy of plane p - c_iz, so over the grid
-// every population row is copied exactly once.
+// population row the row's pulled populations come from, as a segment of
+// SEG entries in which x sits at index x + 4.  Only the x range a direction
+// reads is copied: x = 0 .. TX - 1 for c_ix = 0, from x = -4 (the 16-byte
+// aligned start that covers the ghost at x = -1) for c_ix = +1, up to
+// x = TX + 3 (covering x = TX) for c_ix = -1.  Each source row is y - c_iy of
+// plane p - c_iz, so over the grid every population row is copied once.  The
+// copies are issued by the lanes of warp 0, one population row per lane,
+// after lane 0 has armed the plane's mbarrier with their total size.
+//
+// Raw is what a thread carries in registers from the plane's density pass to
+// its collision one march step later (the stage is refilled in between).
 template <int TX, typename ST>
 struct StagePlane;
 
 template <int TX>
 struct StagePlane<TX, float> {
-    static constexpr int SEG = TX + 8;  // floats per segment, x = -4 .. TX + 3
-    static constexpr unsigned BYTES = 38u * SEG * 4u;
+    static constexpr int SEG = TX + 8;
+    static constexpr unsigned SMEM = 38u * SEG * 4u;                               // bytes of the image
+    static constexpr unsigned BYTES = 2u * (9u * 4u * TX + 10u * 4u * (TX + 4));  // bytes copied per plane
+    struct Raw {
+        float f[2][19];
+    };
     static __device__ __forceinline__ void issue(const float* src, const Layout& L, int y, int p, unsigned dst,
-                                                 unsigned mbar) {
-#pragma unroll
-        for (int a = 0; a < 38; ++a) {
-            const int s = a / 19, i = a % 19;
-            bulk_g2s(dst + 4u * SEG * a, src + L.at(s, i, -4, y - cy_(i), p - cz_(i)), 4u * SEG, mbar);
+                                                 unsigned mbar, int lane) {
+        for (int a = lane; a < 38; a += 32) {
+            const int s = a / 19, i = a - 19 * s;
+            int cx, cy, cz;
+            dir_rt(i, cx, cy, cz);
+            const int lo = cx > 0 ? -4 : 0;
+            const unsigned len = cx != 0 ? 4u * (TX + 4) : 4u * TX;
+            bulk_g2s(dst + 4u * (unsigned)(SEG * a + lo + 4), src + L.at(s, i, lo, y - cy, p - cz), len, mbar);
         }
     }
-    static __device__ __forceinline__ void densities(const float* st, int x, float& ra, float& rb) {
-        ra = st[x + 4];
-        rb = st[19 * SEG + x + 4];
+    // the node's 38 pulled populations and its densities, summed in the
+    // order of RowIO::density
+    static __device__ __forceinline__ void load(const float* st, int x, Raw& r, float& ra, float& rb) {
+        const float* b = st + x + 4;
+        sfor<19>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            r.f[0][i] = b[i * SEG - cx_(i)];
+            r.f[1][i] = b[(19 + i) * SEG - cx_(i)];
+        });
+        ra = r.f[0][0];
+        rb = r.f[1][0];
 #pragma unroll
         for (int i = 1; i < 19; i += 2) {
-            ra += st[i * SEG + x - cx_(i) + 4] + st[(i + 1) * SEG + x - cx_(i + 1) + 4];
-            rb += st[(19 + i) * SEG + x - cx_(i) + 4] + st[(20 + i) * SEG + x - cx_(i + 1) + 4];
+            ra += r.f[0][i] + r.f[0][i + 1];
+            rb += r.f[1][i] + r.f[1][i + 1];
         }
     }
-    static __device__ __forceinline__ void populations(const float* st, int x, float (&f)[2][19]) {
+    static __device__ __forceinline__ void unpack(const Raw& r, float (&f)[2][19]) {
 #pragma unroll
         for (int s = 0; s < 2; ++s)
 #pragma unroll
-            for (int i = 0; i < 19; ++i) f[s][i] = st[(s * 19 + i) * SEG + x - cx_(i) + 4];
+            for (int i = 0; i < 19; ++i) f[s][i] = r.f[s][i];
     }
 };
 
 template <int TX, typename T>
 struct StagePlane<TX, Dev<T>> {
-    static constexpr int SEG = TX + 8;  // words per deviation segment, x = -4 .. TX + 3
+    static constexpr int SEG = TX + 8;  // words per deviation segment
     static constexpr unsigned NODE_BYTES = 16u * TX;
-    static constexpr unsigned BYTES = NODE_BYTES + 18u * SEG * 4u;
+    static constexpr unsigned SMEM = NODE_BYTES + 18u * SEG * 4u;
+    static constexpr unsigned BYTES = NODE_BYTES + 8u * 4u * TX + 10u * 4u * (TX + 4);
+    struct Raw {
+        float4 o;
+        unsigned w[19];  // w[i]: the word of direction i >= 1
+    };
     static __device__ __forceinline__ void issue(const Dev<T>* src, const Layout& L, int y, int p, unsigned dst,
-                                                 unsigned mbar) {
-        bulk_g2s(dst, reinterpret_cast<const float4*>(src) + L.dev_node(0, y, p), NODE_BYTES, mbar);
-        const unsigned* w = reinterpret_cast<const unsigned*>(src);
-#pragma unroll
-        for (int i = 1; i < 19; ++i)
-            bulk_g2s(dst + NODE_BYTES + 4u * SEG * (i - 1), w + L.dev_word(i, -4, y - cy_(i), p - cz_(i)), 4u * SEG,
-                     mbar);
+                                                 unsigned mbar, int lane) {
+        if (lane == 0) {
+            bulk_g2s(dst, reinterpret_cast<const float4*>(src) + L.dev_node(0, y, p), NODE_BYTES, mbar);
+        } else if (lane < 19) {
+            const int i = lane;
+            int cx, cy, cz;
+            dir_rt(i, cx, cy, cz);
+            const int lo = cx > 0 ? -4 : 0;
+            const unsigned len = cx != 0 ? 4u * (TX + 4) : 4u * TX;
+            const unsigned* w = reinterpret_cast<const unsigned*>(src);
+            bulk_g2s(dst + NODE_BYTES + 4u * (unsigned)(SEG * (i - 1) + lo + 4), w + L.dev_word(i, lo, y - cy, p - cz),
+                     len, mbar);
+        }
     }
-    static __device__ __forceinline__ const unsigned* words(const float* st) {
-        return reinterpret_cast<const unsigned*>(reinterpret_cast<const char*>(st) + NODE_BYTES);
-    }
-    static __device__ __forceinline__ void densities(const float* st, int x, float& ra, float& rb) {
-        const float4 o = reinterpret_cast<const float4*>(st)[x];
-        const unsigned* w = words(st);
+    static __device__ __forceinline__ void load(const float* st, int x, Raw& r, float& ra, float& rb) {
+        r.o = reinterpret_cast<const float4*>(st)[x];
+        const unsigned* b = reinterpret_cast<const unsigned*>(reinterpret_cast<const char*>(st) + NODE_BYTES) + x + 4;
         float da = 0.f, db = 0.f;
-#pragma unroll
-        for (int i = 1; i < 19; i += 2) {
-            const float2 u = dev_unpack2<T>(w[(i - 1) * SEG + x - cx_(i) + 4]);
-            const float2 v = dev_unpack2<T>(w[i * SEG + x - cx_(i + 1) + 4]);
+        sfor<9>([&](auto K) {
+            constexpr int i = 2 * decltype(K)::value + 1;
+            r.w[i] = b[(i - 1) * SEG - cx_(i)];
+            r.w[i + 1] = b[i * SEG - cx_(i + 1)];
+            const float2 u = dev_unpack2<T>(r.w[i]);
+            const float2 v = dev_unpack2<T>(r.w[i + 1]);
             da += u.x + v.x;
             db += u.y + v.y;
-        }
-        ra = o.z + (1.f - wgt<float>(0)) * o.x + da;
-        rb = o.w + (1.f - wgt<float>(0)) * o.y + db;
+        });
+        ra = r.o.z + (1.f - wgt<float>(0)) * r.o.x + da;
+        rb = r.o.w + (1.f - wgt<float>(0)) * r.o.y + db;
     }
-    static __device__ __forceinline__ void populations(const float* st, int x, float (&f)[2][19]) {
-        const float4 o = reinterpret_cast<const float4*>(st)[x];
-        const unsigned* w = words(st);
-        f[0][0] = o.z;
-        f[1][0] = o.w;
+    static __device__ __forceinline__ void unpack(const Raw& r, float (&f)[2][19]) {
+        f[0][0] = r.o.z;
+        f[1][0] = r.o.w;
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
-            const float2 v = dev_unpack2<T>(w[(i - 1) * SEG + x - cx_(i) + 4]);
-            f[0][i] = wgt<float>(i) * o.x + v.x;
-            f[1][i] = wgt<float>(i) * o.y + v.y;
+            const float2 v = dev_unpack2<T>(r.w[i]);
+            f[0][i] = wgt<float>(i) * r.o.x + v.x;
+            f[1][i] = wgt<float>(i) * r.o.y + v.y;
         }
     }
 };
@@ -549,13 +603,15 @@ struct FastLayout {
 };
 
 // Shared memory of the staged variant beyond the density ring: NST stage
-// mbarriers, then (128-byte aligned) NST plane images.
+// mbarriers, then (128-byte aligned) NST plane images.  March plane k lives
+// in stage k mod 2: while plane k is collided (from registers), the copies of
+// planes k + 2 and k + 3 are in flight.
 template <int TX, int CY, typename ST>
 struct StagedLayout {
-    static constexpr int NST = 3;  // march planes k (resident), k + 1 and k + 2 (in flight)
+    static constexpr int NST = 2;
     static constexpr size_t mbar_off = FastLayout<TX, CY>::bytes;
     static constexpr size_t stage_off = ((mbar_off + 8 * NST + 127) / 128) * 128;
-    static constexpr size_t bytes = stage_off + (size_t)NST * StagePlane<TX, ST>::BYTES;
+    static constexpr size_t bytes = stage_off + (size_t)NST * StagePlane<TX, ST>::SMEM;
 };
 
 // Collision of one node from its 38 pulled populations f and the density
@@ -804,7 +860,7 @@ __global__ void __launch_bounds__(TX, MINB)
     const unsigned halo_mbar = cluster_addr(mbar_s, hs.rank);
 
     // staged variant: plane images and their mbarriers (one arrival, by
-    // thread 0, plus the bytes of the copies)
+    // lane 0 of warp 0, plus the bytes of the copies)
     const unsigned smbar_s = smem_u32(ring) + (unsigned)SL::mbar_off;
     const unsigned stage_s = smem_u32(ring) + (unsigned)SL::stage_off;
     const float* stage = reinterpret_cast<const float*>(reinterpret_cast<const char*>(ring) + SL::stage_off);
@@ -830,22 +886,26 @@ __global__ void __launch_bounds__(TX, MINB)
     unsigned long long keep;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
 
-    // Staged variant: march plane k lives in stage k mod NST.  Thread 0 fills
-    // a stage (expect_tx, then the copies); every thread waits on the stage's
-    // mbarrier (bounded) before its first read of the plane.  Only the planes
-    // this chunk reads and that lie in the box are copied.
+    // Staged variant: march plane k lives in stage k mod NST.  Warp 0 fills a
+    // stage (lane 0 arms its mbarrier with the bytes to come, then every
+    // lane issues its population rows); every thread waits on the stage's
+    // mbarrier (bounded) before it reads the plane.  Only the planes this
+    // chunk reads and that lie in the box are copied.
     auto plane_wanted = [&](int k) {
         const int p = plane_of(k);
         return k <= n + 1 && p >= 0 && p < L.Lz;
     };
     unsigned sphase = 0u;   // bit s: parity of stage s's next completion (every thread)
-    unsigned pending = 0u;  // thread 0: stages with copies it has not seen complete
-    auto fill = [&](int k) {
+    unsigned pending = 0u;  // lane 0 of warp 0: stages with copies it has not seen complete
+    auto fill = [&](int k) {  // warp 0
         if (!plane_wanted(k)) return;
         const int st = k % NST;
-        mbar_expect_tx(smbar_s + 8u * st, SP::BYTES);
-        SP::issue(src, L, y, plane_of(k), stage_s + (unsigned)(st * SP::BYTES), smbar_s + 8u * st);
-        pending |= 1u << st;
+        if (x == 0) {
+            mbar_expect_tx(smbar_s + 8u * st, SP::BYTES);
+            pending |= 1u << st;
+        }
+        __syncwarp();
+        SP::issue(src, L, y, plane_of(k), stage_s + (unsigned)(st * SP::SMEM), smbar_s + 8u * st, x);
     };
     auto stage_wait = [&](int k) {
         const int st = k % NST;
@@ -854,25 +914,37 @@ __global__ void __launch_bounds__(TX, MINB)
         else atomicOr(d_err, 4);
         sphase ^= 1u << st;
     };
-    auto stage_ptr = [&](int k) { return stage + (size_t)(k % NST) * (SP::BYTES / 4); };
+    auto stage_ptr = [&](int k) { return stage + (size_t)(k % NST) * (SP::SMEM / 4); };
     if constexpr (STAGED) {
-        if (x == 0)
-            for (int k = 0; k < 3; ++k) fill(k);
+        if (x < 32) {
+            fill(0);
+            fill(1);
+        }
     }
 
     // Post-streaming densities of march plane k: the own node into row 0 of
     // this CTA's ring and into the neighbours' rows -1 / +1; the outer-halo
     // share into the edge CTA's ring.  Ghost densities outside the box.
-    // Every CTA then expects TX_BYTES on its slot barrier.
-    auto densities = [&](int k) {
+    // Every CTA then expects TX_BYTES on its slot barrier.  The staged
+    // variant also keeps the node's pulled populations in `carry`.
+    auto densities = [&](int k, typename SP::Raw* carry) {
         const int p = plane_of(k);
         const int sl = k & (S - 1);
         const bool in = p >= 0 && p < L.Lz;
         float ra = m.rho_b[0], rb = m.rho_b[1];
+        // the outer-halo loads first, so that their latency overlaps the rest
+        float hv = 0.f, ha = m.rho_b[0], hb = m.rho_b[1];
+        if (hs.cta && in && hs.in) {
+            if constexpr (DEV) {
+                if (hs.thr) IO::densities(planes(hbase, p, hs.col), keep, ha, hb);
+            } else {
+                hv = IO::template density<0>(planes(hbase, p, 0), keep);
+            }
+        }
         if (in) {
             if constexpr (STAGED) {
                 stage_wait(k);
-                SP::densities(stage_ptr(k), x, ra, rb);
+                SP::load(stage_ptr(k), x, *carry, ra, rb);
             } else {
                 IO::densities(planes(nbase, p, x), keep, ra, rb);
             }
@@ -885,14 +957,9 @@ __global__ void __launch_bounds__(TX, MINB)
         if (hs.cta) {
             const unsigned hoff = 8u * (unsigned)(sl * FL::SLOT + (hs.row + 1) * RW + hs.col + 1);
             if constexpr (DEV) {
-                if (hs.thr) {
-                    float ha = m.rho_b[0], hb = m.rho_b[1];
-                    if (in && hs.in) IO::densities(planes(hbase, p, hs.col), keep, ha, hb);
-                    st_async_f2(halo_ring + hoff, ha, hb, halo_mbar + mb);
-                }
+                if (hs.thr) st_async_f2(halo_ring + hoff, ha, hb, halo_mbar + mb);
             } else {
-                float v = m.rho_b[hs.comp];
-                if (in && hs.in) v = IO::template density<0>(planes(hbase, p, 0), keep);
+                const float v = in && hs.in ? hv : m.rho_b[hs.comp];
                 const float other = __shfl_xor_sync(0xffffffffu, v, 1);
                 if (hs.thr) st_async_f2(halo_ring + hoff, v, other, halo_mbar + mb);
             }
@@ -908,48 +975,82 @@ __global__ void __launch_bounds__(TX, MINB)
     float cm[4] = {0.f, 0.f, 0.f, 0.f};
     int bad = 0;
     const float px = (float)x - 0.5f * (float)(L.Lx - 1), py = (float)y - 0.5f * (float)(L.Ly - 1);
-
-    densities(0);
-    densities(1);
-    wait_rows(0);
-    wait_rows(1);
-    if constexpr (STAGED) {
-        __syncthreads();  // march plane 0 read by all: its stage takes plane 3
-        if (x == 0) {
-            fence_proxy_async();
-            fill(3);
-        }
-    }
-    for (int k = 1; k <= n; ++k) {
-        densities(k + 1);
+    auto collide = [&](int k, const float (&f)[2][19]) {
         const int z = plane_of(k);
-        // this node's populations for the collision, read while the
-        // neighbour rows of plane k + 1 are in flight
-        float f[2][19];
-        if constexpr (STAGED) SP::populations(stage_ptr(k), x, f);
-        else IO::populations(planes(nbase, z, x), f);
-        __syncthreads();  // own row of plane k + 1 complete
-        if constexpr (STAGED) {
-            // plane k has been read by every thread: its stage takes plane k + 3
-            if (x == 0) {
-                fence_proxy_async();
-                fill(k + 3);
-            }
-        }
-        wait_rows(k + 1);
-
         const float2* rprev = ring + ((k - 1) & (S - 1)) * FL::SLOT + x + 1;
         const float2* rcur = ring + (k & (S - 1)) * FL::SLOT + x + 1;
         const float2* rnext = ring + ((k + 1) & (S - 1)) * FL::SLOT + x + 1;
         collide_node<TX, ST, MRT>(down ? rnext : rprev, rcur, down ? rprev : rnext, f, m, IO::out(dst, L, x, y, z),
                                   cm, bad, px, py, (float)z - 0.5f * (float)(L.Lz - 1));
-        // Before a later plane reuses this plane's own-row slot, all threads
-        // must be done reading it: the __syncthreads of the next iterations
-        // (S - 1 march planes apart) order that.
+    };
+
+    if constexpr (STAGED) {
+        // Planes k + 1 .. k + 3 are in the stages or in flight while plane k
+        // is collided from the registers its density pass filled.
+        typename SP::Raw cur, nxt;
+        densities(0, &nxt);
+        __syncthreads();  // march plane 0 read by all: its stage takes plane 2
+        if (x < 32) {
+            fence_proxy_async();
+            fill(2);
+        }
+        densities(1, &cur);
+        __syncthreads();
+        if (x < 32) {
+            fence_proxy_async();
+            fill(3);
+        }
+        wait_rows(0);
+        wait_rows(1);
+        // one march step: the density pass of plane k + 1 into `next`, the
+        // collision of plane k from `now`
+        auto step = [&](int k, const typename SP::Raw& now, typename SP::Raw& next) {
+            densities(k + 1, &next);
+            __syncthreads();  // own row of plane k + 1 complete; its stage read by all
+            if (x < 32) {
+                fence_proxy_async();
+                fill(k + 3);
+            }
+            wait_rows(k + 1);
+            float f[2][19];
+            SP::unpack(now, f);
+            collide(k, f);
+        };
+        if constexpr (DEV) {
+            for (int k = 1; k <= n; ++k) {
+                step(k, cur, nxt);
+                cur = nxt;
+            }
+        } else {
+            // two steps per trip, so that the carried registers swap roles
+            // instead of being copied
+            for (int k = 1; k <= n; k += 2) {
+                step(k, cur, nxt);
+                if (k + 1 <= n) step(k + 1, nxt, cur);
+            }
+        }
+    } else {
+        densities(0, nullptr);
+        densities(1, nullptr);
+        wait_rows(0);
+        wait_rows(1);
+        for (int k = 1; k <= n; ++k) {
+            densities(k + 1, nullptr);
+            // this node's populations for the collision, read while the
+            // neighbour rows of plane k + 1 are in flight
+            float f[2][19];
+            IO::populations(planes(nbase, plane_of(k), x), f);
+            __syncthreads();  // own row of plane k + 1 complete
+            wait_rows(k + 1);
+            collide(k, f);
+            // Before a later plane reuses this plane's own-row slot, all
+            // threads must be done reading it: the __syncthreads of the next
+            // iterations (S - 1 march planes apart) order that.
+        }
     }
     if (bad) atomicOr(d_err, bad);
-    // staged variant: copies whose completion thread 0 did not observe (a
-    // wait that gave up) are waited for again, bounded, before the CTA exits
+    // staged variant: copies whose completion lane 0 of warp 0 did not observe
+    // (a wait that gave up) are waited for again, bounded, before the CTA exits
     if constexpr (STAGED) {
         if (x == 0) {
             for (int st = 0; st < NST; ++st) {
@@ -1157,11 +1258,12 @@ __global__ void __launch_bounds__(2 * TX, MINB)
 }
 
 // Resident CTAs per SM asked of the compiler (it sets the register budget)
-// for the direct-load variant, per row width; the staged variant is bounded
-// by its shared memory (about 2 x 128-thread CTAs per SM).
+// for the direct-load variant, per row width; the staged variant holds two
+// plane images (about 53 KB of shared memory at TX = 128, 105 KB at 256),
+// which fit 4 CTAs of 128 threads or 2 of 256 per SM.
 template <int TX, bool STAGED>
 constexpr int row_min_blocks() {
-    if (STAGED) return 256 / TX > 0 ? 256 / TX : 1;
+    if (STAGED) return TX >= 256 ? 2 : 512 / TX;
     return TX == 32 ? LBM_ROWS_MINB_32
                     : (TX == 64 ? LBM_ROWS_MINB_64 : (TX == 128 ? LBM_ROWS_MINB_128 : LBM_ROWS_MINB_256));
 }

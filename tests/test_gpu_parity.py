@@ -267,16 +267,17 @@ def test_row_cluster_kernel_shapes(built, oracle_mod, box, variant):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16dev", "bf16dev"])
 @pytest.mark.parametrize("box,z_chunk", [((128, 32, 40), 8), ((64, 16, 13), 5), ((32, 8, 6), 1)])
-def test_warp_specialised_variant_bit_identical(built, oracle_mod, precision, box, z_chunk):
-    """Loader and collider threads (variant 3) compute the same node updates
-    as per-thread loads (variant 1) in the same order: with the same z chunks
-    (hence the same centre-of-mass partials and frame origin) the stored
-    states agree bit for bit after 25 steps of an OU-driven droplet, including
-    chunks of one plane and ragged last chunks."""
+def test_row_variants_bit_identical(built, oracle_mod, precision, box, z_chunk):
+    """Shared-memory staging with the populations carried in registers
+    (variant 2) and loader and collider threads (variant 3) compute the same
+    node updates as per-thread loads (variant 1) in the same order: with the
+    same z chunks (hence the same march directions, centre-of-mass partials
+    and frame origin) the stored states agree bit for bit after 25 steps of an
+    OU-driven droplet, including chunks of one plane and ragged last chunks."""
     hist = inputs.ou_gradient_history(25, 20.0, 600.0, seed=11)
     R = min(box) / 4.0
     states = []
-    for variant in (1, 3):
+    for variant in (1, 2, 3):
         g = DropletLBM(box, R, (0.5 / 3, 0.5 / 3), 3.5, precision=precision, rho_hi=1.0, rho_lo=workloads.RHO_LO,
                        z_chunk=z_chunk, row_variant=variant)
         assert g.launch_shape()[1] == z_chunk
@@ -284,5 +285,6 @@ def test_warp_specialised_variant_bit_identical(built, oracle_mod, precision, bo
         g.step(25)
         states.append((g.populations(), g.deformation()[0]))
         g.close()
-    assert np.array_equal(states[0][0], states[1][0])
-    assert states[0][1] == states[1][1]
+    for other in states[1:]:
+        assert np.array_equal(states[0][0], other[0])
+        assert states[0][1] == other[1]
