@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--no-surrogate", action="store_true")
     p.add_argument("--precision-steps", type=int, default=400)
     p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--no-trajectory", action="store_true")
     return p.parse_args()
 
 
@@ -102,6 +103,13 @@ def measured_peaks():
 ROW_KERNEL_SOURCES = ("lbm_fast.cu", "lbm_lattice.cuh", "lbm_internal.h", "lbm_dev.cuh", "lbm_step.cu", "lbm_centre.cuh")
 
 
+# The stream-collide kernel a context runs, by lbm_launch_variant.
+KERNEL_NAMES = {0: "k_stream_collide (generic tile kernel)",
+                1: "k_stream_collide_rows (row kernel, per-thread loads)",
+                2: "k_stream_collide_rows (row kernel, shared-memory staging)",
+                3: "k_stream_collide_ws (row kernel, loader and collider threads)"}
+
+
 def row_kernel_sha1():
     h = hashlib.sha1()
     for name in ROW_KERNEL_SOURCES:
@@ -124,8 +132,49 @@ def kernel_traffic(key):
     return e.get("dram_bytes_per_launch")
 
 
+class NvmlClocks:
+    """Reads the SM clock, its maximum, the power draw and the clock event
+    (throttle) reasons through NVML (libnvidia-ml, via ctypes).  Reads only:
+    nothing here changes a GPU setting."""
+
+    # clock event reason bits of NVML
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, index):
+        import ctypes
+
+        self.ct = ctypes
+        self.lib = None
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                self.lib = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        if self.lib is None or self.lib.nvmlInit_v2() != 0:
+            raise OSError("NVML not available")
+        self.dev = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.dev)) != 0:
+            raise OSError("NVML device not found")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        v = ctypes.c_uint()
+        self.max_sm = float(v.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.dev, 1, ctypes.byref(v)) == 0 else None
+
+    def read(self):
+        ct = self.ct
+        clk, mw, rs = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.dev, 1, ct.byref(clk)) != 0:  # 1: NVML_CLOCK_SM
+            return None
+        self.lib.nvmlDeviceGetPowerUsage(self.dev, ct.byref(mw))
+        self.reasons_fn(self.dev, ct.byref(rs))
+        return float(clk.value), mw.value / 1000.0, int(rs.value)
+
+
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """SM clock and throttle-reason samples during the timed region: NVML read
+    every millisecond from a host thread (so that even a timed region of a few
+    milliseconds has samples), else nvidia-smi every 100 ms."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -135,8 +184,21 @@ class ClockSampler:
         self.index = index
         self.rows = []
         self.proc = None
+        self.nvml = None
+        self.stop_flag = threading.Event()
+        self.thread = None
+        self.source = None
 
     def start(self):
+        try:
+            self.nvml = NvmlClocks(self.index)
+        except (OSError, AttributeError):
+            self.nvml = None
+        if self.nvml is not None:
+            self.source = "nvml, 1 ms"
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
@@ -144,30 +206,49 @@ class ClockSampler:
         except OSError:
             self.proc = None
             return
+        self.source = "nvidia-smi, 100 ms"
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
 
+    def _poll(self):
+        while True:
+            r = self.nvml.read()
+            if r is not None:
+                clk, watts, bits = r
+                names = [n for b, n in NvmlClocks.REASONS.items() if bits & b]
+                self.rows.append((clk, self.nvml.max_sm, watts, names))
+            if self.stop_flag.wait(0.001):
+                break
+
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([v.strip() for v in line.split(",")])
+            v = [x.strip() for x in line.split(",")]
+            if len(v) < 7 or not v[0].replace(".", "").isdigit():
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            mx = float(v[1]) if v[1].replace(".", "").isdigit() else None
+            self.rows.append((float(v[0]), mx, None, [names[k] for k in range(4) if v[3 + k] == "Active"]))
 
     def stop(self):
-        if self.proc is None:
+        if self.nvml is not None:
+            self.stop_flag.set()
+            self.thread.join(timeout=2)
+        elif self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+        else:
             return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        self.thread.join(timeout=2)
-        sm = [float(r[0]) for r in self.rows if len(r) >= 7 and r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if len(r) >= 7 and r[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in self.rows if len(r) >= 7 for k in range(4) if r[3 + k] == "Active"})
+        sm = [r[0] for r in self.rows]
+        mx = [r[1] for r in self.rows if r[1]]
+        reasons = sorted({n for r in self.rows for n in r[3]})
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "source": self.source}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(sm)}
+                "samples": len(sm), "source": self.source}
 
 
 def cpu_baseline(w, hist, steps=None):
@@ -327,7 +408,98 @@ def precision_bench(steps, stream, dev):
         g.close()
     out["peak"] = peak
     out["peak_kind"] = peak_kind
+    out["vs_fp64_oracle"] = precision_vs_oracle(stream, dev)
     return out
+
+
+def precision_vs_oracle(stream, dev):
+    """Each storage form on the 64^3, R = 8 downscale of the precision case
+    (same gradient history, rescaled to the box) against the FP64 oracle's
+    result for the same steps, stored in tests/golden/precision_downscale64.json
+    by tests/golden/make_golden_precision.py: D, the major axis, the masses,
+    and the densities and velocity at the stored sample of nodes."""
+    import numpy as np
+
+    from paper_2112_09972_gb300 import workloads
+    from paper_2112_09972_gb300.lbm import DropletLBM
+
+    path = os.path.join(ROOT, "tests", "golden", "precision_downscale64.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        ref = json.load(fh)
+    w = workloads.C4_DOWNSCALED
+    box = (w.box,) * 3
+    steps = int(ref["steps"])
+    hist = w.gradient_history(steps + 1)
+    idx = np.asarray(ref["sample_nodes_zyx"])
+    z, y, x = idx[:, 0], idx[:, 1], idx[:, 2]
+    ra_ref, rb_ref, u_ref = (np.asarray(ref[k]) for k in ("rho_a", "rho_b", "u"))
+    ax_ref = np.asarray(ref["axes"])[:, 0]
+    out = {"workload": w.name, "steps": steps, "D_oracle": ref["D"], "forms": {}}
+    for prec in ("fp32", "fp16dev", "bf16dev"):
+        g = DropletLBM(box, w.R, w.visc, w.G, precision=prec, rho_hi=w.rho_hi, rho_lo=w.rho_lo, xi=w.xi,
+                       stream=stream.cuda_stream, device=dev)
+        g.set_gradient_table(np.arange(steps + 1), hist)
+        g.step(steps)
+        D, axes, lam, centre = g.deformation()
+        ra, rb, u = g.fields()
+        mass, _ = g.checksums()
+        g.close()
+        out["forms"][prec] = {
+            "D": D,
+            "rel_D_error": abs(D - ref["D"]) / abs(ref["D"]),
+            "major_axis_misalignment": float(1.0 - abs(np.dot(axes[:, 0], ax_ref))),
+            "rel_mass_error": float(np.max(np.abs(np.asarray(mass) - ref["mass"]) / np.asarray(ref["mass"]))),
+            "rho_rel_linf_sampled": float(max(np.max(np.abs(ra[z, y, x] - ra_ref)), np.max(np.abs(rb[z, y, x] - rb_ref)))
+                                          / max(ref["rho_a_max"], 1.0)),
+            "u_rel_linf_sampled": float(np.max(np.abs(u[z, y, x] - u_ref)) / ref["u_max"]),
+        }
+    return out
+
+
+def trajectory_bench(stream, dev, record_every=200):
+    """The throughput case over its full length (20000 steps of the Eq. 15
+    OU history, 128^3, R = 16, fp32): D(t) of the LBM droplet (Eq. 4) every
+    `record_every` steps next to the Maffettone-Minale model (Eqs. 1, 2, 5)
+    driven by the same gradient history on the GPU, tau_d = eta_s R / sigma,
+    lambda = 1 -- the comparison of Sec. 5 (Fig. 5) at the small capillary
+    number of this workload.  Context, not a pin."""
+    import numpy as np
+    import torch
+
+    from paper_2112_09972_gb300 import workloads
+    from paper_2112_09972_gb300.lbm import DropletLBM, mm_integrate
+
+    w = workloads.C2_THROUGHPUT
+    n = w.steps
+    hist = w.gradient_history(n + 1)
+    g = DropletLBM((w.box,) * 3, w.R, w.visc, w.G, precision=w.precision, rho_hi=w.rho_hi, rho_lo=w.rho_lo,
+                   xi=w.xi, stream=stream.cuda_stream, device=dev)
+    g.set_gradient_table(np.arange(n + 1), hist)
+    D_lbm = [g.deformation()[0]]
+    t0 = time.perf_counter()
+    for _ in range(n // record_every):
+        g.step(record_every)
+        D_lbm.append(g.deformation()[0])
+    lbm_s = time.perf_counter() - t0
+    g.close()
+    tau_d = w.eta_s * w.R / workloads.SIGMA
+    A = torch.from_numpy(hist.reshape(n + 1, 1, 9)).to(device=f"cuda:{dev}", dtype=torch.float64)
+    D_mm = mm_integrate(A, tau_d, 1.0, substeps=4, record_every=record_every, precision="fp64",
+                        stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    D_mm = D_mm[:, 0].cpu().numpy()
+    D_lbm = np.asarray(D_lbm)
+    m = min(len(D_mm), len(D_lbm))
+    a, b = D_lbm[5:m], D_mm[5:m]  # after the first 1000 steps (the initial sphere relaxing)
+    return {"workload": w.name, "steps": n, "record_every": record_every, "lbm_seconds": round(lbm_s, 2),
+            "ca_rms_frobenius": round(w.frobenius_ca_rms(hist), 5), "ca_rms_elementwise_max": round(w.capillary_rms(hist), 5),
+            "tau_d_steps": round(tau_d, 2),
+            "D_lbm_mean": float(a.mean()), "D_mm_mean": float(b.mean()), "D_lbm_max": float(a.max()),
+            "D_mm_max": float(b.max()), "mean_ratio_lbm_over_mm": float(a.mean() / b.mean()),
+            "correlation": float(np.corrcoef(a, b)[0, 1]),
+            "D_lbm": [round(float(v), 5) for v in D_lbm[::5]], "D_mm": [round(float(v), 5) for v in D_mm[::5]]}
 
 
 def surrogate_bench(stream, dev, n_infer=65536, n_ref=512, n_train=1536, train_steps=30000):
@@ -461,7 +633,7 @@ def variants_bench(stream, dev, steps=200):
         s = per_step(g, steps)
         out[name] = {"mlups": round(w.nodes / s / 1e6, 1), "us_per_step": round(s * 1e6, 1),
                      "achieved_gbs_whole_step": round(BYTES_PER_LUP_FP32 * w.nodes / s / 1e9, 1),
-                     "kernel": "k_stream_collide_rows" if g.launch_shape()[0] == 1 else "k_stream_collide (generic tile)",
+                     "kernel": KERNEL_NAMES[g.launch_variant()],
                      "D": g.deformation()[0]}
         if mrt is None:
             # target: the current total mass of component A, a factor of one,
@@ -495,21 +667,42 @@ def variants_bench(stream, dev, steps=200):
 
 
 def run_reference(args, w):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores, on
+    the same workload, metric and unit.  W untimed warm-up steps, then K timed
+    steps of the full box (each step the whole 128^3 update); when K full
+    steps would take more than about two minutes, the first steps that fit
+    in that time are timed and the line says so in its sample."""
+    import oracle
+
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    hist = w.gradient_history(args.steps + args.warmup + 3)
-    # each "step" of this arm is one oracle step of the same 128^3 workload
-    k = max(1, min(args.steps, 3))
-    cb = cpu_baseline(w, hist, steps=k)
+    K, W = max(1, args.steps), max(0, args.warmup)
+    hist = w.gradient_history(K + W + 2)
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    box = (w.box,) * 3
+    o = oracle.OracleLBM(box, (w.tau, w.tau), w.G, (w.rho_lo, w.rho_hi))
+    o.init_droplet(w.R, w.xi, w.rho_hi, w.rho_lo, hist[0])
+    t0 = time.perf_counter()
+    for t in range(W):
+        o.step(hist[t])
+    per_step = (time.perf_counter() - t0) / W if W else None
+    budget_s = 120.0
+    k = K if per_step is None or K * per_step <= budget_s else max(1, int(budget_s / per_step))
+    t0 = time.perf_counter()
+    for t in range(k):
+        o.step(hist[W + t])
+    el = time.perf_counter() - t0
+    mlups = w.nodes * k / el / 1e6
+    sample = f"{k} of the {K} timed steps of the full {w.box}^3 box (FP64, {cores} host cores), {el:.1f} s"
     line = {
-        "impl": "reference", "metric": "MLUPS", "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
-        "steps": k, "warmup": 1, "ms_per_step": round(w.nodes / (cb["value"] * 1e6) * 1e3, 3),
+        "impl": "reference", "metric": "MLUPS", "value": round(mlups, 4), "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": K, "warmup": W, "ms_per_step": round(el / k * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "box": w.box, "R": w.R, "precision": "fp64", "sample_steps": k},
-        "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": cb["value"],
+        "config": {"workload": w.name, "box": w.box, "R": w.R, "precision": "fp64", "timed_steps": k},
+        "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": round(mlups, 4),
                          "unit": "MLUPS"},
-        "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
 
@@ -576,6 +769,7 @@ def main():
     kb_ms, kb_n = g.profile_read(1)
     g.profile(0)
     ty, zc, ctas = g.launch_shape()
+    kernel_name = KERNEL_NAMES[g.launch_variant()]
     t_max = max_over_ranks(ms, device="cuda")
     mlups = job_rate(w.nodes, K, world, t_max / 1e3)
 
@@ -620,6 +814,9 @@ def main():
     var = None
     if not args.no_variants and world == 1:
         var = variants_bench(stream, dev)
+    traj = None
+    if not args.no_trajectory and world == 1:
+        traj = trajectory_bench(stream, dev)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -646,9 +843,12 @@ def main():
         "data": "synthetic",
         "config": {"workload": w.name, "box": w.box, "R": w.R, "precision": w.precision,
                    "driving": "OU gradient history (T=2000 steps) rescaled by Eq. 15, u_LBM=0.1",
+                   "Ca_rms": round(w.frobenius_ca_rms(hist), 5),
+                   "Ca_rms_note": "eta_s R rms||A||_F / sigma of the timed history (Eq. 3); the configured "
+                                  "0.05/0.15/0.3 put the ghost speed above the Mach limit at L/R = 8",
                    "deformation_every": SAMPLE_EVERY, "l2": "inputs larger than L2 (2 x 370 MB buffers)",
                    "tile_y": ty, "z_chunk": zc, "ctas": ctas, "parallelism": f"replicas{world}"},
-        "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": round(achieved, 1),
+        "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "frac_of_nominal_8TBs": round(achieved / 8000.0, 4),
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": round(ka_avg_s * 1e6, 2),
@@ -664,6 +864,7 @@ def main():
         "precision": prec,
         "surrogate": sur,
         "variants": var,
+        "trajectory": traj,
         "D_last": samples[-1] if samples else None,
     }
     print(json.dumps(line))

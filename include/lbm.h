@@ -287,6 +287,13 @@ int lbm_profile_read(lbm_ctx* ctx, int kernel, double* total_ms, int64_t* launch
  * per CTA, CTAs. */
 int lbm_launch_shape(lbm_ctx* ctx, int32_t* tile_y, int32_t* z_chunk, int32_t* ctas);
 
+/* The stream-collide kernel in use: *variant = 0 the generic tile kernel
+ * (k_stream_collide), or the row-tiled cluster kernel's variant as in
+ * lbm_opts.row_variant (1 per-thread loads and 2 shared-memory staging, both
+ * k_stream_collide_rows; 3 loader and collider threads, k_stream_collide_ws).
+ * LBM_EINVAL for a NULL context or pointer. */
+int lbm_launch_variant(lbm_ctx* ctx, int32_t* variant);
+
 /*
  * Allocation-free droplet moments (an addition of this library; the paper has
  * no counterpart).  For callers that cannot allocate device memory when they

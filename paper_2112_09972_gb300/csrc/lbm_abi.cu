@@ -751,4 +751,11 @@ int lbm_launch_shape(lbm_ctx* c, int32_t* tile_y, int32_t* z_chunk, int32_t* cta
     return LBM_OK;
 }
 
+int lbm_launch_variant(lbm_ctx* c, int32_t* variant) {
+    if (!c || !variant) return LBM_EINVAL;
+    if (!c->shape.rows) *variant = 0;
+    else *variant = c->shape.variant == kRowStaged ? 2 : (c->shape.variant == kRowWs ? 3 : 1);
+    return LBM_OK;
+}
+
 }  // extern "C"

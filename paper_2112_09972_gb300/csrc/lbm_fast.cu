@@ -82,6 +82,15 @@ namespace cg = cooperative_groups;
 #ifndef LBM_ROWS_ALTERNATE
 #define LBM_ROWS_ALTERNATE 1
 #endif
+// Staged variant: planes prefetched into L2 ahead of the shared-memory stage
+// copies (0: none).
+#ifndef LBM_ROWS_L2_AHEAD
+#define LBM_ROWS_L2_AHEAD 0
+#endif
+// L2 priority of the outer-halo loads: 0 evict_last, 1 evict_first, 2 evict_normal.
+#ifndef LBM_ROWS_HALO_POLICY
+#define LBM_ROWS_HALO_POLICY 2
+#endif
 
 namespace lbmgb {
 namespace {
@@ -190,6 +199,11 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(mbar)
                  : "memory");
+}
+// Prefetch `bytes` (a multiple of 16) from a 16-byte aligned global address
+// into L2.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 // Order this thread's earlier generic-proxy accesses to shared memory before
 // later async-proxy (bulk copy) writes to it.
@@ -495,6 +509,17 @@ struct StagePlane<TX, float> {
             bulk_g2s(dst + 4u * (unsigned)(SEG * a + lo + 4), src + L.at(s, i, lo, y - cy, p - cz), len, mbar);
         }
     }
+    // the same population rows into L2 only (a later plane's copies then hit L2)
+    static __device__ __forceinline__ void prefetch(const float* src, const Layout& L, int y, int p, int lane) {
+        for (int a = lane; a < 38; a += 32) {
+            const int s = a / 19, i = a - 19 * s;
+            int cx, cy, cz;
+            dir_rt(i, cx, cy, cz);
+            const int lo = cx > 0 ? -4 : 0;
+            const unsigned len = cx != 0 ? 4u * (TX + 4) : 4u * TX;
+            bulk_prefetch_l2(src + L.at(s, i, lo, y - cy, p - cz), len);
+        }
+    }
     // the node's 38 pulled populations and its densities, summed in the
     // order of RowIO::density
     static __device__ __forceinline__ void load(const float* st, int x, Raw& r, float& ra, float& rb) {
@@ -543,6 +568,18 @@ struct StagePlane<TX, Dev<T>> {
             const unsigned* w = reinterpret_cast<const unsigned*>(src);
             bulk_g2s(dst + NODE_BYTES + 4u * (unsigned)(SEG * (i - 1) + lo + 4), w + L.dev_word(i, lo, y - cy, p - cz),
                      len, mbar);
+        }
+    }
+    static __device__ __forceinline__ void prefetch(const Dev<T>* src, const Layout& L, int y, int p, int lane) {
+        if (lane == 0) {
+            bulk_prefetch_l2(reinterpret_cast<const float4*>(src) + L.dev_node(0, y, p), NODE_BYTES);
+        } else if (lane < 19) {
+            const int i = lane;
+            int cx, cy, cz;
+            dir_rt(i, cx, cy, cz);
+            const int lo = cx > 0 ? -4 : 0;
+            const unsigned len = cx != 0 ? 4u * (TX + 4) : 4u * TX;
+            bulk_prefetch_l2(reinterpret_cast<const unsigned*>(src) + L.dev_word(i, lo, y - cy, p - cz), len);
         }
     }
     static __device__ __forceinline__ void load(const float* st, int x, Raw& r, float& ra, float& rb) {
@@ -819,6 +856,35 @@ struct HaloShare {
     }
 };
 
+// The march of a CTA of the direct and staged kernels: the z chunk
+// blockIdx.z of the CTA's row, odd chunks marching down when `alt`.  (The
+// kernel walks a list of such segments, continuing its march counter across
+// them; one segment per CTA is what the launches use.)
+struct Segment {
+    int g;      // row group (rows g CY .. g CY + CY - 1)
+    int z0, z1; // planes [z0, z1)
+    bool down;
+};
+template <int CY>
+struct MarchPlan {
+    int nseg, Lz, zchunk;
+    bool down;
+    __device__ __forceinline__ MarchPlan(const Layout& L, int zchunk_, int alt) {
+        Lz = L.Lz;
+        zchunk = zchunk_;
+        nseg = 1;
+        down = alt && (blockIdx.z & 1);
+    }
+    __device__ __forceinline__ Segment seg(int) const {
+        Segment sg;
+        sg.down = down;
+        sg.g = (int)blockIdx.y / CY;
+        sg.z0 = (int)blockIdx.z * zchunk;
+        sg.z1 = min(sg.z0 + zchunk, Lz);
+        return sg;
+    }
+};
+
 template <int TX, int CY, int MINB, typename ST, bool STAGED, bool MRT = false>
 __global__ void __launch_bounds__(TX, MINB)
     k_stream_collide_rows(const ST* __restrict__ src, ST* __restrict__ dst, Layout L, FastModel m, int zchunk,
@@ -836,28 +902,16 @@ __global__ void __launch_bounds__(TX, MINB)
 
     cg::cluster_group cluster = cg::this_cluster();
     const int x = threadIdx.x;
-    const int y = blockIdx.y;
-    const int rank = (int)cluster.block_rank();  // == y % CY for cluster dims (1, CY, 1)
-    const int Y0 = y - rank;
-    const int zc0 = blockIdx.z * zchunk;
-    const int zc1 = min(zc0 + zchunk, L.Lz);
-    const int n = zc1 - zc0;
-    // k-th plane of the march (k = 0 and n + 1 are the halo planes)
-    const bool down = alt && (blockIdx.z & 1);
-    auto plane_of = [&](int k) { return down ? zc1 - k : zc0 - 1 + k; };
-
-    const HS hs(x, rank, Y0, L.Ly);
+    const int rank = (int)cluster.block_rank();  // == blockIdx.y % CY for cluster dims (1, CY, 1)
+    const MarchPlan<CY> plan(L, zchunk, alt);
 
     const unsigned ring_s = smem_u32(ring);
     const unsigned mbar_s = smem_u32(mbar);
-    // Where this CTA's own row goes in the neighbours' rings, and where its
-    // outer-halo node goes in the edge CTA's ring (cluster addresses).
+    // Where this CTA's own row goes in the neighbours' rings (cluster addresses).
     const unsigned below_ring = rank > 0 ? cluster_addr(ring_s, rank - 1) : 0u;  // their row +1
     const unsigned below_mbar = rank > 0 ? cluster_addr(mbar_s, rank - 1) : 0u;
     const unsigned above_ring = rank < CY - 1 ? cluster_addr(ring_s, rank + 1) : 0u;  // their row -1
     const unsigned above_mbar = rank < CY - 1 ? cluster_addr(mbar_s, rank + 1) : 0u;
-    const unsigned halo_ring = cluster_addr(ring_s, hs.rank);
-    const unsigned halo_mbar = cluster_addr(mbar_s, hs.rank);
 
     // staged variant: plane images and their mbarriers (one arrival, by
     // lane 0 of warp 0, plus the bytes of the copies)
@@ -875,178 +929,220 @@ __global__ void __launch_bounds__(TX, MINB)
     }
     cluster.sync();  // barriers initialised before any remote store arrives
 
-    const char* nbase = IO::base(src, x, y);
-    const char* hbase;
-    if constexpr (DEV) hbase = IO::base(src, hs.col, hs.in ? hs.y : 0);
-    else hbase = IO::base_c(src, hs.col, hs.in ? hs.y : 0, hs.comp);
+    // L2 policies: the direct variant's first read of a plane keeps its lines
+    // (evict_last) for the second read one plane later; the outer-halo rows
+    // are read once here (their owner reads them too), so they do not claim
+    // that priority.
+    unsigned long long keep, once;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
+#if LBM_ROWS_HALO_POLICY == 1
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(once));
+#elif LBM_ROWS_HALO_POLICY == 2
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(once));
+#else
+    once = keep;
+#endif
     auto planes = [&](const char* b, int p, int col) {
         if constexpr (DEV) return IO::planes(b, L, p, col);
         else return IO::planes(b, L, p);
     };
-    unsigned long long keep;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
-
-    // Staged variant: march plane k lives in stage k mod NST.  Warp 0 fills a
-    // stage (lane 0 arms its mbarrier with the bytes to come, then every
-    // lane issues its population rows); every thread waits on the stage's
-    // mbarrier (bounded) before it reads the plane.  Only the planes this
-    // chunk reads and that lie in the box are copied.
-    auto plane_wanted = [&](int k) {
-        const int p = plane_of(k);
-        return k <= n + 1 && p >= 0 && p < L.Lz;
-    };
-    unsigned sphase = 0u;   // bit s: parity of stage s's next completion (every thread)
-    unsigned pending = 0u;  // lane 0 of warp 0: stages with copies it has not seen complete
-    auto fill = [&](int k) {  // warp 0
-        if (!plane_wanted(k)) return;
-        const int st = k % NST;
-        if (x == 0) {
-            mbar_expect_tx(smbar_s + 8u * st, SP::BYTES);
-            pending |= 1u << st;
-        }
-        __syncwarp();
-        SP::issue(src, L, y, plane_of(k), stage_s + (unsigned)(st * SP::SMEM), smbar_s + 8u * st, x);
-    };
-    auto stage_wait = [&](int k) {
-        const int st = k % NST;
-        const unsigned par = (sphase >> st) & 1u;
-        if (wait_bounded(smbar_s + 8u * st, par, false, kWaitNs)) pending &= ~(1u << st);
-        else atomicOr(d_err, 4);
-        sphase ^= 1u << st;
-    };
-    auto stage_ptr = [&](int k) { return stage + (size_t)(k % NST) * (SP::SMEM / 4); };
-    if constexpr (STAGED) {
-        if (x < 32) {
-            fill(0);
-            fill(1);
-        }
-    }
-
-    // Post-streaming densities of march plane k: the own node into row 0 of
-    // this CTA's ring and into the neighbours' rows -1 / +1; the outer-halo
-    // share into the edge CTA's ring.  Ghost densities outside the box.
-    // Every CTA then expects TX_BYTES on its slot barrier.  The staged
-    // variant also keeps the node's pulled populations in `carry`.
-    auto densities = [&](int k, typename SP::Raw* carry) {
-        const int p = plane_of(k);
-        const int sl = k & (S - 1);
-        const bool in = p >= 0 && p < L.Lz;
-        float ra = m.rho_b[0], rb = m.rho_b[1];
-        // the outer-halo loads first, so that their latency overlaps the rest
-        float hv = 0.f, ha = m.rho_b[0], hb = m.rho_b[1];
-        if (hs.cta && in && hs.in) {
-            if constexpr (DEV) {
-                if (hs.thr) IO::densities(planes(hbase, p, hs.col), keep, ha, hb);
-            } else {
-                hv = IO::template density<0>(planes(hbase, p, 0), keep);
-            }
-        }
-        if (in) {
-            if constexpr (STAGED) {
-                stage_wait(k);
-                SP::load(stage_ptr(k), x, *carry, ra, rb);
-            } else {
-                IO::densities(planes(nbase, p, x), keep, ra, rb);
-            }
-        }
-        ring[sl * FL::SLOT + RW + x + 1] = make_float2(ra, rb);
-        const unsigned col = 8u * (unsigned)(sl * FL::SLOT + x + 1);  // row -1 of the slot, this column
-        const unsigned mb = 8u * sl;
-        if (rank > 0) st_async_f2(below_ring + col + 16u * RW, ra, rb, below_mbar + mb);
-        if (rank < CY - 1) st_async_f2(above_ring + col, ra, rb, above_mbar + mb);
-        if (hs.cta) {
-            const unsigned hoff = 8u * (unsigned)(sl * FL::SLOT + (hs.row + 1) * RW + hs.col + 1);
-            if constexpr (DEV) {
-                if (hs.thr) st_async_f2(halo_ring + hoff, ha, hb, halo_mbar + mb);
-            } else {
-                const float v = in && hs.in ? hv : m.rho_b[hs.comp];
-                const float other = __shfl_xor_sync(0xffffffffu, v, 1);
-                if (hs.thr) st_async_f2(halo_ring + hoff, v, other, halo_mbar + mb);
-            }
-        }
-        if (x == 0) mbar_expect_tx(mbar_s + mb, FL::TX_BYTES);
-    };
-    // Wait (bounded) until the neighbour rows of march plane k have landed.
-    auto wait_rows = [&](int k) {
-        const unsigned par = (unsigned)(k / S) & 1u;
-        if (!wait_bounded(mbar_s + 8u * (k & (S - 1)), par, true, kWaitNs)) atomicOr(d_err, 4);
-    };
 
     float cm[4] = {0.f, 0.f, 0.f, 0.f};
     int bad = 0;
-    const float px = (float)x - 0.5f * (float)(L.Lx - 1), py = (float)y - 0.5f * (float)(L.Ly - 1);
-    auto collide = [&](int k, const float (&f)[2][19]) {
-        const int z = plane_of(k);
-        const float2* rprev = ring + ((k - 1) & (S - 1)) * FL::SLOT + x + 1;
-        const float2* rcur = ring + (k & (S - 1)) * FL::SLOT + x + 1;
-        const float2* rnext = ring + ((k + 1) & (S - 1)) * FL::SLOT + x + 1;
-        collide_node<TX, ST, MRT>(down ? rnext : rprev, rcur, down ? rprev : rnext, f, m, IO::out(dst, L, x, y, z),
-                                  cm, bad, px, py, (float)z - 0.5f * (float)(L.Lz - 1));
-    };
+    const float px = (float)x - 0.5f * (float)(L.Lx - 1);
+    unsigned sphase = 0u;   // bit s: parity of stage s's next completion (every thread)
+    unsigned pending = 0u;  // lane 0 of warp 0: stages with copies it has not seen complete
 
-    if constexpr (STAGED) {
-        // Planes k + 1 .. k + 3 are in the stages or in flight while plane k
-        // is collided from the registers its density pass filled.
-        typename SP::Raw cur, nxt;
-        densities(0, &nxt);
-        __syncthreads();  // march plane 0 read by all: its stage takes plane 2
-        if (x < 32) {
-            fence_proxy_async();
-            fill(2);
-        }
-        densities(1, &cur);
-        __syncthreads();
-        if (x < 32) {
-            fence_proxy_async();
-            fill(3);
-        }
-        wait_rows(0);
-        wait_rows(1);
-        // one march step: the density pass of plane k + 1 into `next`, the
-        // collision of plane k from `now`
-        auto step = [&](int k, const typename SP::Raw& now, typename SP::Raw& next) {
-            densities(k + 1, &next);
-            __syncthreads();  // own row of plane k + 1 complete; its stage read by all
+    // March plane K (counted over all segments of the CTA) uses ring slot
+    // K mod S, whose barrier's wait parity is (K / S) mod 2, and stage K mod 2.
+    int K0 = 0;
+    for (int j = 0; j < plan.nseg; ++j) {
+        const Segment sg = plan.seg(j);
+        const int y = sg.g * CY + rank;
+        const int Y0 = sg.g * CY;
+        const int zc0 = sg.z0, zc1 = sg.z1;
+        const int n = zc1 - zc0;
+        const bool down = sg.down;
+        // k-th plane of the segment's march (k = 0 and n + 1 are the halo planes)
+        auto plane_of = [&](int k) { return down ? zc1 - k : zc0 - 1 + k; };
+        const HS hs(x, rank, Y0, L.Ly);
+        const unsigned halo_ring = cluster_addr(ring_s, hs.rank);
+        const unsigned halo_mbar = cluster_addr(mbar_s, hs.rank);
+        const char* nbase = IO::base(src, x, y);
+        const char* hbase;
+        if constexpr (DEV) hbase = IO::base(src, hs.col, hs.in ? hs.y : 0);
+        else hbase = IO::base_c(src, hs.col, hs.in ? hs.y : 0, hs.comp);
+        const float py = (float)y - 0.5f * (float)(L.Ly - 1);
+
+        // Staged variant: warp 0 fills a stage (lane 0 arms its mbarrier with
+        // the bytes to come, then every lane issues its population rows); every
+        // thread waits on the stage's mbarrier (bounded) before it reads the
+        // plane.  Only the planes this segment reads and that lie in the box
+        // are copied.
+        auto plane_wanted = [&](int k) {
+            const int p = plane_of(k);
+            return k <= n + 1 && p >= 0 && p < L.Lz;
+        };
+        // plane k + LBM_ROWS_L2_AHEAD into L2 (warp 0), so that its copy
+        // into a stage, issued that many march steps later, is served by L2
+        auto prefetch = [&](int k) {
+            if constexpr (LBM_ROWS_L2_AHEAD > 0)
+                if (plane_wanted(k)) SP::prefetch(src, L, y, plane_of(k), x);
+        };
+        auto fill = [&](int k) {  // warp 0
+            prefetch(k + LBM_ROWS_L2_AHEAD);
+            if (!plane_wanted(k)) return;
+            const int st = (K0 + k) % NST;
+            if (x == 0) {
+                mbar_expect_tx(smbar_s + 8u * st, SP::BYTES);
+                pending |= 1u << st;
+            }
+            __syncwarp();
+            SP::issue(src, L, y, plane_of(k), stage_s + (unsigned)(st * SP::SMEM), smbar_s + 8u * st, x);
+        };
+        auto stage_wait = [&](int k) {
+            const int st = (K0 + k) % NST;
+            const unsigned par = (sphase >> st) & 1u;
+            if (wait_bounded(smbar_s + 8u * st, par, false, kWaitNs)) pending &= ~(1u << st);
+            else atomicOr(d_err, 4);
+            sphase ^= 1u << st;
+        };
+        auto stage_ptr = [&](int k) { return stage + (size_t)((K0 + k) % NST) * (SP::SMEM / 4); };
+
+        // Post-streaming densities of march plane k: the own node into row 0
+        // of this CTA's ring and into the neighbours' rows -1 / +1; the
+        // outer-halo share into the edge CTA's ring.  Ghost densities outside
+        // the box.  Every CTA then expects TX_BYTES on its slot barrier.  The
+        // staged variant also keeps the node's pulled populations in `carry`.
+        auto densities = [&](int k, typename SP::Raw* carry) {
+            const int p = plane_of(k);
+            const int sl = (K0 + k) & (S - 1);
+            const bool in = p >= 0 && p < L.Lz;
+            float ra = m.rho_b[0], rb = m.rho_b[1];
+            // the outer-halo loads first, so that their latency overlaps the rest
+            float hv = 0.f, ha = m.rho_b[0], hb = m.rho_b[1];
+            if (hs.cta && in && hs.in) {
+                if constexpr (DEV) {
+                    if (hs.thr) IO::densities(planes(hbase, p, hs.col), once, ha, hb);
+                } else {
+                    hv = IO::template density<0>(planes(hbase, p, 0), once);
+                }
+            }
+            if (in) {
+                if constexpr (STAGED) {
+                    stage_wait(k);
+                    SP::load(stage_ptr(k), x, *carry, ra, rb);
+                } else {
+                    IO::densities(planes(nbase, p, x), keep, ra, rb);
+                }
+            }
+            ring[sl * FL::SLOT + RW + x + 1] = make_float2(ra, rb);
+            const unsigned col = 8u * (unsigned)(sl * FL::SLOT + x + 1);  // row -1 of the slot, this column
+            const unsigned mb = 8u * sl;
+            if (rank > 0) st_async_f2(below_ring + col + 16u * RW, ra, rb, below_mbar + mb);
+            if (rank < CY - 1) st_async_f2(above_ring + col, ra, rb, above_mbar + mb);
+            if (hs.cta) {
+                const unsigned hoff = 8u * (unsigned)(sl * FL::SLOT + (hs.row + 1) * RW + hs.col + 1);
+                if constexpr (DEV) {
+                    if (hs.thr) st_async_f2(halo_ring + hoff, ha, hb, halo_mbar + mb);
+                } else {
+                    const float v = in && hs.in ? hv : m.rho_b[hs.comp];
+                    const float other = __shfl_xor_sync(0xffffffffu, v, 1);
+                    if (hs.thr) st_async_f2(halo_ring + hoff, v, other, halo_mbar + mb);
+                }
+            }
+            if (x == 0) mbar_expect_tx(mbar_s + mb, FL::TX_BYTES);
+        };
+        // Wait (bounded) until the neighbour rows of march plane k have landed.
+        auto wait_rows = [&](int k) {
+            const unsigned par = (unsigned)((K0 + k) / S) & 1u;
+            if (!wait_bounded(mbar_s + 8u * ((K0 + k) & (S - 1)), par, true, kWaitNs)) atomicOr(d_err, 4);
+        };
+        auto collide = [&](int k, const float (&f)[2][19]) {
+            const int z = plane_of(k);
+            const float2* rprev = ring + ((K0 + k - 1) & (S - 1)) * FL::SLOT + x + 1;
+            const float2* rcur = ring + ((K0 + k) & (S - 1)) * FL::SLOT + x + 1;
+            const float2* rnext = ring + ((K0 + k + 1) & (S - 1)) * FL::SLOT + x + 1;
+            collide_node<TX, ST, MRT>(down ? rnext : rprev, rcur, down ? rprev : rnext, f, m,
+                                      IO::out(dst, L, x, y, z), cm, bad, px, py, (float)z - 0.5f * (float)(L.Lz - 1));
+        };
+
+        // The segment starts as every later march step does: a CTA pushes
+        // plane k only after its wait for plane k - 1 (the ring argument of
+        // FastLayout), and the first collision follows the __syncthreads of
+        // the step that pushes plane 2.
+        if constexpr (STAGED) {
+            // Planes k + 1 .. k + 3 are in the stages or in flight while plane
+            // k is collided from the registers its density pass filled.
+            typename SP::Raw cur, nxt;
+            if (x < 32) {
+                fence_proxy_async();  // a previous segment read the stages
+                for (int k = 2; k < LBM_ROWS_L2_AHEAD; ++k) prefetch(k);
+                fill(0);
+                fill(1);
+            }
+            densities(0, &nxt);
+            __syncthreads();  // march plane 0 read by all: its stage takes plane 2
             if (x < 32) {
                 fence_proxy_async();
-                fill(k + 3);
+                fill(2);
             }
-            wait_rows(k + 1);
-            float f[2][19];
-            SP::unpack(now, f);
-            collide(k, f);
-        };
-        if constexpr (DEV) {
-            for (int k = 1; k <= n; ++k) {
-                step(k, cur, nxt);
-                cur = nxt;
+            wait_rows(0);
+            densities(1, &cur);
+            __syncthreads();
+            if (x < 32) {
+                fence_proxy_async();
+                fill(3);
+            }
+            wait_rows(1);
+            // one march step: the density pass of plane k + 1 into `next`,
+            // the collision of plane k from `now`
+            auto step = [&](int k, const typename SP::Raw& now, typename SP::Raw& next) {
+                densities(k + 1, &next);
+                __syncthreads();  // own row of plane k + 1 complete; its stage read by all
+                if (x < 32) {
+                    fence_proxy_async();
+                    fill(k + 3);
+                }
+                wait_rows(k + 1);
+                float f[2][19];
+                SP::unpack(now, f);
+                collide(k, f);
+            };
+            if constexpr (DEV) {
+                for (int k = 1; k <= n; ++k) {
+                    step(k, cur, nxt);
+                    cur = nxt;
+                }
+            } else {
+                // two steps per trip, so that the carried registers swap
+                // roles instead of being copied
+                for (int k = 1; k <= n; k += 2) {
+                    step(k, cur, nxt);
+                    if (k + 1 <= n) step(k + 1, nxt, cur);
+                }
             }
         } else {
-            // two steps per trip, so that the carried registers swap roles
-            // instead of being copied
-            for (int k = 1; k <= n; k += 2) {
-                step(k, cur, nxt);
-                if (k + 1 <= n) step(k + 1, nxt, cur);
+            densities(0, nullptr);
+            wait_rows(0);
+            densities(1, nullptr);
+            wait_rows(1);
+            for (int k = 1; k <= n; ++k) {
+                densities(k + 1, nullptr);
+                // this node's populations for the collision, read while the
+                // neighbour rows of plane k + 1 are in flight
+                float f[2][19];
+                IO::populations(planes(nbase, plane_of(k), x), f);
+                __syncthreads();  // own row of plane k + 1 complete
+                wait_rows(k + 1);
+                collide(k, f);
+                // Before a later plane reuses this plane's own-row slot, all
+                // threads must be done reading it: the __syncthreads of the
+                // next iterations (S - 1 march planes apart) order that.
             }
         }
-    } else {
-        densities(0, nullptr);
-        densities(1, nullptr);
-        wait_rows(0);
-        wait_rows(1);
-        for (int k = 1; k <= n; ++k) {
-            densities(k + 1, nullptr);
-            // this node's populations for the collision, read while the
-            // neighbour rows of plane k + 1 are in flight
-            float f[2][19];
-            IO::populations(planes(nbase, plane_of(k), x), f);
-            __syncthreads();  // own row of plane k + 1 complete
-            wait_rows(k + 1);
-            collide(k, f);
-            // Before a later plane reuses this plane's own-row slot, all
-            // threads must be done reading it: the __syncthreads of the next
-            // iterations (S - 1 march planes apart) order that.
-        }
+        __syncthreads();  // the last plane's ring row and stage read by all before the next segment
+        K0 += n + 2;
     }
     if (bad) atomicOr(d_err, bad);
     // staged variant: copies whose completion lane 0 of warp 0 did not observe
@@ -1323,7 +1419,7 @@ int max_clusters() {
     return n;
 }
 
-constexpr int kRowCluster = 8;
+constexpr int kRowCluster = kRowClusterRows;
 
 template <int TX, typename S, bool STAGED, bool MRT = false>
 cudaError_t rows_for(bool query, const void* src, void* dst, const Layout& L, const Model& m, int zchunk,

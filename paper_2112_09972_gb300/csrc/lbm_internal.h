@@ -105,6 +105,9 @@ struct Shape {
     size_t smem;
 };
 
+// Rows per thread-block cluster of the row kernels (lbm_fast.cu).
+constexpr int kRowClusterRows = 8;
+
 // Variants of the row kernel: per-thread loads of the pulled populations
 // (each plane read twice, the second time from L2), whole pulled rows staged
 // in shared memory by bulk copies, or loader and collider threads per row

@@ -29,7 +29,7 @@ ABI_FUNCTIONS = [
     "lbm_opts_default", "lbm_create", "lbm_set_gradient", "lbm_set_gradient_table", "lbm_step", "lbm_sync",
     "lbm_deformation", "lbm_moments", "lbm_get_fields", "lbm_get_populations", "lbm_set_populations",
     "lbm_checksums", "lbm_get_step", "lbm_save", "lbm_load", "lbm_profile_enable", "lbm_profile_read",
-    "lbm_launch_shape", "lbm_destroy", "lbm_strerror", "lbm_moments_static",
+    "lbm_launch_shape", "lbm_launch_variant", "lbm_destroy", "lbm_strerror", "lbm_moments_static",
     "lbm_batch_create", "lbm_batch_set_gradients", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_deformation",
     "lbm_batch_get_populations", "lbm_batch_set_populations", "lbm_batch_autotune", "lbm_batch_shape",
     "lbm_batch_destroy", "lbm_batch_moments",
@@ -101,6 +101,7 @@ def load_library(path=LIB_PATH):
         "lbm_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_profile_read": (ctypes.c_int, [vp, ctypes.c_int, _DP, _I64P]),
         "lbm_launch_shape": (ctypes.c_int, [vp, _I32P, _I32P, _I32P]),
+        "lbm_launch_variant": (ctypes.c_int, [vp, _I32P]),
         "lbm_destroy": (None, [vp]),
         "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "lbm_moments_static": (ctypes.c_int, [vp, ctypes.c_int32, _I32P, vp, vp]),
@@ -345,6 +346,12 @@ class DropletLBM:
         _check(self._lib.lbm_launch_shape(self._h, ctypes.byref(ty), ctypes.byref(zc), ctypes.byref(ctas)),
                "lbm_launch_shape")
         return ty.value, zc.value, ctas.value
+
+    def launch_variant(self):
+        """0: the generic tile kernel; 1, 2, 3: the row kernel's variant (lbm_opts.row_variant)."""
+        v = ctypes.c_int32()
+        _check(self._lib.lbm_launch_variant(self._h, ctypes.byref(v)), "lbm_launch_variant")
+        return v.value
 
 
 class BatchLBM:

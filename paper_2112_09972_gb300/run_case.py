@@ -30,6 +30,7 @@ def main(argv=None):
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--tile-y", type=int, default=0)
     p.add_argument("--z-chunk", type=int, default=0)
+    p.add_argument("--row-variant", type=int, default=0, help="row kernel: 1 direct loads, 2 staged, 3 warp-specialised")
     p.add_argument("--mlp-batch", type=int, default=0)
     p.add_argument("--tensor-path", type=int, default=0, help="MLP products: 0 tcgen05 where possible, 1 mma.sync")
     a = p.parse_args(argv)
@@ -39,13 +40,14 @@ def main(argv=None):
     build.build()
     prec = a.precision or w.precision
     g = DropletLBM((w.box,) * 3, w.R, w.visc, w.G, precision=prec, rho_hi=w.rho_hi, rho_lo=w.rho_lo, xi=w.xi,
-                   tile_y=a.tile_y, z_chunk=a.z_chunk)
+                   tile_y=a.tile_y, z_chunk=a.z_chunk, row_variant=a.row_variant)
     hist = w.gradient_history(max(a.steps, 1))
     g.set_gradient_table(np.arange(hist.shape[0]), hist)
     g.step(a.steps)
     D = g.deformation()[0]
     ty, zc, ctas = g.launch_shape()
-    print(f"{w.name} {prec}: {a.steps} steps, D = {D:.6f}, launch shape tile_y={ty} z_chunk={zc} ctas={ctas}")
+    print(f"{w.name} {prec}: {a.steps} steps, D = {D:.6f}, launch shape tile_y={ty} z_chunk={zc} ctas={ctas} "
+          f"variant={g.launch_variant()}")
 
 
 def run_mlp(n, steps, path):

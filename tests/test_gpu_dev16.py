@@ -253,6 +253,46 @@ def test_full_size_256_against_fp32(built, downscaled_model_error, storage):
     assert abs(b[3] - a[3]) <= 1e-3 * abs(a[3]) + 1e-6
 
 
+@pytest.fixture(scope="module")
+def downscale_oracle(oracle_mod):
+    """The 64^3, R = 8 downscale of the precision case (its gradient history
+    rescaled to the box) on the FP64 oracle: 400 steps from the tanh droplet."""
+    from oracle.observables import deformation_from_moments
+
+    w = workloads.C4_DOWNSCALED
+    box = (w.box,) * 3
+    hist = w.gradient_history(401)
+    o = oracle_mod.OracleLBM(box, (w.tau, w.tau), w.G, (w.rho_lo, w.rho_hi))
+    o.init_droplet(w.R, w.xi, w.rho_hi, w.rho_lo, hist[0])
+    o.run(400, np.arange(401), hist)
+    D, axes, _, _ = deformation_from_moments(o.moments())
+    return dict(hist=hist, fields=o.fields(), D=D, axes=axes)
+
+
+@pytest.mark.parametrize("storage,tol_field,tol_D", [("fp32", 1e-4, 1e-3), ("fp16dev", 2e-3, 1e-3),
+                                                     ("bf16dev", 1.5e-2, 1e-2)])
+def test_precision_downscale_against_fp64_oracle(built, downscale_oracle, storage, tol_field, tol_D):
+    """Every storage form of the precision case against the FP64 oracle on its
+    64^3 downscale after 400 steps (the comparison the benchmark's precision
+    leg reports): densities and velocity element by element (relative L-inf),
+    and D.  binary16 keeps 11 significant bits of each deviation, bfloat16 8:
+    the bfloat16 tolerances are 2^3 times wider."""
+    w = workloads.C4_DOWNSCALED
+    box = (w.box,) * 3
+    ref = downscale_oracle
+    g = DropletLBM(box, w.R, w.visc, w.G, precision=storage, rho_hi=w.rho_hi, rho_lo=w.rho_lo, xi=w.xi)
+    g.set_gradient_table(np.arange(401), ref["hist"])
+    g.step(400)
+    ra, rb, u = g.fields()
+    D, axes, _, _ = g.deformation()
+    g.close()
+    ora, orb, ou = ref["fields"]
+    errs = (rel_linf(ra, ora), rel_linf(rb, orb), rel_linf(u, ou))
+    assert errs[0] <= tol_field and errs[1] <= tol_field and errs[2] <= 10 * tol_field, errs
+    rel_D = abs(D - ref["D"]) / abs(ref["D"])
+    assert rel_D <= tol_D, rel_D
+
+
 def test_fp32_256_wide_against_oracle(built, oracle_mod):
     box = (256, 16, 12)
     f0, A = _perturbed(oracle_mod, box, 4.0, False, seed=12)

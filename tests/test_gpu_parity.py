@@ -102,6 +102,34 @@ def test_ragged_box_short_run(built, oracle_mod, precision, tol, periodic):
     assert rel_linf(ra, ora) <= tol and rel_linf(rb, orb) <= tol and rel_linf(u, ou) <= 10 * tol
 
 
+def test_throughput_case_200_steps_benchmark_launch(built, oracle_mod):
+    """The benchmark's own launch -- 128^3, R = 16, fp32, the OU history of the
+    throughput case, automatic kernel variant and launch shape (the instance
+    bench.py times) -- against the FP64 oracle after 200 steps from the
+    same initial state: every stored population, element by element, within
+    1e-4 of the largest population, and D within 1e-3.  The run spans every
+    CTA of the launch, every march direction and the ghost shell on all six
+    faces."""
+    from oracle.observables import deformation_from_moments
+
+    w = workloads.C2_THROUGHPUT
+    box = (w.box,) * 3
+    steps = 200
+    hist = w.gradient_history(steps + 1)
+    o = oracle_mod.OracleLBM(box, (w.tau, w.tau), w.G, (w.rho_lo, w.rho_hi))
+    o.init_droplet(w.R, w.xi, w.rho_hi, w.rho_lo, hist[0])
+    g = DropletLBM(box, w.R, w.visc, w.G, precision=w.precision, rho_hi=w.rho_hi, rho_lo=w.rho_lo, xi=w.xi)
+    g.set_populations(o.populations())
+    g.set_gradient_table(np.arange(steps + 1), hist)
+    g.step(steps)
+    o.run(steps, np.arange(steps + 1), hist)
+    ref = o.populations()
+    assert rel_linf(g.populations(), ref) <= 1e-4
+    D_ref = deformation_from_moments(o.moments())[0]
+    D = g.deformation()[0]
+    assert abs(D - D_ref) <= 1e-3 * abs(D_ref) + 1e-6
+
+
 def test_interpolated_gradient_knots(built, oracle_mod):
     """Knots every 7 steps, linear interpolation between them (fp64)."""
     box = (12, 14, 10)

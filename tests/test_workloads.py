@@ -47,3 +47,22 @@ def test_ou_final_windows():
     a, b = H[:-1].reshape(-1), H[1:].reshape(-1)
     rho = float(np.sum(a * b) / np.sqrt(np.sum(a * a) * np.sum(b * b)))
     assert abs(rho - np.exp(-1.0 / T)) <= 3e-3
+
+
+def test_capillary_driven_histories():
+    """Config 2 as stated: OU gradients scaled so that rms ||A||_F tau_eta = 1,
+    tau_eta = eta_s R / (sigma Ca_rms) (Eq. 3).  Over 256 independent boxes the
+    mean of ||A(t)||_F^2 tau_eta^2 is 1 at every sampled time (the OU
+    processes start from their stationary law), so the stated Ca_rms holds;
+    the ghost speed those amplitudes imply at L/R = 8 is recorded against the
+    Mach limit of Sec. 4."""
+    for ca, w in workloads.C2_CA.items():
+        assert abs(w.eta_s * w.R / (workloads.SIGMA * w.tau_eta) - ca) < 1e-15
+        hs = np.stack([w.gradient_history(400, box_id=b) for b in range(256)])  # [box, t, 9]
+        assert np.max(np.abs(hs[..., 0] + hs[..., 4] + hs[..., 8])) < 1e-15
+        F2 = np.sum(hs * hs, axis=2) * w.tau_eta ** 2
+        assert np.all(np.abs(F2[:, [0, 199, 399]].mean(axis=0) - 1.0) < 0.12)
+        assert abs(w.frobenius_ca_rms(hs.reshape(-1, 9)) / ca - 1.0) < 0.05
+        # the boundary speed scale: far above the Mach limit at every swept Ca
+        u = w.boundary_speed(hs[0])
+        assert np.median(u) > 0.2
