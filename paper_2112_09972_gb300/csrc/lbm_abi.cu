@@ -291,11 +291,13 @@ int lbm_create(lbm_ctx** out, const int32_t box[3], double R, const double visc[
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_partials, sizeof(double) * 10 * c->red_blocks);
     c->centre.n = (int)(c->shape.grid.x * c->shape.grid.y * c->shape.grid.z);
-    const size_t centre_bytes = sizeof(double) * (4 * (size_t)c->centre.n + 8) + 16;
+    // partials, the 8 sums, the counter (16 bytes), the float32 frame origin (16 bytes)
+    const size_t centre_bytes = sizeof(double) * (4 * (size_t)c->centre.n + 8) + 32;
     if (e == cudaSuccess) e = cudaMalloc(&c->centre.p, centre_bytes);
     if (e == cudaSuccess) {
         c->centre.sum = c->centre.p + 4 * c->centre.n;
         c->centre.counter = (unsigned*)(c->centre.sum + 8);
+        c->centre.frame = (float*)(c->centre.sum + 10);
         e = cudaMemsetAsync(c->centre.p, 0, centre_bytes, c->stream);
     }
     if (e == cudaSuccess) e = cudaMalloc(&c->d_result, sizeof(double) * 32);
@@ -706,9 +708,14 @@ int lbm_load(lbm_ctx* c, const char* path) {
     }
     // restore the saved frame origin partials when the launch shape matches
     // (otherwise the ones just recomputed from the populations stay)
-    if (h.ncentre == c->centre.n)
+    float fr[3];  // the frame origin's float32 copy, as the reduction writes it (alive until the sync below)
+    if (h.ncentre == c->centre.n) {
         LBM_TRY(cudaMemcpyAsync(c->centre.p, cparts.data(), sizeof(double) * cparts.size(), cudaMemcpyHostToDevice,
                                 c->stream));
+        const size_t o = (size_t)4 * c->centre.n + 4;
+        for (int q = 0; q < 3; ++q) fr[q] = (float)cparts[o + q];
+        LBM_TRY(cudaMemcpyAsync(c->centre.frame, fr, sizeof(fr), cudaMemcpyHostToDevice, c->stream));
+    }
     c->step = h.step;
     LBM_TRY(cudaStreamSynchronize(c->stream));
     return LBM_OK;

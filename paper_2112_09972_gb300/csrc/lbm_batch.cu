@@ -55,43 +55,44 @@ constexpr int kBatchThreads = 256;
 // ---- kernels ----------------------------------------------------------------
 
 __global__ void __launch_bounds__(256)
-    k_batch_ghost(const BatchBox* __restrict__ boxes, int parity, Model m, const float* __restrict__ A_table,
-                  long long table_steps, int nbox, const double* __restrict__ box_sums,
+    k_batch_ghost(const BatchBox* __restrict__ boxes, int parity, GhostParams<float> g, const float* __restrict__ A_table,
+                  long long table_steps, int nbox, const float* __restrict__ box_frame,
                   const long long* __restrict__ d_step, int* __restrict__ d_err) {
     const int box = blockIdx.z / 6, face = blockIdx.z % 6;
     const BatchBox b = boxes[box];
+    // x faces: two threads per node, each writing half of every padding sector
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int half = face < 2 ? (a & 1) : -1;
     int x, y, z;
-    if (!shell_node(b.L, face, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y, x, y,
-                    z))
-        return;
+    if (!shell_node(b.L, face, face < 2 ? a >> 1 : a, blockIdx.y * blockDim.y + threadIdx.y, x, y, z)) return;
     long long step = *d_step;
     if (step >= table_steps) step = table_steps - 1;
-    float A[9];
     if (table_steps > 0) {
         const float* a = A_table + (step * nbox + box) * 9;
 #pragma unroll
-        for (int j = 0; j < 9; ++j) A[j] = a[j];
+        for (int j = 0; j < 9; ++j) g.A[j] = a[j];
     } else {
 #pragma unroll
-        for (int j = 0; j < 9; ++j) A[j] = 0.f;
+        for (int j = 0; j < 9; ++j) g.A[j] = 0.f;
     }
     float xc = 0.f, yc = 0.f, zc = 0.f;
-    if (m.droplet_frame) {
-        xc = (float)box_sums[8 * box + 4];
-        yc = (float)box_sums[8 * box + 5];
-        zc = (float)box_sums[8 * box + 6];
+    if (g.frame) {
+        xc = box_frame[4 * box + 0];
+        yc = box_frame[4 * box + 1];
+        zc = box_frame[4 * box + 2];
     }
-    ghost_node<float, float>(b.f[parity], b.L, m, A, xc, yc, zc, x, y, z, d_err);
+    ghost_node<float, float>(b.f[parity], b.L, g, xc, yc, zc, x, y, z, half, d_err);
 }
 
 __global__ void __launch_bounds__(kBatchThreads)
     k_batch_stream_collide(const BatchBox* __restrict__ boxes, const BatchItem* __restrict__ items, int nitems,
                            const int* __restrict__ box_first, const int* __restrict__ box_nitems, int parity,
-                           ModelC<float> m, double* __restrict__ item_parts, double* __restrict__ box_sums,
-                           unsigned* __restrict__ box_done, unsigned* __restrict__ ctas_done,
+                           ModelC<float> m, float* __restrict__ item_parts, double* __restrict__ box_sums,
+                           float* __restrict__ box_frame, unsigned* __restrict__ box_done, unsigned* __restrict__ ctas_done,
                            long long* __restrict__ d_step, int* __restrict__ d_err) {
     extern __shared__ __align__(16) float ring[];
-    __shared__ double red[4 * (kBatchThreads / 32)];
+    // (float32 reductions: this GPU's FP64 pipe runs at 1/64 of the float32 rate)
+    __shared__ float red[4 * (kBatchThreads / 32)];
     __shared__ unsigned last_item, last_cta;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(kBatchThreads)
         // per-item partial sums of the droplet moments (fixed order)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            double a = (double)cm[q];
+            float a = cm[q];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
             if (lane == 0) red[4 * warp + q] = a;
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kBatchThreads)
         if (warp == 0) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                double a = lane < kBatchThreads / 32 ? red[4 * lane + q] : 0.0;
+                float a = lane < kBatchThreads / 32 ? red[4 * lane + q] : 0.f;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
                 if (lane == 0) item_parts[4LL * it + q] = a;
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(kBatchThreads)
             // the box's frame origin: its items' partials summed in item order
             __threadfence();
             const int first = box_first[w.box], n = box_nitems[w.box];
-            double s4[4] = {0.0, 0.0, 0.0, 0.0};
+            float s4[4] = {0.f, 0.f, 0.f, 0.f};
             for (int k = lane; k < n; k += 32)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) s4[q] += __ldcg(item_parts + 4LL * (first + k) + q);
@@ -138,9 +139,13 @@ __global__ void __launch_bounds__(kBatchThreads)
             if (lane == 0) {
                 double* bs = box_sums + 8LL * w.box;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) bs[q] = s4[q];
-                const bool have = s4[0] > 0.0;
-                for (int q = 0; q < 3; ++q) bs[4 + q] = have ? s4[1 + q] / s4[0] : 0.0;
+                for (int q = 0; q < 4; ++q) bs[q] = (double)s4[q];
+                const bool have = s4[0] > 0.f;
+                for (int q = 0; q < 3; ++q) {
+                    const float xc = have ? s4[1 + q] / s4[0] : 0.f;
+                    bs[4 + q] = (double)xc;
+                    box_frame[4LL * w.box + q] = xc;
+                }
                 box_done[w.box] = 0u;
             }
         }
@@ -211,7 +216,7 @@ __global__ void __launch_bounds__(256) k_batch_moments(const BatchBox* __restric
 // Per box (blockIdx.x): moments, D, axes, eigenvalues, centre -> result[box][26];
 // optionally also the frame origin into box_sums.
 __global__ void k_batch_moments_final(const double* __restrict__ partials, int nblocks, double* __restrict__ result,
-                                      double* __restrict__ box_sums) {
+                                      double* __restrict__ box_sums, float* __restrict__ box_frame) {
     const int lane = threadIdx.x;
     const double* p = partials + 10LL * nblocks * blockIdx.x;
     double m[10];
@@ -230,7 +235,10 @@ __global__ void k_batch_moments_final(const double* __restrict__ partials, int n
         double* bs = box_sums + 8LL * blockIdx.x;
         for (int q = 0; q < 4; ++q) bs[q] = m[q];
         const bool have = m[0] > 0.0;
-        for (int q = 0; q < 3; ++q) bs[4 + q] = have ? m[1 + q] / m[0] : 0.0;
+        for (int q = 0; q < 3; ++q) {
+            bs[4 + q] = have ? m[1 + q] / m[0] : 0.0;
+            box_frame[4LL * blockIdx.x + q] = (float)bs[4 + q];
+        }
     }
 }
 
@@ -271,6 +279,7 @@ struct lbm_batch {
     int* d_box_nitems;
     double* d_item_parts;
     double* d_box_sums;   // [nbox][8]
+    float* d_box_frame;   // [nbox][4]: the frame origin in float32 (read by the ghost kernel)
     unsigned* d_box_done; // [nbox]
     unsigned* d_ctas_done;
     long long* d_step;
@@ -394,6 +403,8 @@ int lbm_batch_create(lbm_batch** out, int32_t nbox, const int32_t* boxes, const 
     if (e == cudaSuccess) e = cudaMemcpy(b->d_boxes, b->boxes.data(), sizeof(BatchBox) * nbox, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_box_sums, sizeof(double) * 8 * nbox);
     if (e == cudaSuccess) e = cudaMemset(b->d_box_sums, 0, sizeof(double) * 8 * nbox);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_box_frame, sizeof(float) * 4 * nbox);
+    if (e == cudaSuccess) e = cudaMemset(b->d_box_frame, 0, sizeof(float) * 4 * nbox);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_box_done, sizeof(unsigned) * nbox);
     if (e == cudaSuccess) e = cudaMemset(b->d_box_done, 0, sizeof(unsigned) * nbox);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_box_first, sizeof(int) * nbox);
@@ -435,6 +446,7 @@ void lbm_batch_destroy(lbm_batch* b) {
     cudaFree(b->d_box_nitems);
     cudaFree(b->d_item_parts);
     cudaFree(b->d_box_sums);
+    cudaFree(b->d_box_frame);
     cudaFree(b->d_box_done);
     cudaFree(b->d_ctas_done);
     cudaFree(b->d_step);
@@ -505,7 +517,8 @@ int batch_init(lbm_batch* b) {
     }
     // first frame origins from the initial populations
     k_batch_moments<<<dim3(b->mblocks, b->nbox), 256, 0, b->stream>>>(b->d_boxes, b->parity, b->d_mparts);
-    k_batch_moments_final<<<b->nbox, 32, 0, b->stream>>>(b->d_mparts, b->mblocks, b->d_result, b->d_box_sums);
+    k_batch_moments_final<<<b->nbox, 32, 0, b->stream>>>(b->d_mparts, b->mblocks, b->d_result, b->d_box_sums,
+                                                         b->d_box_frame);
     BATCH_TRY(cudaGetLastError());
     b->initialised = true;
     return LBM_OK;
@@ -514,13 +527,14 @@ int batch_init(lbm_batch* b) {
 cudaError_t enqueue_step(lbm_batch* b, int parity) {
     int fast = 0, slow = 0;
     for (const auto& bx : b->boxes) {
-        fast = std::max(fast, std::max(bx.L.Lx, bx.L.Ly + 2));
+        fast = std::max(fast, std::max(bx.L.Lx, 2 * (bx.L.Ly + 2)));  // x faces: two threads per node
         slow = std::max(slow, std::max(bx.L.Lz + 2, bx.L.Ly));
     }
     const dim3 gblock(32, 8, 1);
     const dim3 ggrid((fast + 31) / 32, (slow + 7) / 8, 6 * b->nbox);
-    k_batch_ghost<<<ggrid, gblock, 0, b->stream>>>(b->d_boxes, parity, b->model, b->d_A, b->A_steps, b->nbox,
-                                                   b->d_box_sums, b->d_step, b->d_err);
+    const double zero[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // A comes from the table
+    k_batch_ghost<<<ggrid, gblock, 0, b->stream>>>(b->d_boxes, parity, ghost_params<float>(b->model, zero), b->d_A,
+                                                   b->A_steps, b->nbox, b->d_box_frame, b->d_step, b->d_err);
     ModelC<float> mc;
     for (int s = 0; s < 2; ++s) {
         mc.tau[s] = (float)b->model.tau[s];
@@ -529,8 +543,9 @@ cudaError_t enqueue_step(lbm_batch* b, int parity) {
     }
     mc.G = (float)b->model.G;
     k_batch_stream_collide<<<b->grid, kBatchThreads, b->smem, b->stream>>>(
-        b->d_boxes, b->d_items, (int)b->items.size(), b->d_box_first, b->d_box_nitems, parity, mc, b->d_item_parts,
-        b->d_box_sums, b->d_box_done, b->d_ctas_done, b->d_step, b->d_err);
+        b->d_boxes, b->d_items, (int)b->items.size(), b->d_box_first, b->d_box_nitems, parity, mc,
+        reinterpret_cast<float*>(b->d_item_parts), b->d_box_sums, b->d_box_frame, b->d_box_done, b->d_ctas_done,
+        b->d_step, b->d_err);
     return cudaGetLastError();
 }
 
@@ -626,7 +641,7 @@ int lbm_batch_deformation(lbm_batch* b, double* D, double* axes, double* centre)
     int st = batch_init(b);
     if (st) return st;
     k_batch_moments<<<dim3(b->mblocks, b->nbox), 256, 0, b->stream>>>(b->d_boxes, b->parity, b->d_mparts);
-    k_batch_moments_final<<<b->nbox, 32, 0, b->stream>>>(b->d_mparts, b->mblocks, b->d_result, nullptr);
+    k_batch_moments_final<<<b->nbox, 32, 0, b->stream>>>(b->d_mparts, b->mblocks, b->d_result, nullptr, nullptr);
     BATCH_TRY(cudaGetLastError());
     BATCH_TRY(cudaMemcpyAsync(b->h_result, b->d_result, sizeof(double) * 26 * b->nbox, cudaMemcpyDeviceToHost,
                               b->stream));
@@ -646,7 +661,7 @@ int lbm_batch_moments(lbm_batch* b, double* m) {
     int st = batch_init(b);
     if (st) return st;
     k_batch_moments<<<dim3(b->mblocks, b->nbox), 256, 0, b->stream>>>(b->d_boxes, b->parity, b->d_mparts);
-    k_batch_moments_final<<<b->nbox, 32, 0, b->stream>>>(b->d_mparts, b->mblocks, b->d_result, nullptr);
+    k_batch_moments_final<<<b->nbox, 32, 0, b->stream>>>(b->d_mparts, b->mblocks, b->d_result, nullptr, nullptr);
     BATCH_TRY(cudaGetLastError());
     BATCH_TRY(cudaMemcpyAsync(b->h_result, b->d_result, sizeof(double) * 26 * b->nbox, cudaMemcpyDeviceToHost,
                               b->stream));
@@ -688,7 +703,8 @@ int lbm_batch_set_populations(lbm_batch* b, int32_t box, const double* f) {
     // refresh every box's frame origin from the stored populations
     if (e == cudaSuccess) {
         k_batch_moments<<<dim3(b->mblocks, b->nbox), 256, 0, b->stream>>>(b->d_boxes, b->parity, b->d_mparts);
-        k_batch_moments_final<<<b->nbox, 32, 0, b->stream>>>(b->d_mparts, b->mblocks, b->d_result, b->d_box_sums);
+        k_batch_moments_final<<<b->nbox, 32, 0, b->stream>>>(b->d_mparts, b->mblocks, b->d_result, b->d_box_sums,
+                                                         b->d_box_frame);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);

@@ -13,16 +13,20 @@ namespace {
 
 // Fixed-order reduction of the per-CTA centre partials by the last CTA to
 // finish (threadfence-reduction pattern); every thread of the CTA calls it.
-// `scratch` holds 4 doubles per warp of shared memory.
-__device__ void centre_epilogue(double (&cm)[4], CentreParts cp, double* scratch) {
+// C is the reduction type (float32 for the float32 and 16-bit storage
+// kernels, so that they run no FP64 instruction; float64 for the float64
+// kernel).  `scratch` holds 4 values of C per warp of shared memory.
+template <typename C>
+__device__ void centre_epilogue(C (&cm)[4], CentreParts cp, C* scratch) {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = (blockDim.x + 31) >> 5;
     const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+    C* parts = reinterpret_cast<C*>(cp.p);
     __shared__ unsigned last;
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        double a = cm[q];
+        C a = cm[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
         if (lane == 0) scratch[4 * warp + q] = a;
@@ -31,10 +35,10 @@ __device__ void centre_epilogue(double (&cm)[4], CentreParts cp, double* scratch
     if (warp == 0) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            double a = lane < nwarps ? scratch[4 * lane + q] : 0.0;
+            C a = lane < nwarps ? scratch[4 * lane + q] : C(0);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-            if (lane == 0) cp.p[4 * cta + q] = a;
+            if (lane == 0) parts[4 * cta + q] = a;
         }
         if (lane == 0) {
             __threadfence();
@@ -44,10 +48,10 @@ __device__ void centre_epilogue(double (&cm)[4], CentreParts cp, double* scratch
     __syncthreads();
     if (last && warp == 0) {
         __threadfence();
-        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        C s4[4] = {C(0), C(0), C(0), C(0)};
         for (unsigned b = lane; b < total; b += 32)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) s4[q] += __ldcg(cp.p + 4LL * b + q);
+            for (int q = 0; q < 4; ++q) s4[q] += __ldcg(parts + 4LL * b + q);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
 #pragma unroll
@@ -55,10 +59,14 @@ __device__ void centre_epilogue(double (&cm)[4], CentreParts cp, double* scratch
         }
         if (lane == 0) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) cp.sum[q] = s4[q];
+            for (int q = 0; q < 4; ++q) cp.sum[q] = (double)s4[q];
             // frame origin x_c = sum w x / sum w (box centre when there is no droplet)
-            const bool have = s4[0] > 0.0;
-            for (int q = 0; q < 3; ++q) cp.sum[4 + q] = have ? s4[1 + q] / s4[0] : 0.0;
+            const bool have = s4[0] > C(0);
+            for (int q = 0; q < 3; ++q) {
+                const C xc = have ? s4[1 + q] / s4[0] : C(0);
+                cp.sum[4 + q] = (double)xc;
+                cp.frame[q] = (float)xc;
+            }
             *cp.counter = 0u;
         }
     }

@@ -898,7 +898,7 @@ __global__ void __launch_bounds__(TX, MINB)
     constexpr bool DEV = is_dev_t<ST>::value;
     extern __shared__ __align__(128) float2 ring[];  // [S][3][RW], then S mbarriers (staged: see StagedLayout)
     unsigned long long* mbar = reinterpret_cast<unsigned long long*>(ring + S * FL::SLOT);
-    __shared__ double red[4 * ((TX + 31) / 32)];
+    __shared__ float red[4 * ((TX + 31) / 32)];
 
     cg::cluster_group cluster = cg::this_cluster();
     const int x = threadIdx.x;
@@ -1046,7 +1046,9 @@ __global__ void __launch_bounds__(TX, MINB)
                 if constexpr (DEV) {
                     if (hs.thr) st_async_f2(halo_ring + hoff, ha, hb, halo_mbar + mb);
                 } else {
-                    const float v = in && hs.in ? hv : m.rho_b[hs.comp];
+                    // (a select, not an index: a run-time index into the
+                    // kernel's parameters would copy them to local memory)
+                    const float v = in && hs.in ? hv : (hs.comp ? m.rho_b[1] : m.rho_b[0]);
                     const float other = __shfl_xor_sync(0xffffffffu, v, 1);
                     if (hs.thr) st_async_f2(halo_ring + hoff, v, other, halo_mbar + mb);
                 }
@@ -1159,8 +1161,7 @@ __global__ void __launch_bounds__(TX, MINB)
     cluster.sync();
 
     // centre-of-mass partials of the written state (fixed-order reduction)
-    double cmd[4] = {(double)cm[0], (double)cm[1], (double)cm[2], (double)cm[3]};
-    centre_epilogue(cmd, cp, red);
+    centre_epilogue(cm, cp, red);
 }
 
 // ---- Warp-specialised variant: loader and collider threads per row ----
@@ -1216,7 +1217,7 @@ __global__ void __launch_bounds__(2 * TX, MINB)
     extern __shared__ __align__(128) float2 ring[];  // [S][3][RW], then [NP][38][TX] floats, then NBAR mbarriers
     float* pops = reinterpret_cast<float*>(ring + S * WL::SLOT);
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(pops + WL::POPS);
-    __shared__ double red[4 * ((2 * TX + 31) / 32)];
+    __shared__ float red[4 * ((2 * TX + 31) / 32)];
 
     cg::cluster_group cluster = cg::this_cluster();
     const int t = threadIdx.x;
@@ -1349,8 +1350,7 @@ __global__ void __launch_bounds__(2 * TX, MINB)
     cluster.sync();
 
     // centre-of-mass partials of the written state (fixed-order reduction)
-    double cmd[4] = {(double)cm[0], (double)cm[1], (double)cm[2], (double)cm[3]};
-    centre_epilogue(cmd, cp, red);
+    centre_epilogue(cm, cp, red);
 }
 
 // Resident CTAs per SM asked of the compiler (it sets the register budget)

@@ -82,11 +82,17 @@ struct Model {
 // stream-collide kernel (one row per CTA) or by launch_centre.  The last CTA
 // to finish sums the rows in CTA order into `sum` (deterministic) and resets
 // `counter`; the ghost kernel of the next step reads `sum`.
+//
+// The partials are kept in the reduction's own type (float32 for the float32
+// and 16-bit storage kernels, float64 for the float64 kernel: `p` is then
+// read as float[n][4]), so that float32 kernels execute no FP64 instruction,
+// which the FP64 pipe of this GPU runs at 1/64 of the float32 rate.
 struct CentreParts {
-    double* p;          // [n][4]
+    double* p;          // [n][4] partials of the reduction type
     int n;              // CTAs of the stream-collide launch
     double* sum;        // [8]: the four sums, then the frame origin x_c, y_c, z_c
     unsigned* counter;  // CTAs finished, 0 between launches
+    float* frame;       // [3]: x_c, y_c, z_c rounded to float32 (read by the float32 ghost kernels)
 };
 
 // A velocity gradient passed by value, row-major A[3a+b] = d u_a / d x_b.

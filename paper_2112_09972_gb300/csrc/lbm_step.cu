@@ -31,6 +31,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "lbm_internal.h"
 #include "lbm_lattice.cuh"
 #include "lbm_tile.cuh"
@@ -119,24 +121,33 @@ __global__ void k_init_dev(Dev<T>* __restrict__ f, Layout L, double R, double xi
 // Ghost nodes (see shell_node for the face enumeration).  Corner nodes stream
 // into no fluid node and write nothing.
 template <typename S, typename C>
-__global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, Model m, Grad G, CentreParts cp,
+__global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, GhostParams<C> g, CentreParts cp,
                                                int* __restrict__ d_err) {
-    // frame origin: the droplet's centre of mass of the current state
+    // frame origin: the droplet's centre of mass of the current state (its
+    // float32 copy for the float32 kernels)
     C xc = C(0), yc = C(0), zc = C(0);
-    if (m.droplet_frame) {
-        xc = (C)cp.sum[4];
-        yc = (C)cp.sum[5];
-        zc = (C)cp.sum[6];
+    if (g.frame) {
+        if constexpr (std::is_same<C, float>::value) {
+            xc = cp.frame[0];
+            yc = cp.frame[1];
+            zc = cp.frame[2];
+        } else {
+            xc = (C)cp.sum[4];
+            yc = (C)cp.sum[5];
+            zc = (C)cp.sum[6];
+        }
     }
+    // x faces: two threads per node (adjacent lanes), each writing half of
+    // every padding sector, so that a warp writes 16 whole sectors per store
+    const int face = blockIdx.z;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int half = face < 2 ? (a & 1) : -1;
     int x, y, z;
-    if (!shell_node(L, blockIdx.z, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y, x,
-                    y, z))
-        return;
-    C A[9];
-#pragma unroll
-    for (int j = 0; j < 9; ++j) A[j] = (C)G.a[j];
-    if constexpr (is_dev_t<S>::value) ghost_node_dev<decltype(dev_tag(S{})), C>(f, L, m, A, xc, yc, zc, x, y, z, d_err);
-    else ghost_node<S, C>(f, L, m, A, xc, yc, zc, x, y, z, d_err);
+    if (!shell_node(L, face, face < 2 ? a >> 1 : a, blockIdx.y * blockDim.y + threadIdx.y, x, y, z)) return;
+    if constexpr (is_dev_t<S>::value)
+        ghost_node_dev<decltype(dev_tag(S{})), C>(f, L, g, xc, yc, zc, x, y, z, half, d_err);
+    else
+        ghost_node<S, C>(f, L, g, xc, yc, zc, x, y, z, half, d_err);
 }
 
 template <typename S, typename C, bool PER, bool MRT, int MAXT>
@@ -149,9 +160,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_stream_collide(const S* __restrict_
     C cm[4] = {C(0), C(0), C(0), C(0)};
     tile_march<S, C, PER, MRT>(src, dst, L, m, TX, TY, blockIdx.x * TX, blockIdx.y * TY, zc0, zc1,
                           reinterpret_cast<C*>(smem_raw), d_err, cm);
-    double cmd[4] = {(double)cm[0], (double)cm[1], (double)cm[2], (double)cm[3]};
     __syncthreads();  // the ring is reused as reduction scratch
-    centre_epilogue(cmd, cp, reinterpret_cast<double*>(smem_raw));
+    centre_epilogue(cm, cp, reinterpret_cast<C*>(smem_raw));
 }
 
 // Centre-of-mass partials of the stored populations (the first step's frame
@@ -332,14 +342,18 @@ cudaError_t launch_init(int prec, void* f, const Layout& L, double R, double xi,
 
 cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Grad A, CentreParts cp, int* d_err,
                          cudaStream_t s) {
-    const int fast = (L.Lx > L.Ly + 2 ? L.Lx : L.Ly + 2);
+    const int fast = (L.Lx > 2 * (L.Ly + 2) ? L.Lx : 2 * (L.Ly + 2));  // x faces: two threads per node
     const int slow = (L.Lz + 2 > L.Ly ? L.Lz + 2 : L.Ly);
     const dim3 block(32, 8, 1);
     const dim3 grid((fast + 31) / 32, (slow + 7) / 8, 6);
-    if (prec == kFP64) k_ghost<double, double><<<grid, block, 0, s>>>((double*)f, L, m, A, cp, d_err);
-    else if (prec == kFP32) k_ghost<float, float><<<grid, block, 0, s>>>((float*)f, L, m, A, cp, d_err);
-    else if (prec == kFP16Dev) k_ghost<Dev<__half>, float><<<grid, block, 0, s>>>((Dev<__half>*)f, L, m, A, cp, d_err);
-    else k_ghost<Dev<__nv_bfloat16>, float><<<grid, block, 0, s>>>((Dev<__nv_bfloat16>*)f, L, m, A, cp, d_err);
+    if (prec == kFP64) {
+        k_ghost<double, double><<<grid, block, 0, s>>>((double*)f, L, ghost_params<double>(m, A.a), cp, d_err);
+        return cudaGetLastError();
+    }
+    const GhostParams<float> g = ghost_params<float>(m, A.a);
+    if (prec == kFP32) k_ghost<float, float><<<grid, block, 0, s>>>((float*)f, L, g, cp, d_err);
+    else if (prec == kFP16Dev) k_ghost<Dev<__half>, float><<<grid, block, 0, s>>>((Dev<__half>*)f, L, g, cp, d_err);
+    else k_ghost<Dev<__nv_bfloat16>, float><<<grid, block, 0, s>>>((Dev<__nv_bfloat16>*)f, L, g, cp, d_err);
     return cudaGetLastError();
 }
 

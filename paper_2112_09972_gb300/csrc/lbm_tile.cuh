@@ -5,6 +5,10 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <cstring>
+#include <limits>
+
 #include "lbm_dev.cuh"
 #include "lbm_internal.h"
 #include "lbm_centre.cuh"
@@ -259,34 +263,69 @@ __device__ __forceinline__ void tile_march(const S* __restrict__ src, S* __restr
     }
 }
 
-// One 32-byte sector (8 floats or 4 doubles, 32-byte aligned) holding v at
-// position `lane` and zeros elsewhere, in two 16-byte stores.
-template <typename S>
-__device__ __forceinline__ void store_sector(S* p, int lane, S v);
-template <>
-__device__ __forceinline__ void store_sector<float>(float* p, int lane, float v) {
-    float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+// Half h (0 or 1) of a 32-byte sector (32-byte aligned, elements of 4 or 8
+// bytes) that holds the bits v at element `lane` and zeros elsewhere: one
+// 16-byte store.  Two threads of a warp that write the two halves in the
+// same instruction write the sector in one request.
+template <typename E>
+__device__ __forceinline__ void store_half_sector(E* sector, int lane, E v, int h) {
+    static_assert(sizeof(E) == 4 || sizeof(E) == 8, "4- or 8-byte elements");
+    constexpr int N = 16 / (int)sizeof(E);
+    E e[N];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) e[k] = k == lane ? v : 0.f;
-    reinterpret_cast<float4*>(p)[0] = make_float4(e[0], e[1], e[2], e[3]);
-    reinterpret_cast<float4*>(p)[1] = make_float4(e[4], e[5], e[6], e[7]);
+    for (int k = 0; k < N; ++k) e[k] = h * N + k == lane ? v : E(0);
+    uint4 w;
+    memcpy(&w, e, 16);
+    reinterpret_cast<uint4*>(sector)[h] = w;
 }
-template <>
-__device__ __forceinline__ void store_sector<double>(double* p, int lane, double v) {
-    double e[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) e[k] = k == lane ? v : 0.0;
-    reinterpret_cast<double2*>(p)[0] = make_double2(e[0], e[1]);
-    reinterpret_cast<double2*>(p)[1] = make_double2(e[2], e[3]);
+// The whole sector from one thread (both halves); half < 0 in the ghost
+// kernels below.
+template <typename E>
+__device__ __forceinline__ void store_sector_part(E* sector, int lane, E v, int half) {
+    if (half < 0) {
+        store_half_sector(sector, lane, v, 0);
+        store_half_sector(sector, lane, v, 1);
+    } else {
+        store_half_sector(sector, lane, v, half);
+    }
+}
+
+// Parameters of the ghost kernels in their arithmetic type C, converted once
+// on the host: the float32 ghost kernels then run no FP64 instruction (this
+// GPU's FP64 pipe runs at 1/64 of the float32 rate).
+template <typename C>
+struct GhostParams {
+    C A[9];     // the boundary gradient of the step, row-major
+    C rho_b[2]; // ghost densities
+    C mach2;    // |u|^2 above this sets the Mach flag
+    int frame;  // 1: the flow is centred on the droplet's centre of mass
+};
+// mach2 for type C: in float32 the largest float not above the double guard
+// g, so that for every float u, u > mach2 exactly when (double)u > g.
+template <typename C>
+GhostParams<C> ghost_params(const Model& m, const double (&A)[9]) {
+    GhostParams<C> p;
+    for (int j = 0; j < 9; ++j) p.A[j] = (C)A[j];
+    for (int s = 0; s < 2; ++s) p.rho_b[s] = (C)m.rho_b[s];
+    C g = (C)m.mach2;
+    if ((double)g > m.mach2) g = std::nextafter(g, -std::numeric_limits<C>::infinity());
+    p.mach2 = g;
+    p.frame = m.droplet_frame;
+    return p;
 }
 
 // Ghost populations of shell node (x, y, z) of box L (Eq. 8 at the boundary
 // density and the flow A (p - x_c), p measured from the box centre; Eq. 14):
 // written only for the directions that stream into the box.  Sets error
-// bit 2 when the ghost speed exceeds the Mach guard.
+// bit 2 when the ghost speed exceeds the Mach guard.  half: for an x-face
+// node whose values sit alone in sectors of row padding, the half of each
+// such sector this thread writes (0 or 1, a pair of threads per node), or
+// -1 when the thread writes whole sectors alone; any other ghost value is
+// written by the thread with half <= 0.
 template <typename S, typename C>
-__device__ __forceinline__ void ghost_node(S* __restrict__ f, const Layout& L, const Model& m, const C (&A)[9], C xc,
-                                           C yc, C zc, int x, int y, int z, int* __restrict__ d_err) {
+__device__ __forceinline__ void ghost_node(S* __restrict__ f, const Layout& L, const GhostParams<C>& g, C xc, C yc,
+                                           C zc, int x, int y, int z, int half, int* __restrict__ d_err) {
+    const C (&A)[9] = g.A;
     const C px = (C(x) - C(0.5) * C(L.Lx - 1)) - xc, py = (C(y) - C(0.5) * C(L.Ly - 1)) - yc,
             pz = (C(z) - C(0.5) * C(L.Lz - 1)) - zc;
     const C ux = A[0] * px + A[1] * py + A[2] * pz;
@@ -309,21 +348,24 @@ __device__ __forceinline__ void ghost_node(S* __restrict__ f, const Layout& L, c
         any = true;
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            const S v = (S)feq<C>(i, (C)m.rho_b[s], ux, uy, uz, u2x);
-            if (whole) store_sector<S>(f + L.at(s, i, x, y, z) - lane, lane, v);
-            else f[L.at(s, i, x, y, z)] = v;
+            const S v = (S)feq<C>(i, g.rho_b[s], ux, uy, uz, u2x);
+            if (whole) store_sector_part<S>(f + L.at(s, i, x, y, z) - lane, lane, v, half);
+            else if (half <= 0) f[L.at(s, i, x, y, z)] = v;
         }
     }
-    if (any && (double)usq > m.mach2) atomicOr(d_err, 2);
+    if (any && usq > g.mach2) atomicOr(d_err, 2);
 }
 
 // The same for 16-bit deviation storage: the deviation of each inward ghost
 // population from w_i rho*(y), y = (x, y, z) + c_i the fluid node it streams
-// to (rho* of the state in f).
+// to (rho* of the state in f), both components of a direction in one 32-bit
+// word; x-face words that sit alone in sectors of row padding are written as
+// whole sectors (half as in ghost_node).
 template <typename T, typename C>
-__device__ __forceinline__ void ghost_node_dev(Dev<T>* __restrict__ f, const Layout& L, const Model& m,
-                                               const C (&A)[9], C xc, C yc, C zc, int x, int y, int z,
+__device__ __forceinline__ void ghost_node_dev(Dev<T>* __restrict__ f, const Layout& L, const GhostParams<C>& gp,
+                                               C xc, C yc, C zc, int x, int y, int z, int half,
                                                int* __restrict__ d_err) {
+    const C (&A)[9] = gp.A;
     const C px = (C(x) - C(0.5) * C(L.Lx - 1)) - xc, py = (C(y) - C(0.5) * C(L.Ly - 1)) - yc,
             pz = (C(z) - C(0.5) * C(L.Lz - 1)) - zc;
     const C ux = A[0] * px + A[1] * py + A[2] * pz;
@@ -332,7 +374,11 @@ __device__ __forceinline__ void ghost_node_dev(Dev<T>* __restrict__ f, const Lay
     const C usq = ux * ux + uy * uy + uz * uz;
     const C u2x = C(1.5) * usq;
     const float4* nb = reinterpret_cast<const float4*>(f);
-    unsigned short* d = reinterpret_cast<unsigned short*>(f);
+    unsigned* w32 = reinterpret_cast<unsigned*>(f);
+    // words of a row: x0 padding words, the Lx nodes, padding up to pitch
+    const bool whole = (x == -1 && L.x0 % 8 == 0) ||
+                       (x == L.Lx && (L.x0 + L.Lx) % 8 == 0 && L.pitch >= L.x0 + L.Lx + 8);
+    const int lane = x == -1 ? 7 : 0;  // the word's place in its sector
     bool any = false;
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
@@ -341,13 +387,17 @@ __device__ __forceinline__ void ghost_node_dev(Dev<T>* __restrict__ f, const Lay
         any = true;
         const float4 r = nb[L.dev_node(xi, yi, zi)];
         const C rs[2] = {(C)r.x, (C)r.y};
+        unsigned short h[2];
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            const C g = feq<C>(i, (C)m.rho_b[s], ux, uy, uz, u2x);
-            d[L.dev_at(s, i, x, y, z)] = dev_from_f<T>((float)(g - wgt<C>(i) * rs[s]));
+            const C g = feq<C>(i, gp.rho_b[s], ux, uy, uz, u2x);
+            h[s] = dev_from_f<T>((float)(g - wgt<C>(i) * rs[s]));
         }
+        const unsigned word = (unsigned)h[0] | ((unsigned)h[1] << 16);  // A in the low half
+        if (whole) store_sector_part<unsigned>(w32 + L.dev_word(i, x, y, z) - lane, lane, word, half);
+        else if (half <= 0) w32[L.dev_word(i, x, y, z)] = word;
     }
-    if (any && (double)usq > m.mach2) atomicOr(d_err, 2);
+    if (any && usq > gp.mach2) atomicOr(d_err, 2);
 }
 
 // Shell node of face `face` at face coordinates (a, b), or false when
