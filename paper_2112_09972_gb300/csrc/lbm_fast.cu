@@ -82,11 +82,6 @@ namespace cg = cooperative_groups;
 #ifndef LBM_ROWS_ALTERNATE
 #define LBM_ROWS_ALTERNATE 1
 #endif
-// Staged variant: planes prefetched into L2 ahead of the shared-memory stage
-// copies (0: none).
-#ifndef LBM_ROWS_L2_AHEAD
-#define LBM_ROWS_L2_AHEAD 0
-#endif
 // L2 priority of the outer-halo loads: 0 evict_last, 1 evict_first, 2 evict_normal.
 #ifndef LBM_ROWS_HALO_POLICY
 #define LBM_ROWS_HALO_POLICY 2
@@ -200,14 +195,23 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
                  "l"(src), "r"(bytes), "r"(mbar)
                  : "memory");
 }
-// Prefetch `bytes` (a multiple of 16) from a 16-byte aligned global address
-// into L2.
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
 // Order this thread's earlier generic-proxy accesses to shared memory before
 // later async-proxy (bulk copy) writes to it.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Asynchronous copies of 4 bytes (at a pointer plus an immediate byte
+// offset) and of 16 bytes from global to this thread's shared memory, and the
+// wait for all of this thread's such copies.
+template <int OFF>
+__device__ __forceinline__ void cp_async4(unsigned dst, const void* src, unsigned long long pol) {
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1+%3], 4, %2;" ::"r"(dst), "l"(src), "l"(pol),
+                 "n"(OFF)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(unsigned dst, const void* src, unsigned long long pol) {
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Global loads and stores at a pointer plus an immediate byte offset.  The
 // first read of a plane keeps its lines in L2 (evict_last policy) for the
@@ -397,19 +401,30 @@ struct RowIO<TX, Dev<T>> {
     static __device__ __forceinline__ const char* src_plane(const P3& q) {
         return cz_(I) > 0 ? q.m : (cz_(I) < 0 ? q.p : q.o);
     }
-    // sum_i (w_i rho* + d_i) + f*_0 = f*_0 + (1 - w_0) rho* + sum_i d_i
-    static __device__ __forceinline__ void densities(const P3& q, unsigned long long pol, float& ra, float& rb) {
-        const float4 o = ld_keep_f4(q.o + q.blk, pol);
+    // sum_i (w_i rho* + d_i) + f*_0 = f*_0 + (1 - w_0) rho* + sum_i d_i, from
+    // the node's block o and its pulled words word(integral_constant<int, i>)
+    template <typename W>
+    static __device__ __forceinline__ void sum_words(const float4& o, W&& word, float& ra, float& rb) {
         float da = 0.f, db = 0.f;
         sfor<9>([&](auto K) {
             constexpr int i = 2 * decltype(K)::value + 1;
-            const float2 u = dev_unpack2<T>(ld_keep_u32<woff<i>()>(src_plane<i>(q), pol));
-            const float2 v = dev_unpack2<T>(ld_keep_u32<woff<i + 1>()>(src_plane<i + 1>(q), pol));
+            const float2 u = dev_unpack2<T>(word(std::integral_constant<int, i>{}));
+            const float2 v = dev_unpack2<T>(word(std::integral_constant<int, i + 1>{}));
             da += u.x + v.x;
             db += u.y + v.y;
         });
         ra = o.z + (1.f - wgt<float>(0)) * o.x + da;
         rb = o.w + (1.f - wgt<float>(0)) * o.y + db;
+    }
+    static __device__ __forceinline__ void densities(const P3& q, unsigned long long pol, float& ra, float& rb) {
+        const float4 o = ld_keep_f4(q.o + q.blk, pol);
+        sum_words(
+            o,
+            [&](auto I) {
+                constexpr int i = decltype(I)::value;
+                return ld_keep_u32<woff<i>()>(src_plane<i>(q), pol);
+            },
+            ra, rb);
     }
     static __device__ __forceinline__ void populations(const P3& q, float (&f)[2][19]) {
         const float4 o = ld_last_f4(q.o + q.blk);
@@ -446,6 +461,56 @@ struct RowIO<TX, Dev<T>> {
     template <int I>
     static __device__ __forceinline__ void store_word(Out o, unsigned v) {
         st_cs_u32<4 * (3 + I) * G::PITCH>(o.w, v);
+    }
+};
+
+// Outer-halo pulls of the staged variant, prefetched into shared memory one
+// march step ahead by asynchronous copies (each halo thread copies the
+// values it sums into its own slots, so no barrier is involved; it waits for
+// its own copies before it sums them, in the order of RowIO::density /
+// RowIO::densities).  Float32: thread x copies the 19 pulled populations of
+// its component, slot [i][x].  Deviations: threads x < TX / 2 copy the
+// node's float4 block (slot [x]) and its 18 pulled words (slots [i - 1][x]).
+template <int TX, typename ST>
+struct HaloPrefetch;
+template <int TX>
+struct HaloPrefetch<TX, float> {
+    using IO = RowIO<TX, float>;
+    static constexpr unsigned BYTES = 19u * 4u * TX;
+    static __device__ __forceinline__ void issue(const typename IO::P3& q, unsigned long long pol, unsigned buf,
+                                                 int x) {
+        sfor<19>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            cp_async4<IO::template poff<0, i>()>(buf + 4u * (unsigned)(i * TX + x), IO::template src_plane<i>(q), pol);
+        });
+    }
+    static __device__ __forceinline__ float sum(const float* buf, int x) {
+        const float* b = buf + x;
+        float r = b[0];
+#pragma unroll
+        for (int i = 1; i < 19; i += 2) r += b[i * TX] + b[(i + 1) * TX];
+        return r;
+    }
+};
+template <int TX, typename T>
+struct HaloPrefetch<TX, Dev<T>> {
+    using IO = RowIO<TX, Dev<T>>;
+    static constexpr int NT = TX / 2;  // halo threads
+    static constexpr unsigned BYTES = 16u * NT + 18u * 4u * NT;
+    static __device__ __forceinline__ void issue(const typename IO::P3& q, unsigned long long pol, unsigned buf,
+                                                 int x) {
+        cp_async16(buf + 16u * (unsigned)x, q.o + q.blk, pol);
+        sfor<18>([&](auto K) {
+            constexpr int i = decltype(K)::value + 1;
+            cp_async4<IO::template woff<i>()>(buf + 16u * NT + 4u * (unsigned)((i - 1) * NT + x),
+                                              IO::template src_plane<i>(q), pol);
+        });
+    }
+    static __device__ __forceinline__ void sum(const float* buf, int x, float& ra, float& rb) {
+        const float4 o = reinterpret_cast<const float4*>(buf)[x];
+        const unsigned* w = reinterpret_cast<const unsigned*>(buf + 4 * NT) + x;
+        IO::sum_words(
+            o, [&](auto I) { return w[(decltype(I)::value - 1) * NT]; }, ra, rb);
     }
 };
 
@@ -509,17 +574,6 @@ struct StagePlane<TX, float> {
             bulk_g2s(dst + 4u * (unsigned)(SEG * a + lo + 4), src + L.at(s, i, lo, y - cy, p - cz), len, mbar);
         }
     }
-    // the same population rows into L2 only (a later plane's copies then hit L2)
-    static __device__ __forceinline__ void prefetch(const float* src, const Layout& L, int y, int p, int lane) {
-        for (int a = lane; a < 38; a += 32) {
-            const int s = a / 19, i = a - 19 * s;
-            int cx, cy, cz;
-            dir_rt(i, cx, cy, cz);
-            const int lo = cx > 0 ? -4 : 0;
-            const unsigned len = cx != 0 ? 4u * (TX + 4) : 4u * TX;
-            bulk_prefetch_l2(src + L.at(s, i, lo, y - cy, p - cz), len);
-        }
-    }
     // the node's 38 pulled populations and its densities, summed in the
     // order of RowIO::density
     static __device__ __forceinline__ void load(const float* st, int x, Raw& r, float& ra, float& rb) {
@@ -568,18 +622,6 @@ struct StagePlane<TX, Dev<T>> {
             const unsigned* w = reinterpret_cast<const unsigned*>(src);
             bulk_g2s(dst + NODE_BYTES + 4u * (unsigned)(SEG * (i - 1) + lo + 4), w + L.dev_word(i, lo, y - cy, p - cz),
                      len, mbar);
-        }
-    }
-    static __device__ __forceinline__ void prefetch(const Dev<T>* src, const Layout& L, int y, int p, int lane) {
-        if (lane == 0) {
-            bulk_prefetch_l2(reinterpret_cast<const float4*>(src) + L.dev_node(0, y, p), NODE_BYTES);
-        } else if (lane < 19) {
-            const int i = lane;
-            int cx, cy, cz;
-            dir_rt(i, cx, cy, cz);
-            const int lo = cx > 0 ? -4 : 0;
-            const unsigned len = cx != 0 ? 4u * (TX + 4) : 4u * TX;
-            bulk_prefetch_l2(reinterpret_cast<const unsigned*>(src) + L.dev_word(i, lo, y - cy, p - cz), len);
         }
     }
     static __device__ __forceinline__ void load(const float* st, int x, Raw& r, float& ra, float& rb) {
@@ -640,15 +682,20 @@ struct FastLayout {
 };
 
 // Shared memory of the staged variant beyond the density ring: NST stage
-// mbarriers, then (128-byte aligned) NST plane images.  March plane k lives
-// in stage k mod 2: while plane k is collided (from registers), the copies of
-// planes k + 2 and k + 3 are in flight.
+// mbarriers, then (128-byte aligned) NST plane images, then the outer-halo
+// prefetch slots (HaloPrefetch).  March plane k lives in stage k mod 2: while
+// plane k is collided (from registers), the copies of planes k + 2 and k + 3
+// are in flight, and so are the halo copies of plane k + 2.
 template <int TX, int CY, typename ST>
 struct StagedLayout {
     static constexpr int NST = 2;
     static constexpr size_t mbar_off = FastLayout<TX, CY>::bytes;
     static constexpr size_t stage_off = ((mbar_off + 8 * NST + 127) / 128) * 128;
-    static constexpr size_t bytes = stage_off + (size_t)NST * StagePlane<TX, ST>::SMEM;
+    // the outer-halo prefetch slots (rows up to 128 wide: at 256 they would
+    // halve the resident CTAs per SM)
+    static constexpr bool HALO = TX <= 128;
+    static constexpr size_t halo_off = stage_off + (size_t)NST * StagePlane<TX, ST>::SMEM;
+    static constexpr size_t bytes = halo_off + (HALO ? (size_t)HaloPrefetch<TX, ST>::BYTES : 0);
 };
 
 // Collision of one node from its 38 pulled populations f and the density
@@ -918,6 +965,11 @@ __global__ void __launch_bounds__(TX, MINB)
     const unsigned smbar_s = smem_u32(ring) + (unsigned)SL::mbar_off;
     const unsigned stage_s = smem_u32(ring) + (unsigned)SL::stage_off;
     const float* stage = reinterpret_cast<const float*>(reinterpret_cast<const char*>(ring) + SL::stage_off);
+    // staged variant: the outer-halo prefetch slots
+    using HP = HaloPrefetch<TX, ST>;
+    constexpr bool PREF = STAGED && SL::HALO;
+    const unsigned halo_s = smem_u32(ring) + (unsigned)SL::halo_off;
+    const float* halo_buf = reinterpret_cast<const float*>(reinterpret_cast<const char*>(ring) + SL::halo_off);
 
     // ghost density in every slot (x halo columns keep it for good), barriers
     for (int e = x; e < S * FL::SLOT; e += TX) ring[e] = make_float2(m.rho_b[0], m.rho_b[1]);
@@ -983,14 +1035,7 @@ __global__ void __launch_bounds__(TX, MINB)
             const int p = plane_of(k);
             return k <= n + 1 && p >= 0 && p < L.Lz;
         };
-        // plane k + LBM_ROWS_L2_AHEAD into L2 (warp 0), so that its copy
-        // into a stage, issued that many march steps later, is served by L2
-        auto prefetch = [&](int k) {
-            if constexpr (LBM_ROWS_L2_AHEAD > 0)
-                if (plane_wanted(k)) SP::prefetch(src, L, y, plane_of(k), x);
-        };
         auto fill = [&](int k) {  // warp 0
-            prefetch(k + LBM_ROWS_L2_AHEAD);
             if (!plane_wanted(k)) return;
             const int st = (K0 + k) % NST;
             if (x == 0) {
@@ -1014,6 +1059,18 @@ __global__ void __launch_bounds__(TX, MINB)
         // outer-halo share into the edge CTA's ring.  Ghost densities outside
         // the box.  Every CTA then expects TX_BYTES on its slot barrier.  The
         // staged variant also keeps the node's pulled populations in `carry`.
+        // Staged variant: the outer-halo copies of march plane k into this
+        // thread's prefetch slots (issued one march step before its
+        // densities() call reads them, so a whole collision hides them).
+        auto prefetch_halo = [&](int k) {
+            const int p = plane_of(k);
+            if (!(hs.cta && hs.in && k <= n + 1 && p >= 0 && p < L.Lz)) return;
+            if constexpr (DEV) {
+                if (hs.thr) HP::issue(planes(hbase, p, hs.col), once, halo_s, x);
+            } else {
+                HP::issue(planes(hbase, p, 0), once, halo_s, x);
+            }
+        };
         auto densities = [&](int k, typename SP::Raw* carry) {
             const int p = plane_of(k);
             const int sl = (K0 + k) & (S - 1);
@@ -1022,7 +1079,14 @@ __global__ void __launch_bounds__(TX, MINB)
             // the outer-halo loads first, so that their latency overlaps the rest
             float hv = 0.f, ha = m.rho_b[0], hb = m.rho_b[1];
             if (hs.cta && in && hs.in) {
-                if constexpr (DEV) {
+                if constexpr (PREF) {
+                    cp_async_wait_all();  // this thread's copies of plane k (prefetch_halo)
+                    if constexpr (DEV) {
+                        if (hs.thr) HP::sum(halo_buf, x, ha, hb);
+                    } else {
+                        hv = HP::sum(halo_buf, x);
+                    }
+                } else if constexpr (DEV) {
                     if (hs.thr) IO::densities(planes(hbase, p, hs.col), once, ha, hb);
                 } else {
                     hv = IO::template density<0>(planes(hbase, p, 0), once);
@@ -1054,6 +1118,8 @@ __global__ void __launch_bounds__(TX, MINB)
                 }
             }
             if (x == 0) mbar_expect_tx(mbar_s + mb, FL::TX_BYTES);
+            // the slots are free again (their values went into the pushes above)
+            if constexpr (PREF) prefetch_halo(k + 1);
         };
         // Wait (bounded) until the neighbour rows of march plane k have landed.
         auto wait_rows = [&](int k) {
@@ -1079,10 +1145,10 @@ __global__ void __launch_bounds__(TX, MINB)
             typename SP::Raw cur, nxt;
             if (x < 32) {
                 fence_proxy_async();  // a previous segment read the stages
-                for (int k = 2; k < LBM_ROWS_L2_AHEAD; ++k) prefetch(k);
                 fill(0);
                 fill(1);
             }
+            if constexpr (PREF) prefetch_halo(0);
             densities(0, &nxt);
             __syncthreads();  // march plane 0 read by all: its stage takes plane 2
             if (x < 32) {
