@@ -61,6 +61,7 @@
 #include "lbm_dev.cuh"
 #include "lbm_internal.h"
 #include "lbm_lattice.cuh"
+#include "lbm_pdl.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -691,9 +692,10 @@ struct StagedLayout {
     static constexpr int NST = 2;
     static constexpr size_t mbar_off = FastLayout<TX, CY>::bytes;
     static constexpr size_t stage_off = ((mbar_off + 8 * NST + 127) / 128) * 128;
-    // the outer-halo prefetch slots (rows up to 128 wide: at 256 they would
-    // halve the resident CTAs per SM)
-    static constexpr bool HALO = TX <= 128;
+    // the outer-halo prefetch slots (rows up to 128 wide, and 16-bit storage
+    // at any width: for float32 rows of 256 they would halve the resident
+    // CTAs per SM)
+    static constexpr bool HALO = TX <= 128 || is_dev_t<ST>::value;
     static constexpr size_t halo_off = stage_off + (size_t)NST * StagePlane<TX, ST>::SMEM;
     static constexpr size_t bytes = halo_off + (HALO ? (size_t)HaloPrefetch<TX, ST>::BYTES : 0);
 };
@@ -980,6 +982,7 @@ __global__ void __launch_bounds__(TX, MINB)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     cluster.sync();  // barriers initialised before any remote store arrives
+    pdl_wait();      // the ghost kernel (or the previous step) has completed
 
     // L2 policies: the direct variant's first read of a plane keeps its lines
     // (evict_last) for the second read one plane later; the outer-halo rows
@@ -1212,6 +1215,7 @@ __global__ void __launch_bounds__(TX, MINB)
         __syncthreads();  // the last plane's ring row and stage read by all before the next segment
         K0 += n + 2;
     }
+    pdl_trigger();  // this CTA's march is done: the next step's kernel may start its prologue
     if (bad) atomicOr(d_err, bad);
     // staged variant: copies whose completion lane 0 of warp 0 did not observe
     // (a wait that gave up) are waited for again, bounded, before the CTA exits
@@ -1328,6 +1332,7 @@ __global__ void __launch_bounds__(2 * TX, MINB)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     cluster.sync();  // barriers initialised before any remote store arrives
+    pdl_wait();      // the ghost kernel (or the previous step) has completed
 
     auto planes = [&](const char* b, int p, int col) {
         if constexpr (DEV) return IO::planes(b, L, p, col);
@@ -1411,6 +1416,7 @@ __global__ void __launch_bounds__(2 * TX, MINB)
             mbar_arrive(empty_s + 8u * b);
         }
     }
+    pdl_trigger();  // this CTA's march is done: the next step's kernel may start its prologue
     if (bad) atomicOr(d_err, bad);
     // no CTA leaves while another may still address its shared memory
     cluster.sync();
@@ -1421,8 +1427,9 @@ __global__ void __launch_bounds__(2 * TX, MINB)
 
 // Resident CTAs per SM asked of the compiler (it sets the register budget)
 // for the direct-load variant, per row width; the staged variant holds two
-// plane images (about 53 KB of shared memory at TX = 128, 105 KB at 256),
-// which fit 4 CTAs of 128 threads or 2 of 256 per SM.
+// plane images and the halo slots (float32: about 64 KB of shared memory at
+// TX = 128, 105 KB at 256; 16-bit storage: 42 KB and 82 KB), so 3 CTAs of
+// 128 threads or 2 of 256 fit per SM.
 template <int TX, bool STAGED>
 constexpr int row_min_blocks() {
     if (STAGED) return TX >= 256 ? 2 : 512 / TX;
@@ -1448,13 +1455,14 @@ cudaError_t launch_rows(const void* src, void* dst, const Layout& L, const Model
     cfg.blockDim = dim3(TX, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 1;
     attr[0].val.clusterDim.y = CY;
     attr[0].val.clusterDim.z = 1;
+    attr[1] = pdl_attribute();
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, k, (const S*)src, (S*)dst, L, fm, zchunk, (int)LBM_ROWS_ALTERNATE, cp, d_err);
 }
 
@@ -1523,11 +1531,12 @@ cudaError_t ws_for(bool query, const void* src, void* dst, const Layout& L, cons
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(2 * TX, 1, 1);
     cfg.dynamicSmemBytes = smem;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 1;
     attr[0].val.clusterDim.y = CY;
     attr[0].val.clusterDim.z = 1;
+    attr[1] = pdl_attribute();
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (query) {
@@ -1543,6 +1552,7 @@ cudaError_t ws_for(bool query, const void* src, void* dst, const Layout& L, cons
     const FastModel fm = fast_model(m);
     cfg.gridDim = dim3(1, L.Ly, (L.Lz + zchunk - 1) / zchunk);
     cfg.stream = s;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, k, (const S*)src, (S*)dst, L, fm, zchunk, (int)LBM_ROWS_ALTERNATE, cp, d_err);
 }
 

@@ -35,6 +35,7 @@
 
 #include "lbm_internal.h"
 #include "lbm_lattice.cuh"
+#include "lbm_pdl.cuh"
 #include "lbm_tile.cuh"
 
 namespace lbmgb {
@@ -123,6 +124,11 @@ __global__ void k_init_dev(Dev<T>* __restrict__ f, Layout L, double R, double xi
 template <typename S, typename C>
 __global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, GhostParams<C> g, CentreParts cp,
                                                int* __restrict__ d_err) {
+    // the previous stream-collide launch wrote the frame origin (and, with
+    // deviation storage, the densities read below); then the next
+    // stream-collide launch may start its prologue
+    pdl_wait();
+    pdl_trigger();
     // frame origin: the droplet's centre of mass of the current state (its
     // float32 copy for the float32 kernels)
     C xc = C(0), yc = C(0), zc = C(0);
@@ -260,9 +266,10 @@ Shape choose_shape(const Layout& L, int prec, int periodic, int mrt, int ty_req,
     sh.variant = kRowDirect;
     if (ty_req <= 0 && (!mrt || prec == kFP32) && rows_kernel_applies(L, prec, periodic)) {
         // One CTA per row.  MRT rows: direct loads only.  Automatic choice,
-        // measured on GB300: shared-memory staging, except 16-bit deviation
-        // storage on 256-wide rows, where direct loads are 3 % faster.
-        const int automatic = (is_dev(prec) && L.Lx >= 256) ? kRowDirect : kRowStaged;
+        // measured on GB300: shared-memory staging (at 128^3 fp32 129 us per
+        // launch against 166 us for direct loads; at 256^3 fp16dev 734 us
+        // against 801 us).
+        const int automatic = kRowStaged;
         const int variant = mrt ? kRowDirect
                                 : (variant_req == 1 ? kRowDirect
                                                     : (variant_req == 2 ? kRowStaged
@@ -346,15 +353,20 @@ cudaError_t launch_ghost(int prec, void* f, const Layout& L, const Model& m, Gra
     const int slow = (L.Lz + 2 > L.Ly ? L.Lz + 2 : L.Ly);
     const dim3 block(32, 8, 1);
     const dim3 grid((fast + 31) / 32, (slow + 7) / 8, 6);
-    if (prec == kFP64) {
-        k_ghost<double, double><<<grid, block, 0, s>>>((double*)f, L, ghost_params<double>(m, A.a), cp, d_err);
-        return cudaGetLastError();
-    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1] = {pdl_attribute()};
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (prec == kFP64)
+        return cudaLaunchKernelEx(&cfg, k_ghost<double, double>, (double*)f, L, ghost_params<double>(m, A.a), cp, d_err);
     const GhostParams<float> g = ghost_params<float>(m, A.a);
-    if (prec == kFP32) k_ghost<float, float><<<grid, block, 0, s>>>((float*)f, L, g, cp, d_err);
-    else if (prec == kFP16Dev) k_ghost<Dev<__half>, float><<<grid, block, 0, s>>>((Dev<__half>*)f, L, g, cp, d_err);
-    else k_ghost<Dev<__nv_bfloat16>, float><<<grid, block, 0, s>>>((Dev<__nv_bfloat16>*)f, L, g, cp, d_err);
-    return cudaGetLastError();
+    if (prec == kFP32) return cudaLaunchKernelEx(&cfg, k_ghost<float, float>, (float*)f, L, g, cp, d_err);
+    if (prec == kFP16Dev)
+        return cudaLaunchKernelEx(&cfg, k_ghost<Dev<__half>, float>, (Dev<__half>*)f, L, g, cp, d_err);
+    return cudaLaunchKernelEx(&cfg, k_ghost<Dev<__nv_bfloat16>, float>, (Dev<__nv_bfloat16>*)f, L, g, cp, d_err);
 }
 
 cudaError_t launch_centre(int prec, const void* f, const Layout& L, CentreParts cp, cudaStream_t s) {
