@@ -982,7 +982,7 @@ __global__ void __launch_bounds__(TX, MINB)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     cluster.sync();  // barriers initialised before any remote store arrives
-    pdl_wait();      // the ghost kernel (or the previous step) has completed
+    pdl_wait();      // (a no-op unless launched with the programmatic attribute)
 
     // L2 policies: the direct variant's first read of a plane keeps its lines
     // (evict_last) for the second read one plane later; the outer-halo rows
@@ -1215,7 +1215,7 @@ __global__ void __launch_bounds__(TX, MINB)
         __syncthreads();  // the last plane's ring row and stage read by all before the next segment
         K0 += n + 2;
     }
-    pdl_trigger();  // this CTA's march is done: the next step's kernel may start its prologue
+    pdl_trigger();  // this CTA's march is done: the next step's ghost kernel may launch
     if (bad) atomicOr(d_err, bad);
     // staged variant: copies whose completion lane 0 of warp 0 did not observe
     // (a wait that gave up) are waited for again, bounded, before the CTA exits
@@ -1332,7 +1332,7 @@ __global__ void __launch_bounds__(2 * TX, MINB)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     cluster.sync();  // barriers initialised before any remote store arrives
-    pdl_wait();      // the ghost kernel (or the previous step) has completed
+    pdl_wait();      // (a no-op unless launched with the programmatic attribute)
 
     auto planes = [&](const char* b, int p, int col) {
         if constexpr (DEV) return IO::planes(b, L, p, col);
@@ -1416,7 +1416,7 @@ __global__ void __launch_bounds__(2 * TX, MINB)
             mbar_arrive(empty_s + 8u * b);
         }
     }
-    pdl_trigger();  // this CTA's march is done: the next step's kernel may start its prologue
+    pdl_trigger();  // this CTA's march is done: the next step's ghost kernel may launch
     if (bad) atomicOr(d_err, bad);
     // no CTA leaves while another may still address its shared memory
     cluster.sync();
@@ -1455,14 +1455,16 @@ cudaError_t launch_rows(const void* src, void* dst, const Layout& L, const Model
     cfg.blockDim = dim3(TX, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[2];
+    // (no programmatic-serialization attribute: measured at 128^3, CTAs that
+    // start while the ghost kernel runs are placed unevenly over the SMs and
+    // the step took 212 us instead of 133 us)
+    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 1;
     attr[0].val.clusterDim.y = CY;
     attr[0].val.clusterDim.z = 1;
-    attr[1] = pdl_attribute();
     cfg.attrs = attr;
-    cfg.numAttrs = 2;
+    cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k, (const S*)src, (S*)dst, L, fm, zchunk, (int)LBM_ROWS_ALTERNATE, cp, d_err);
 }
 
@@ -1531,12 +1533,11 @@ cudaError_t ws_for(bool query, const void* src, void* dst, const Layout& L, cons
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(2 * TX, 1, 1);
     cfg.dynamicSmemBytes = smem;
-    cudaLaunchAttribute attr[2];
+    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 1;
     attr[0].val.clusterDim.y = CY;
     attr[0].val.clusterDim.z = 1;
-    attr[1] = pdl_attribute();
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (query) {
@@ -1552,7 +1553,6 @@ cudaError_t ws_for(bool query, const void* src, void* dst, const Layout& L, cons
     const FastModel fm = fast_model(m);
     cfg.gridDim = dim3(1, L.Ly, (L.Lz + zchunk - 1) / zchunk);
     cfg.stream = s;
-    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, k, (const S*)src, (S*)dst, L, fm, zchunk, (int)LBM_ROWS_ALTERNATE, cp, d_err);
 }
 

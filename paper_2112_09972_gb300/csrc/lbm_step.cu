@@ -125,8 +125,7 @@ template <typename S, typename C>
 __global__ void __launch_bounds__(256) k_ghost(S* __restrict__ f, Layout L, GhostParams<C> g, CentreParts cp,
                                                int* __restrict__ d_err) {
     // the previous stream-collide launch wrote the frame origin (and, with
-    // deviation storage, the densities read below); then the next
-    // stream-collide launch may start its prologue
+    // deviation storage, the densities read below)
     pdl_wait();
     pdl_trigger();
     // frame origin: the droplet's centre of mass of the current state (its
