@@ -41,9 +41,11 @@ def test_committed_traffic_entries_are_consistent():
     for key, e in d.items():
         total = e["dram_read_bytes"] + e["dram_write_bytes"]
         assert e["dram_bytes_per_launch"] == total, key
-        # DRAM bytes of a launch are at least its algorithmic bytes, and
-        # within a few per cent of them when nothing is re-read
-        assert 1.0 <= total / e["algorithmic_bytes_per_launch"] < 1.1, key
+        # DRAM bytes of a launch are within a few per cent of its
+        # algorithmic bytes when nothing is re-read; a little below them
+        # when some reads hit lines the previous launch left in L2 (the
+        # ghost values the ghost kernel writes just before)
+        assert 0.95 <= total / e["algorithmic_bytes_per_launch"] < 1.1, key
 
 
 def test_job_rate_counts_every_rank():
