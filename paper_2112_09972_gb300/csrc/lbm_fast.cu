@@ -337,8 +337,10 @@ struct RowIO<TX, float> {
         ra = density<0>(q, pol);
         rb = density<1>(q, pol);
     }
-    // the node's 38 pulled populations (second read, last use)
-    static __device__ __forceinline__ void populations(const P3& q, float (&f)[2][19]) {
+    // the node's 38 pulled populations (second read, last use); rs: unused
+    // in float32 (the deviation forms return the node's rho* there)
+    static __device__ __forceinline__ void populations(const P3& q, float (&f)[2][19], float (&rs)[2]) {
+        rs[0] = rs[1] = 0.f;
         sfor<19>([&](auto I) {
             constexpr int i = decltype(I)::value;
             f[0][i] = ld_last<poff<0, i>()>(src_plane<i>(q));
@@ -347,8 +349,9 @@ struct RowIO<TX, float> {
     }
     // one read of the 38 pulled populations and the densities summed from
     // them in the order of density() (the warp-specialised kernel)
-    static __device__ __forceinline__ void load_all(const P3& q, float (&f)[2][19], float& ra, float& rb) {
-        populations(q, f);
+    static __device__ __forceinline__ void load_all(const P3& q, float (&f)[2][19], float (&rs)[2], float& ra,
+                                                    float& rb) {
+        populations(q, f, rs);
         ra = f[0][0];
         rb = f[1][0];
 #pragma unroll
@@ -427,23 +430,32 @@ struct RowIO<TX, Dev<T>> {
             },
             ra, rb);
     }
-    static __device__ __forceinline__ void populations(const P3& q, float (&f)[2][19]) {
+    // The collision's input in deviation form: f[s][0] the rest population,
+    // f[s][i >= 1] the pulled deviation d_i (the population is
+    // w_i rho*_s + d_i; collide_node folds w_i rho*_s into its constants),
+    // rs the node's rho* of both components.
+    static __device__ __forceinline__ void populations(const P3& q, float (&f)[2][19], float (&rs)[2]) {
         const float4 o = ld_last_f4(q.o + q.blk);
         f[0][0] = o.z;
         f[1][0] = o.w;
+        rs[0] = o.x;
+        rs[1] = o.y;
         sfor<18>([&](auto K) {
             constexpr int i = decltype(K)::value + 1;
             const float2 v = dev_unpack2<T>(ld_last_u32<woff<i>()>(src_plane<i>(q)));
-            f[0][i] = wgt<float>(i) * o.x + v.x;
-            f[1][i] = wgt<float>(i) * o.y + v.y;
+            f[0][i] = v.x;
+            f[1][i] = v.y;
         });
     }
-    // one read of the block and the 18 pulled words: the populations of
+    // one read of the block and the 18 pulled words: the input of
     // populations() and the densities of densities(), with their arithmetic
-    static __device__ __forceinline__ void load_all(const P3& q, float (&f)[2][19], float& ra, float& rb) {
+    static __device__ __forceinline__ void load_all(const P3& q, float (&f)[2][19], float (&rs)[2], float& ra,
+                                                    float& rb) {
         const float4 o = ld_last_f4(q.o + q.blk);
         f[0][0] = o.z;
         f[1][0] = o.w;
+        rs[0] = o.x;
+        rs[1] = o.y;
         float da = 0.f, db = 0.f;
         sfor<9>([&](auto K) {
             constexpr int i = 2 * decltype(K)::value + 1;
@@ -451,10 +463,10 @@ struct RowIO<TX, Dev<T>> {
             const float2 v = dev_unpack2<T>(ld_last_u32<woff<i + 1>()>(src_plane<i + 1>(q)));
             da += u.x + v.x;
             db += u.y + v.y;
-            f[0][i] = wgt<float>(i) * o.x + u.x;
-            f[1][i] = wgt<float>(i) * o.y + u.y;
-            f[0][i + 1] = wgt<float>(i + 1) * o.x + v.x;
-            f[1][i + 1] = wgt<float>(i + 1) * o.y + v.y;
+            f[0][i] = u.x;
+            f[1][i] = u.y;
+            f[0][i + 1] = v.x;
+            f[1][i + 1] = v.y;
         });
         ra = o.z + (1.f - wgt<float>(0)) * o.x + da;
         rb = o.w + (1.f - wgt<float>(0)) * o.y + db;
@@ -592,7 +604,8 @@ struct StagePlane<TX, float> {
             rb += r.f[1][i] + r.f[1][i + 1];
         }
     }
-    static __device__ __forceinline__ void unpack(const Raw& r, float (&f)[2][19]) {
+    static __device__ __forceinline__ void unpack(const Raw& r, float (&f)[2][19], float (&rs)[2]) {
+        rs[0] = rs[1] = 0.f;
 #pragma unroll
         for (int s = 0; s < 2; ++s)
 #pragma unroll
@@ -641,14 +654,17 @@ struct StagePlane<TX, Dev<T>> {
         ra = r.o.z + (1.f - wgt<float>(0)) * r.o.x + da;
         rb = r.o.w + (1.f - wgt<float>(0)) * r.o.y + db;
     }
-    static __device__ __forceinline__ void unpack(const Raw& r, float (&f)[2][19]) {
+    // the collision's input in deviation form (RowIO<TX, Dev<T>>::populations)
+    static __device__ __forceinline__ void unpack(const Raw& r, float (&f)[2][19], float (&rs)[2]) {
         f[0][0] = r.o.z;
         f[1][0] = r.o.w;
+        rs[0] = r.o.x;
+        rs[1] = r.o.y;
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
             const float2 v = dev_unpack2<T>(r.w[i]);
-            f[0][i] = wgt<float>(i) * r.o.x + v.x;
-            f[1][i] = wgt<float>(i) * r.o.y + v.y;
+            f[0][i] = v.x;
+            f[1][i] = v.y;
         }
     }
 };
@@ -713,7 +729,7 @@ struct StagedLayout {
 // bit-identical states.
 template <int TX, typename ST, bool MRT = false>
 __device__ __forceinline__ void collide_node(const float2* rzm, const float2* rz0, const float2* rzp,
-                                             const float (&f)[2][19], const FastModel& m,
+                                             const float (&f)[2][19], const float (&rs)[2], const FastModel& m,
                                              typename RowIO<TX, ST>::Out out, float (&cm)[4], int& bad, float px,
                                              float py, float pz) {
     using IO = RowIO<TX, ST>;
@@ -768,8 +784,12 @@ __device__ __forceinline__ void collide_node(const float2* rzm, const float2* rz
         // 16-bit deviations from w_i times the density of the node each
         // population streams to (this CTA's density planes), the pair of
         // components of one direction in one word
+        // f holds the pulled deviations (f_i = w_i rho*_s + d_i, rs = rho*):
+        // (1 - 1/tau) f_i = (1 - 1/tau) d_i + (1 - 1/tau) w_i rho*_s, whose
+        // second term joins the equilibrium's constant (W1 / W2 below), and
+        // the momentum's opposite-pair differences are those of the d_i
         using T = decltype(dev_tag(ST{}));
-        float ux[2], uy[2], uz[2], base[2], e1[2], e2[2];
+        float ux[2], uy[2], uz[2], base[2], e1[2], e2[2], W1[2], W2[2];
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             ux[s] = fmaf(m.sh[s], acc[1 - s][0], up[0]);
@@ -779,6 +799,9 @@ __device__ __forceinline__ void collide_node(const float2* rzm, const float2* rz
             const float ir = m.inv_tau[s] * rho[s];
             e1[s] = ir * wgt<float>(1);  // axis directions
             e2[s] = ir * wgt<float>(7);  // edge directions
+            const float orr = m.omit[s] * rs[s];
+            W1[s] = orr * wgt<float>(1);
+            W2[s] = orr * wgt<float>(7);
         }
         float others[2] = {0.f, 0.f};
         sfor<9>([&](auto K) {
@@ -786,27 +809,26 @@ __device__ __forceinline__ void collide_node(const float2* rzm, const float2* rz
             // densities of the destinations x + c_i and x - c_i (read again
             // from shared memory rather than held since the force)
             const float2 np = nb(cx_(i), cy_(i), cz_(i)), nm = nb(-cx_(i), -cy_(i), -cz_(i));
-            float da[2], dbv[2], refa[2], refb[2];
+            float da[2], dbv[2];
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 const float cu = (float)cx_(i) * ux[s] + (float)cy_(i) * uy[s] + (float)cz_(i) * uz[s];
                 const float e = i < 7 ? e1[s] : e2[s];
-                const float ev = e * fmaf(4.5f * cu, cu, base[s]);
+                const float ev = fmaf(e, fmaf(4.5f * cu, cu, base[s]), i < 7 ? W1[s] : W2[s]);
                 const float od = (3.f * e) * cu;
                 const float oa = fmaf(m.omit[s], f[s][i], ev + od);
                 const float ob = fmaf(m.omit[s], f[s][i + 1], ev - od);
-                refa[s] = wgt<float>(i) * (s ? np.y : np.x);
-                refb[s] = wgt<float>(i) * (s ? nm.y : nm.x);
-                da[s] = oa - refa[s];
-                dbv[s] = ob - refb[s];
+                // deviations from w_i times the destinations' densities
+                da[s] = fmaf(-wgt<float>(i), s ? np.y : np.x, oa);
+                dbv[s] = fmaf(-wgt<float>(i), s ? nm.y : nm.x, ob);
             }
             const unsigned wa = dev_pack2<T>(da[0], da[1]), wb = dev_pack2<T>(dbv[0], dbv[1]);
             IO::template store_word<i>(out, wa);
             IO::template store_word<i + 1>(out, wb);
             // the values the readers will rebuild, for the mass balance
             const float2 qa = dev_unpack2<T>(wa), qb = dev_unpack2<T>(wb);
-            others[0] += (refa[0] + qa.x) + (refb[0] + qb.x);
-            others[1] += (refa[1] + qa.y) + (refb[1] + qb.y);
+            others[0] += fmaf(wgt<float>(i), np.x, qa.x) + fmaf(wgt<float>(i), nm.x, qb.x);
+            others[1] += fmaf(wgt<float>(i), np.y, qa.y) + fmaf(wgt<float>(i), nm.y, qb.y);
         });
         st_cs_f4(out.b, make_float4(rho[0], rho[1], rho[0] - others[0], rho[1] - others[1]));
     } else {
@@ -1129,12 +1151,12 @@ __global__ void __launch_bounds__(TX, MINB)
             const unsigned par = (unsigned)((K0 + k) / S) & 1u;
             if (!wait_bounded(mbar_s + 8u * ((K0 + k) & (S - 1)), par, true, kWaitNs)) atomicOr(d_err, 4);
         };
-        auto collide = [&](int k, const float (&f)[2][19]) {
+        auto collide = [&](int k, const float (&f)[2][19], const float (&rs)[2]) {
             const int z = plane_of(k);
             const float2* rprev = ring + ((K0 + k - 1) & (S - 1)) * FL::SLOT + x + 1;
             const float2* rcur = ring + ((K0 + k) & (S - 1)) * FL::SLOT + x + 1;
             const float2* rnext = ring + ((K0 + k + 1) & (S - 1)) * FL::SLOT + x + 1;
-            collide_node<TX, ST, MRT>(down ? rnext : rprev, rcur, down ? rprev : rnext, f, m,
+            collide_node<TX, ST, MRT>(down ? rnext : rprev, rcur, down ? rprev : rnext, f, rs, m,
                                       IO::out(dst, L, x, y, z), cm, bad, px, py, (float)z - 0.5f * (float)(L.Lz - 1));
         };
 
@@ -1176,9 +1198,9 @@ __global__ void __launch_bounds__(TX, MINB)
                     fill(k + 3);
                 }
                 wait_rows(k + 1);
-                float f[2][19];
-                SP::unpack(now, f);
-                collide(k, f);
+                float f[2][19], rs[2];
+                SP::unpack(now, f, rs);
+                collide(k, f, rs);
             };
             if constexpr (DEV) {
                 for (int k = 1; k <= n; ++k) {
@@ -1202,11 +1224,11 @@ __global__ void __launch_bounds__(TX, MINB)
                 densities(k + 1, nullptr);
                 // this node's populations for the collision, read while the
                 // neighbour rows of plane k + 1 are in flight
-                float f[2][19];
-                IO::populations(planes(nbase, plane_of(k), x), f);
+                float f[2][19], rs[2];
+                IO::populations(planes(nbase, plane_of(k), x), f, rs);
                 __syncthreads();  // own row of plane k + 1 complete
                 wait_rows(k + 1);
-                collide(k, f);
+                collide(k, f, rs);
                 // Before a later plane reuses this plane's own-row slot, all
                 // threads must be done reading it: the __syncthreads of the
                 // next iterations (S - 1 march planes apart) order that.
@@ -1266,7 +1288,7 @@ struct WsLayout {
     static constexpr int S = 2 * CY + 2;
     static constexpr int NP = 2;
     static constexpr int SLOT = 3 * RW;           // float2 per slot
-    static constexpr int POPS = NP * 38 * TX;     // [buffer][s * 19 + i][x] floats
+    static constexpr int POPS = NP * 40 * TX;     // [buffer][s * 19 + i][x] floats, then rho* [2][x]
     static constexpr unsigned TX_BYTES = 2u * TX * 8u;
     static constexpr int NBAR = S + 2 * NP;
     static constexpr size_t bytes = sizeof(float2) * S * SLOT + sizeof(float) * POPS + sizeof(unsigned long long) * NBAR;
@@ -1351,9 +1373,9 @@ __global__ void __launch_bounds__(2 * TX, MINB)
             const int p = plane_of(k);
             const bool in = p >= 0 && p < L.Lz;
             const bool staged = k >= 1 && k <= n;  // a plane this CTA collides
-            float f[2][19];
+            float f[2][19], rs[2];
             float ra = m.rho_b[0], rb = m.rho_b[1];
-            if (in) IO::load_all(planes(nbase, p, x), f, ra, rb);
+            if (in) IO::load_all(planes(nbase, p, x), f, rs, ra, rb);
             float ha = m.rho_b[0], hb = m.rho_b[1];
             if (hthr && in && hin) IO::densities(planes(hbase, p, hcol), keep, ha, hb);  // read again by its own CTA
             // densities first: the colliders of plane k - 1 wait for them
@@ -1376,11 +1398,13 @@ __global__ void __launch_bounds__(2 * TX, MINB)
                     if (!ws_wait(empty_s + 8u * b, (ephase >> b) & 1u, false)) atomicOr(d_err, 4);
                     ephase ^= 1u << b;
                 }
-                float* P = pops + (size_t)b * 38 * TX;
+                float* P = pops + (size_t)b * 40 * TX;
 #pragma unroll
-                for (int s = 0; s < 2; ++s)
+                for (int s = 0; s < 2; ++s) {
 #pragma unroll
                     for (int i = 0; i < 19; ++i) P[(s * 19 + i) * TX + x] = f[s][i];
+                    P[(38 + s) * TX + x] = rs[s];
+                }
                 mbar_arrive(full_s + 8u * b);
             }
         }
@@ -1399,18 +1423,20 @@ __global__ void __launch_bounds__(2 * TX, MINB)
             const int b = (k - 1) % NP;
             if (!ws_wait(full_s + 8u * b, (fphase >> b) & 1u, false)) atomicOr(d_err, 4);
             fphase ^= 1u << b;
-            float f[2][19];
-            const float* P = pops + (size_t)b * 38 * TX;
+            float f[2][19], rs[2];
+            const float* P = pops + (size_t)b * 40 * TX;
 #pragma unroll
-            for (int s = 0; s < 2; ++s)
+            for (int s = 0; s < 2; ++s) {
 #pragma unroll
                 for (int i = 0; i < 19; ++i) f[s][i] = P[(s * 19 + i) * TX + x];
+                rs[s] = P[(38 + s) * TX + x];
+            }
             const int z = plane_of(k);
             const float2* rprev = ring + ((k - 1) % S) * WL::SLOT + x + 1;
             const float2* rcur = ring + (k % S) * WL::SLOT + x + 1;
             const float2* rnext = ring + ((k + 1) % S) * WL::SLOT + x + 1;
-            collide_node<TX, ST>(down ? rnext : rprev, rcur, down ? rprev : rnext, f, m, IO::out(dst, L, x, y, z), cm,
-                                 bad, px, py, (float)z - 0.5f * (float)(L.Lz - 1));
+            collide_node<TX, ST>(down ? rnext : rprev, rcur, down ? rprev : rnext, f, rs, m, IO::out(dst, L, x, y, z),
+                                 cm, bad, px, py, (float)z - 0.5f * (float)(L.Lz - 1));
             // the buffer may take plane k + NP (released after the collision,
             // so that the populations can stay in shared memory until used)
             mbar_arrive(empty_s + 8u * b);
@@ -1509,7 +1535,7 @@ cudaError_t rows_for(bool query, const void* src, void* dst, const Layout& L, co
 }
 
 // Resident CTAs per SM asked of the compiler for the warp-specialised
-// variant (2 TX threads, about 93 KB of shared memory at TX = 128: two CTAs
+// variant (2 TX threads, about 95 KB of shared memory at TX = 128: two CTAs
 // of 256 threads per SM).
 template <int TX>
 constexpr int ws_min_blocks() {
