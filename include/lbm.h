@@ -126,8 +126,9 @@ typedef struct {
                             node's populations carried in registers to its
                             collision), 3 loader and collider threads per row (warp-
                             specialised: each population read once, staged in
-                            shared memory for the collision); 0: automatic;
-                            LBM_EINVAL outside 0..3 */
+                            shared memory for the collision); 0: automatic
+                            (2 for every storage form; 1 when the MRT
+                            collision is selected); LBM_EINVAL outside 0..3 */
     int32_t collision;   /* lbm_collision, default LBM_COLLISION_BGK */
     double mrt_rates[5]; /* MRT rates of the energy, energy-square, energy-flux,
                             stress-partner and third-order moments (s_e, s_eps,
