@@ -330,9 +330,13 @@ int lbm_moments_static(const void* f, int32_t precision, const int32_t box[3], d
  * Batched ensemble: many independent droplet boxes (for deformation
  * statistics over many tracer trajectories, Sec. 6), each a full copy of the
  * single-box method above with its own size, radius and per-step gradient
- * history, advanced together: one ghost launch and one persistent
- * stream-collide launch per step, replayed from a captured CUDA graph.  fp32
- * populations, ghost boundary, the frame of opts->frame.
+ * history, advanced together: one ghost launch and one stream-collide launch
+ * per step, replayed from a captured CUDA graph.  When every box has
+ * Lx <= 64 and Ly a multiple of 8 (and opts->tile_y is 0), the stream-collide
+ * launch is the staged row kernel over the row groups of all boxes, with
+ * rows padded to 64 (lbm_batch_launch_kind 1); otherwise a persistent launch
+ * of the generic tile march over a work list of (box, tile, z chunk) items
+ * (kind 0).  fp32 populations, ghost boundary, the frame of opts->frame.
  * ------------------------------------------------------------------------- */
 typedef struct lbm_batch lbm_batch; /* opaque */
 
@@ -341,8 +345,9 @@ typedef struct lbm_batch lbm_batch; /* opaque */
  * (each 4 .. 1024), R[k] its droplet radius (2 R <= min extent - 2).
  * visc, G as for lbm_create.  opts must ask for LBM_FP32 and the ghost
  * boundary and must give rho_lo > 0 (the ghost density of the droplet
- * component); rho_hi <= 0 means 1.  opts->z_chunk (0: 16) sets the initial
- * z planes per work item.  Each box starts, on first use, at the equilibrium
+ * component); rho_hi <= 0 means 1.  opts->z_chunk (0: 32 for the row kernel,
+ * 16 for the tile march) sets the initial z planes per work item; opts->tile_y
+ * > 0 keeps the tile march.  Each box starts, on first use, at the equilibrium
  * tanh droplet in the flow of its gradient at step 0.
  */
 int lbm_batch_create(lbm_batch** out, int32_t nbox, const int32_t* boxes, const double* R, const double visc[2],
@@ -378,16 +383,23 @@ int lbm_batch_get_populations(lbm_batch* batch, int32_t box, double* f);
 int lbm_batch_set_populations(lbm_batch* batch, int32_t box, const double* f);
 
 /*
- * Time trial_steps steps for each candidate work-list shape (z planes per
- * item in {8, 16, 32, 64}, CTAs per SM in {all that fit, 2, 4}) and keep the
+ * Time trial_steps steps for each candidate work-list shape (tile march: z
+ * planes per item in {8, 16, 32, 64}, CTAs per SM in {all that fit, 2, 4};
+ * row kernel: z planes per chunk in {16, 22, 32, 43, 64}) and keep the
  * fastest.  Only before the first step: the trials run from the initial
  * state, which is restored afterwards (LBM_EINVAL once stepping started).
  * The chosen values are returned in *zchunk and *ctas_per_sm (0 = all that fit).
  */
 int lbm_batch_autotune(lbm_batch* batch, int32_t trial_steps, int32_t* zchunk, int32_t* ctas_per_sm);
 
-/* Work-list shape in use: z planes per item, persistent CTAs, work items. */
+/* Work-list shape in use: z planes per item, CTAs of the stream-collide
+ * launch, work items (tile march: (box, tile, z chunk) items; row kernel:
+ * row groups of 8 rows). */
 int lbm_batch_shape(lbm_batch* batch, int32_t* zchunk, int32_t* ctas, int32_t* items);
+
+/* The stream-collide launch of the ensemble: *kind = 0 the generic tile
+ * march, 1 the row kernel over padded rows.  LBM_EINVAL for NULL. */
+int lbm_batch_launch_kind(lbm_batch* batch, int32_t* kind);
 
 /* Free the ensemble (NULL is allowed). */
 void lbm_batch_destroy(lbm_batch* batch);

@@ -293,6 +293,14 @@ struct lbm_batch {
     int zchunk, ctas_per_sm, grid;
     size_t smem;
     int item_cap;
+    bool prepared;  // the launch tables match zchunk / ctas_per_sm
+    // row-kernel mode (every box fits the padded row geometry): row-group
+    // table, per-box descriptors and centre partials of the batched row launch
+    bool rows;
+    int4* d_groups;
+    RowsBatchBox* d_rbox;
+    float* d_rparts;
+    int rgroups, rmax_chunks;
     // moments
     double* d_mparts;
     double* d_result;
@@ -386,12 +394,22 @@ int lbm_batch_create(lbm_batch** out, int32_t nbox, const int32_t* boxes, const 
         if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) { delete b; return LBM_ECUDA; }
         b->own_stream = true;
     }
-    b->zchunk = o.z_chunk > 0 ? o.z_chunk : 16;
     b->ctas_per_sm = 0;  // 0: as many as fit
+    // the row kernel when every box fits its padded rows (and the tile shape
+    // is left to the library), else the generic tile march
+    b->rows = o.tile_y <= 0;
+    long long rows_total = 0;
+    for (int k = 0; k < nbox; ++k) {
+        b->rows = b->rows && rows_batch_applies(boxes[3 * k], boxes[3 * k + 1], boxes[3 * k + 2]);
+        rows_total += boxes[3 * k + 1];
+    }
+    b->rows = b->rows && rows_total <= 65535;
+    b->zchunk = o.z_chunk > 0 ? o.z_chunk : (b->rows ? 32 : 16);
     b->boxes.resize(nbox);
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < nbox && e == cudaSuccess; ++k) {
-        b->boxes[k].L = make_layout(boxes[3 * k], boxes[3 * k + 1], boxes[3 * k + 2], kFP32);
+        b->boxes[k].L = b->rows ? make_layout_rows(boxes[3 * k], boxes[3 * k + 1], boxes[3 * k + 2])
+                                : make_layout(boxes[3 * k], boxes[3 * k + 1], boxes[3 * k + 2], kFP32);
         const size_t bytes = (size_t)b->boxes[k].L.total * sizeof(float);
         for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
             e = cudaMalloc(&b->boxes[k].f[q], bytes);
@@ -447,6 +465,9 @@ void lbm_batch_destroy(lbm_batch* b) {
     cudaFree(b->d_item_parts);
     cudaFree(b->d_box_sums);
     cudaFree(b->d_box_frame);
+    cudaFree(b->d_groups);
+    cudaFree(b->d_rbox);
+    cudaFree(b->d_rparts);
     cudaFree(b->d_box_done);
     cudaFree(b->d_ctas_done);
     cudaFree(b->d_step);
@@ -473,8 +494,11 @@ void drop_graphs(lbm_batch* b) {
 }
 
 // (Re)build the work list for the current z chunk and CTAs per SM, upload it.
+int prepare_rows(lbm_batch* b);
+
 int prepare_items(lbm_batch* b) {
     BATCH_TRY(cudaStreamSynchronize(b->stream));
+    if (b->rows) return prepare_rows(b);
     std::vector<int> first, count;
     build_items(b, first, count);
     const int n = (int)b->items.size();
@@ -497,12 +521,59 @@ int prepare_items(lbm_batch* b) {
     if (b->ctas_per_sm > 0) per_sm = std::min(per_sm, b->ctas_per_sm);
     b->grid = std::max(1, std::min(n, per_sm * b->num_sms));
     drop_graphs(b);
+    b->prepared = true;
+    return LBM_OK;
+}
+
+// Row-kernel mode: the row groups of every box (largest boxes first, each
+// box's groups contiguous), the boxes' descriptors and their centre-partial
+// slots for the current z chunk.
+int prepare_rows(lbm_batch* b) {
+    const int zc = std::max(1, b->zchunk);
+    std::vector<int> order(b->nbox);
+    for (int k = 0; k < b->nbox; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        const Layout &La = b->boxes[a].L, &Lc = b->boxes[c].L;
+        return (long long)La.Lx * La.Ly * La.Lz > (long long)Lc.Lx * Lc.Ly * Lc.Lz;
+    });
+    std::vector<int4> groups;
+    std::vector<RowsBatchBox> rbox(b->nbox);
+    int part = 0, max_chunks = 1;
+    for (int k : order) {
+        const Layout& L = b->boxes[k].L;
+        const int chunks = (L.Lz + zc - 1) / zc;
+        max_chunks = std::max(max_chunks, chunks);
+        rbox[k].f[0] = b->boxes[k].f[0];
+        rbox[k].f[1] = b->boxes[k].f[1];
+        rbox[k].L = L;
+        rbox[k].ctas = L.Ly * chunks;
+        rbox[k].part0 = part;
+        part += rbox[k].ctas;
+        for (int y0 = 0; y0 < L.Ly; y0 += kRowClusterRows) groups.push_back(make_int4(k, y0, chunks, 0));
+    }
+    cudaFree(b->d_groups);
+    cudaFree(b->d_rbox);
+    cudaFree(b->d_rparts);
+    b->d_groups = nullptr;
+    b->d_rbox = nullptr;
+    b->d_rparts = nullptr;
+    BATCH_TRY(cudaMalloc(&b->d_groups, sizeof(int4) * groups.size()));
+    BATCH_TRY(cudaMalloc(&b->d_rbox, sizeof(RowsBatchBox) * b->nbox));
+    BATCH_TRY(cudaMalloc(&b->d_rparts, sizeof(float) * 4 * (size_t)part));
+    BATCH_TRY(cudaMemcpy(b->d_groups, groups.data(), sizeof(int4) * groups.size(), cudaMemcpyHostToDevice));
+    BATCH_TRY(cudaMemcpy(b->d_rbox, rbox.data(), sizeof(RowsBatchBox) * b->nbox, cudaMemcpyHostToDevice));
+    b->rgroups = (int)groups.size();
+    b->rmax_chunks = max_chunks;
+    b->grid = b->rgroups * kRowClusterRows * max_chunks;
+    b->smem = rows_batch_smem();
+    drop_graphs(b);
+    b->prepared = true;
     return LBM_OK;
 }
 
 int batch_init(lbm_batch* b) {
     if (b->initialised) return LBM_OK;
-    if (b->items.empty()) {
+    if (!b->prepared) {
         const int st = prepare_items(b);
         if (st) return st;
     }
@@ -535,6 +606,19 @@ cudaError_t enqueue_step(lbm_batch* b, int parity) {
     const double zero[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // A comes from the table
     k_batch_ghost<<<ggrid, gblock, 0, b->stream>>>(b->d_boxes, parity, ghost_params<float>(b->model, zero), b->d_A,
                                                    b->A_steps, b->nbox, b->d_box_frame, b->d_step, b->d_err);
+    if (b->rows) {
+        RowsBatch rb;
+        rb.group = b->d_groups;
+        rb.box = b->d_rbox;
+        rb.parts = b->d_rparts;
+        rb.box_done = b->d_box_done;
+        rb.box_sums = b->d_box_sums;
+        rb.box_frame = b->d_box_frame;
+        rb.ctas_done = b->d_ctas_done;
+        rb.d_step = b->d_step;
+        rb.parity = parity;
+        return launch_rows_batch(rb, b->rgroups, b->rmax_chunks, b->zchunk, b->model, b->d_err, b->stream);
+    }
     ModelC<float> mc;
     for (int s = 0; s < 2; ++s) {
         mc.tau[s] = (float)b->model.tau[s];
@@ -714,8 +798,9 @@ int lbm_batch_set_populations(lbm_batch* b, int32_t box, const double* f) {
 int lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, int32_t* zchunk, int32_t* ctas_per_sm) {
     if (!b || trial_steps < 1 || b->step != 0) return LBM_EINVAL;
     cudaSetDevice(b->device);
-    const int zcs[] = {8, 16, 32, 64};
-    const int per[] = {0, 2, 4};
+    // row-kernel mode: z chunks only (one CTA per row and chunk)
+    const std::vector<int> zcs = b->rows ? std::vector<int>{16, 22, 32, 43, 64} : std::vector<int>{8, 16, 32, 64};
+    const std::vector<int> per = b->rows ? std::vector<int>{0} : std::vector<int>{0, 2, 4};
     float best = 1e30f;
     int bz = b->zchunk, bp = b->ctas_per_sm;
     cudaEvent_t e0, e1;
@@ -764,16 +849,24 @@ int lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, int32_t* zchunk, int32
     return LBM_OK;
 }
 
+int lbm_batch_launch_kind(lbm_batch* b, int32_t* kind) {
+    if (!b || !kind) return LBM_EINVAL;
+    *kind = b->rows ? 1 : 0;
+    return LBM_OK;
+}
+
 int lbm_batch_shape(lbm_batch* b, int32_t* zchunk, int32_t* ctas, int32_t* items) {
     if (!b) return LBM_EINVAL;
-    if (b->items.empty()) {
+    if (!b->prepared) {
         cudaSetDevice(b->device);
         const int st = prepare_items(b);
         if (st) return st;
     }
     if (zchunk) *zchunk = b->zchunk;
     if (ctas) *ctas = b->grid;
-    if (items) *items = (int32_t)b->items.size();
+    // work items: the generic march's (box, tile, z chunk) items, or the row
+    // kernel's row groups
+    if (items) *items = b->rows ? (int32_t)b->rgroups : (int32_t)b->items.size();
     return LBM_OK;
 }
 

@@ -11,17 +11,18 @@
 namespace lbmgb {
 namespace {
 
-// Fixed-order reduction of the per-CTA centre partials by the last CTA to
-// finish (threadfence-reduction pattern); every thread of the CTA calls it.
-// C is the reduction type (float32 for the float32 and 16-bit storage
-// kernels, so that they run no FP64 instruction; float64 for the float64
-// kernel).  `scratch` holds 4 values of C per warp of shared memory.
+// Fixed-order reduction of centre partials by the last CTA to finish
+// (threadfence-reduction pattern); every thread of the CTA calls it.  C is
+// the reduction type (float32 for the float32 and 16-bit storage kernels, so
+// that they run no FP64 instruction; float64 for the float64 kernel).  This
+// CTA's partials go to parts[4 slot .. 4 slot + 3]; `total` CTAs share the
+// counter; the last of them sums slots 0 .. total - 1 in order into sum8
+// (the four sums, then x_c, y_c, z_c) and frame (x_c in float32), and resets
+// the counter.  `scratch` holds 4 values of C per warp of shared memory.
 template <typename C>
-__device__ void centre_epilogue(C (&cm)[4], CentreParts cp, C* scratch) {
+__device__ void centre_reduce(C (&cm)[4], C* parts, long long slot, unsigned total, unsigned* counter, double* sum8,
+                              float* frame, C* scratch) {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = (blockDim.x + 31) >> 5;
-    const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    const unsigned total = gridDim.x * gridDim.y * gridDim.z;
-    C* parts = reinterpret_cast<C*>(cp.p);
     __shared__ unsigned last;
     __syncthreads();
 #pragma unroll
@@ -38,11 +39,11 @@ __device__ void centre_epilogue(C (&cm)[4], CentreParts cp, C* scratch) {
             C a = lane < nwarps ? scratch[4 * lane + q] : C(0);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-            if (lane == 0) parts[4 * cta + q] = a;
+            if (lane == 0) parts[4 * slot + q] = a;
         }
         if (lane == 0) {
             __threadfence();
-            last = atomicAdd(cp.counter, 1u) == total - 1 ? 1u : 0u;
+            last = atomicAdd(counter, 1u) == total - 1 ? 1u : 0u;
         }
     }
     __syncthreads();
@@ -59,17 +60,25 @@ __device__ void centre_epilogue(C (&cm)[4], CentreParts cp, C* scratch) {
         }
         if (lane == 0) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) cp.sum[q] = (double)s4[q];
+            for (int q = 0; q < 4; ++q) sum8[q] = (double)s4[q];
             // frame origin x_c = sum w x / sum w (box centre when there is no droplet)
             const bool have = s4[0] > C(0);
             for (int q = 0; q < 3; ++q) {
                 const C xc = have ? s4[1 + q] / s4[0] : C(0);
-                cp.sum[4 + q] = (double)xc;
-                cp.frame[q] = (float)xc;
+                sum8[4 + q] = (double)xc;
+                frame[q] = (float)xc;
             }
-            *cp.counter = 0u;
+            *counter = 0u;
         }
     }
+}
+
+// The same over every CTA of the launch, in CTA order, into CentreParts.
+template <typename C>
+__device__ void centre_epilogue(C (&cm)[4], CentreParts cp, C* scratch) {
+    const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+    centre_reduce(cm, reinterpret_cast<C*>(cp.p), cta, total, cp.counter, cp.sum, cp.frame, scratch);
 }
 
 }  // namespace

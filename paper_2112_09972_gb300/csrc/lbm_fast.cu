@@ -956,10 +956,24 @@ struct MarchPlan {
     }
 };
 
-template <int TX, int CY, int MINB, typename ST, bool STAGED, bool MRT = false>
+// The last CTA of a batched launch advances the device step counter (thread 0).
+__device__ __forceinline__ void rows_batch_count(const RowsBatch& rb) {
+    if (threadIdx.x != 0) return;
+    __threadfence();
+    if (atomicAdd(rb.ctas_done, 1u) == gridDim.x * gridDim.y * gridDim.z - 1u) {
+        *rb.d_step += 1;
+        *rb.ctas_done = 0u;
+    }
+}
+
+// BATCH: the batched ensemble (RowsBatch): the box, its row and z chunk come
+// from the row-group table instead of the launch's single box, nodes at
+// x >= Lx of a padded row are idle (their ring entries hold the ghost
+// density), and the centre of mass is reduced per box.
+template <int TX, int CY, int MINB, typename ST, bool STAGED, bool MRT = false, bool BATCH = false>
 __global__ void __launch_bounds__(TX, MINB)
-    k_stream_collide_rows(const ST* __restrict__ src, ST* __restrict__ dst, Layout L, FastModel m, int zchunk,
-                          int alt, CentreParts cp, int* __restrict__ d_err) {
+    k_stream_collide_rows(const ST* __restrict__ src_p, ST* __restrict__ dst_p, Layout Lp, FastModel m, int zchunk,
+                          int alt, CentreParts cp, int* __restrict__ d_err, RowsBatch bt) {
     using IO = RowIO<TX, ST>;
     using FL = FastLayout<TX, CY>;
     using SP = StagePlane<TX, ST>;
@@ -971,10 +985,30 @@ __global__ void __launch_bounds__(TX, MINB)
     unsigned long long* mbar = reinterpret_cast<unsigned long long*>(ring + S * FL::SLOT);
     __shared__ float red[4 * ((TX + 31) / 32)];
 
+    __shared__ Layout sL;  // BATCH: the box's layout
+
+    // BATCH: this cluster's row group {box, first row, the box's z chunks}; a
+    // cluster beyond its box's chunks leaves at once (all its CTAs together,
+    // before any barrier)
+    int4 gi = make_int4(0, 0, 0, 0);
+    if constexpr (BATCH) {
+        gi = bt.group[blockIdx.y / CY];
+        if ((int)blockIdx.z >= gi.z) {
+            rows_batch_count(bt);
+            return;
+        }
+        if (threadIdx.x == 0) sL = bt.box[gi.x].L;
+        __syncthreads();
+    }
+    const Layout& L = BATCH ? sL : Lp;
+    const ST* __restrict__ src = BATCH ? reinterpret_cast<const ST*>(bt.box[gi.x].f[bt.parity]) : src_p;
+    ST* __restrict__ dst = BATCH ? reinterpret_cast<ST*>(bt.box[gi.x].f[1 - bt.parity]) : dst_p;
+
     cg::cluster_group cluster = cg::this_cluster();
     const int x = threadIdx.x;
     const int rank = (int)cluster.block_rank();  // == blockIdx.y % CY for cluster dims (1, CY, 1)
     const MarchPlan<CY> plan(L, zchunk, alt);
+    const bool xact = !BATCH || x < L.Lx;  // BATCH: a node of the box (not row padding)
 
     const unsigned ring_s = smem_u32(ring);
     const unsigned mbar_s = smem_u32(mbar);
@@ -1035,14 +1069,15 @@ __global__ void __launch_bounds__(TX, MINB)
     int K0 = 0;
     for (int j = 0; j < plan.nseg; ++j) {
         const Segment sg = plan.seg(j);
-        const int y = sg.g * CY + rank;
-        const int Y0 = sg.g * CY;
+        const int Y0 = BATCH ? gi.y : sg.g * CY;
+        const int y = Y0 + rank;
         const int zc0 = sg.z0, zc1 = sg.z1;
         const int n = zc1 - zc0;
         const bool down = sg.down;
         // k-th plane of the segment's march (k = 0 and n + 1 are the halo planes)
         auto plane_of = [&](int k) { return down ? zc1 - k : zc0 - 1 + k; };
         const HS hs(x, rank, Y0, L.Ly);
+        const bool hin = hs.in && (!BATCH || hs.col < L.Lx);  // the halo node lies in the box
         const unsigned halo_ring = cluster_addr(ring_s, hs.rank);
         const unsigned halo_mbar = cluster_addr(mbar_s, hs.rank);
         const char* nbase = IO::base(src, x, y);
@@ -1089,7 +1124,7 @@ __global__ void __launch_bounds__(TX, MINB)
         // densities() call reads them, so a whole collision hides them).
         auto prefetch_halo = [&](int k) {
             const int p = plane_of(k);
-            if (!(hs.cta && hs.in && k <= n + 1 && p >= 0 && p < L.Lz)) return;
+            if (!(hs.cta && hin && k <= n + 1 && p >= 0 && p < L.Lz)) return;
             if constexpr (DEV) {
                 if (hs.thr) HP::issue(planes(hbase, p, hs.col), once, halo_s, x);
             } else {
@@ -1103,7 +1138,7 @@ __global__ void __launch_bounds__(TX, MINB)
             float ra = m.rho_b[0], rb = m.rho_b[1];
             // the outer-halo loads first, so that their latency overlaps the rest
             float hv = 0.f, ha = m.rho_b[0], hb = m.rho_b[1];
-            if (hs.cta && in && hs.in) {
+            if (hs.cta && in && hin) {
                 if constexpr (PREF) {
                     cp_async_wait_all();  // this thread's copies of plane k (prefetch_halo)
                     if constexpr (DEV) {
@@ -1125,6 +1160,11 @@ __global__ void __launch_bounds__(TX, MINB)
                     IO::densities(planes(nbase, p, x), keep, ra, rb);
                 }
             }
+            if constexpr (BATCH)
+                if (!xact) {  // row padding: the ghost density, like the ring's x halo columns
+                    ra = m.rho_b[0];
+                    rb = m.rho_b[1];
+                }
             ring[sl * FL::SLOT + RW + x + 1] = make_float2(ra, rb);
             const unsigned col = 8u * (unsigned)(sl * FL::SLOT + x + 1);  // row -1 of the slot, this column
             const unsigned mb = 8u * sl;
@@ -1137,7 +1177,7 @@ __global__ void __launch_bounds__(TX, MINB)
                 } else {
                     // (a select, not an index: a run-time index into the
                     // kernel's parameters would copy them to local memory)
-                    const float v = in && hs.in ? hv : (hs.comp ? m.rho_b[1] : m.rho_b[0]);
+                    const float v = in && hin ? hv : (hs.comp ? m.rho_b[1] : m.rho_b[0]);
                     const float other = __shfl_xor_sync(0xffffffffu, v, 1);
                     if (hs.thr) st_async_f2(halo_ring + hoff, v, other, halo_mbar + mb);
                 }
@@ -1198,9 +1238,11 @@ __global__ void __launch_bounds__(TX, MINB)
                     fill(k + 3);
                 }
                 wait_rows(k + 1);
-                float f[2][19], rs[2];
-                SP::unpack(now, f, rs);
-                collide(k, f, rs);
+                if (xact) {
+                    float f[2][19], rs[2];
+                    SP::unpack(now, f, rs);
+                    collide(k, f, rs);
+                }
             };
             if constexpr (DEV) {
                 for (int k = 1; k <= n; ++k) {
@@ -1228,7 +1270,7 @@ __global__ void __launch_bounds__(TX, MINB)
                 IO::populations(planes(nbase, plane_of(k), x), f, rs);
                 __syncthreads();  // own row of plane k + 1 complete
                 wait_rows(k + 1);
-                collide(k, f, rs);
+                if (xact) collide(k, f, rs);
                 // Before a later plane reuses this plane's own-row slot, all
                 // threads must be done reading it: the __syncthreads of the
                 // next iterations (S - 1 march planes apart) order that.
@@ -1253,7 +1295,15 @@ __global__ void __launch_bounds__(TX, MINB)
     cluster.sync();
 
     // centre-of-mass partials of the written state (fixed-order reduction)
-    centre_epilogue(cm, cp, red);
+    if constexpr (BATCH) {
+        // the box's centre of mass, in the order of its CTAs (row, z chunk)
+        const RowsBatchBox& B = bt.box[gi.x];
+        centre_reduce(cm, bt.parts + 4LL * B.part0, (long long)(gi.y + rank) * gi.z + blockIdx.z, (unsigned)B.ctas,
+                      bt.box_done + gi.x, bt.box_sums + 8LL * gi.x, bt.box_frame + 4LL * gi.x, red);
+        rows_batch_count(bt);
+    } else {
+        centre_epilogue(cm, cp, red);
+    }
 }
 
 // ---- Warp-specialised variant: loader and collider threads per row ----
@@ -1491,7 +1541,8 @@ cudaError_t launch_rows(const void* src, void* dst, const Layout& L, const Model
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, (const S*)src, (S*)dst, L, fm, zchunk, (int)LBM_ROWS_ALTERNATE, cp, d_err);
+    return cudaLaunchKernelEx(&cfg, k, (const S*)src, (S*)dst, L, fm, zchunk, (int)LBM_ROWS_ALTERNATE, cp, d_err,
+                              RowsBatch{});
 }
 
 template <int TX, int CY, typename S, bool STAGED, bool MRT>
@@ -1522,6 +1573,11 @@ int max_clusters() {
 }
 
 constexpr int kRowCluster = kRowClusterRows;
+
+// The batched ensemble's launch (RowsBatch): float32, staged, rows of width
+// kRowsBatchWidth.
+using RowsBatchKernel = StagedLayout<kRowsBatchWidth, kRowCluster, float>;
+constexpr size_t rows_batch_bytes() { return RowsBatchKernel::bytes; }
 
 template <int TX, typename S, bool STAGED, bool MRT = false>
 cudaError_t rows_for(bool query, const void* src, void* dst, const Layout& L, const Model& m, int zchunk,
@@ -1643,6 +1699,49 @@ __global__ void k_wait_selftest(unsigned long long limit_ns, int arrive) {
 }
 
 }  // namespace
+
+Layout make_layout_rows(int Lx, int Ly, int Lz) {
+    using G = RowGeo<kRowsBatchWidth, float>;
+    Layout L = make_layout(Lx, Ly, Lz, kFP32);  // x0 is G::X0 for float32
+    L.pitch = G::PITCH;
+    L.row = (long long)G::ROW;
+    L.plane = (long long)L.ny * L.row;
+    L.total = (long long)L.nz * L.plane;
+    return L;
+}
+
+bool rows_batch_applies(int Lx, int Ly, int Lz) {
+    return Lx >= 2 && Lx <= kRowsBatchWidth && Ly >= kRowCluster && Ly % kRowCluster == 0 && Lz >= 2;
+}
+
+size_t rows_batch_smem() { return rows_batch_bytes(); }
+
+cudaError_t launch_rows_batch(const RowsBatch& rb, int groups, int max_chunks, int zchunk, const Model& m,
+                              int* d_err, cudaStream_t s) {
+    constexpr int TX = kRowsBatchWidth, CY = kRowCluster;
+    if (groups < 1 || (long long)groups * CY > 65535 || max_chunks < 1 || max_chunks > 65535 || zchunk < 1)
+        return cudaErrorInvalidValue;
+    auto k = k_stream_collide_rows<TX, CY, row_min_blocks<TX, true>(), float, true, false, true>;
+    const size_t smem = rows_batch_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const FastModel fm = fast_model(m);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1, groups * CY, max_chunks);
+    cfg.blockDim = dim3(TX, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = CY;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const Layout L0 = {};
+    return cudaLaunchKernelEx(&cfg, k, (const float*)nullptr, (float*)nullptr, L0, fm, zchunk,
+                              (int)LBM_ROWS_ALTERNATE, CentreParts{}, d_err, rb);
+}
 
 bool rows_kernel_applies(const Layout& L, int prec, int periodic) {
     if ((prec != kFP32 && !is_dev(prec)) || periodic) return false;

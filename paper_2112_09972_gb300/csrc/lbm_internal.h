@@ -150,6 +150,41 @@ cudaError_t launch_stream_collide_rows(int prec, int variant, const void* src, v
                                        const Model& m, const Grad& A, int zchunk, CentreParts cp, int* d_err,
                                        cudaStream_t s);
 
+// ---- the batched ensemble on the row kernel (lbm_fast.cu) ----
+// Every box of the ensemble is laid out with the row geometry of width
+// kRowsBatchWidth (rows padded to that width: Lx <= kRowsBatchWidth, Ly a
+// multiple of kRowClusterRows), float32.  One launch runs the staged row
+// kernel over the row groups of all boxes, stacked along grid y, with z chunks
+// along grid z (boxes with fewer chunks leave the extra clusters idle); each
+// box's centre of mass is reduced by the last of its CTAs, and the last CTA
+// of the launch advances the device step counter.
+constexpr int kRowsBatchWidth = 64;
+struct RowsBatchBox {
+    float* f[2];  // the two population buffers
+    Layout L;     // make_layout_rows
+    int ctas;     // CTAs of the box: Ly x its z chunks
+    int part0;    // its first slot of centre partials
+};
+struct RowsBatch {
+    const int4* group;          // per row group: {box, first row in the box, z chunks of the box, 0}
+    const RowsBatchBox* box;
+    float* parts;               // [slots][4] centre partials (float32)
+    unsigned* box_done;         // [box] CTAs finished, 0 between launches
+    double* box_sums;           // [box][8]: the four sums, then x_c, y_c, z_c
+    float* box_frame;           // [box][4]: x_c, y_c, z_c in float32
+    unsigned* ctas_done;        // CTAs of the launch finished, 0 between launches
+    long long* d_step;          // advanced by the launch's last CTA
+    int parity;                 // the boxes' f[parity] is read, f[1 - parity] written
+};
+// The layout of an Lx x Ly x Lz box with rows padded to kRowsBatchWidth.
+Layout make_layout_rows(int Lx, int Ly, int Lz);
+bool rows_batch_applies(int Lx, int Ly, int Lz);
+// groups: total row groups (grid y / kRowClusterRows); max_chunks: grid z.
+cudaError_t launch_rows_batch(const RowsBatch& rb, int groups, int max_chunks, int zchunk, const Model& m,
+                              int* d_err, cudaStream_t s);
+// Dynamic shared memory of a batched launch (bytes).
+size_t rows_batch_smem();
+
 // ---- launchers (lbm_reduce.cu) ----
 // Ten moments of w = max(phi, 0) and the deformation: result[0..9] moments,
 // [10] D, [11..19] axes (column-major by axis), [20..22] lambda,

@@ -32,6 +32,7 @@ ABI_FUNCTIONS = [
     "lbm_launch_shape", "lbm_launch_variant", "lbm_destroy", "lbm_strerror", "lbm_moments_static",
     "lbm_batch_create", "lbm_batch_set_gradients", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_deformation",
     "lbm_batch_get_populations", "lbm_batch_set_populations", "lbm_batch_autotune", "lbm_batch_shape",
+    "lbm_batch_launch_kind",
     "lbm_batch_destroy", "lbm_batch_moments",
     "lbm_mlp_create", "lbm_mlp_set_normalisation", "lbm_mlp_param_count", "lbm_mlp_get_params",
     "lbm_mlp_set_params", "lbm_mlp_forward", "lbm_mlp_deformation", "lbm_mlp_gradients", "lbm_mlp_train_step",
@@ -115,6 +116,7 @@ def load_library(path=LIB_PATH):
         "lbm_batch_set_populations": (ctypes.c_int, [vp, ctypes.c_int32, _DP]),
         "lbm_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int32, _I32P, _I32P]),
         "lbm_batch_shape": (ctypes.c_int, [vp, _I32P, _I32P, _I32P]),
+        "lbm_batch_launch_kind": (ctypes.c_int, [vp, _I32P]),
         "lbm_batch_destroy": (None, [vp]),
         "lbm_batch_moments": (ctypes.c_int, [vp, _DP]),
         "lbm_mlp_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int32, _I32P, ctypes.c_int32, ctypes.c_uint64,
@@ -362,7 +364,7 @@ class BatchLBM:
     """
 
     def __init__(self, boxes, R, visc, G, rho_lo, rho_hi=0.0, xi=0.0, mach_limit=0.0, stream=None, device=-1,
-                 z_chunk=0, frame="droplet"):
+                 z_chunk=0, frame="droplet", tile_y=0):
         lib = load_library()
         self._lib = lib
         self.boxes = [tuple(int(v) for v in b) for b in boxes]
@@ -377,6 +379,7 @@ class BatchLBM:
         o.cuda_stream = stream
         o.device = int(device)
         o.z_chunk = int(z_chunk)
+        o.tile_y = int(tile_y)  # > 0: the generic tile march even where the row kernel applies
         o.frame = FRAMES[frame]
         flat = (ctypes.c_int32 * (3 * self.nbox))(*[v for b in self.boxes for v in b])
         r = np.ascontiguousarray(np.asarray(R, dtype=np.float64).reshape(self.nbox))
@@ -446,6 +449,12 @@ class BatchLBM:
         _check(self._lib.lbm_batch_shape(self._h, ctypes.byref(zc), ctypes.byref(ctas), ctypes.byref(items)),
                "lbm_batch_shape")
         return zc.value, ctas.value, items.value
+
+    def launch_kind(self):
+        """0: the generic tile march, 1: the row kernel over padded rows."""
+        k = ctypes.c_int32()
+        _check(self._lib.lbm_batch_launch_kind(self._h, ctypes.byref(k)), "lbm_batch_launch_kind")
+        return k.value
 
 
 def _fptr(a):

@@ -1,4 +1,8 @@
-"""The batched ensemble (lbm_batch_*) against the oracle and the single-box path."""
+"""The batched ensemble (lbm_batch_*) against the oracle and the single-box path,
+in both of its launch kinds: the generic tile march (a box with Ly not a
+multiple of 8 selects it) and the row kernel over rows padded to 64 (every
+box Lx <= 64, Ly a multiple of 8; widths below 64 leave idle padding nodes,
+one box is a full-width row, and z chunks are ragged)."""
 
 import numpy as np
 import pytest
@@ -22,19 +26,30 @@ def built():
     return build.build()
 
 
-BOXES = [(24, 24, 20), (20, 18, 22), (16, 16, 16)]
+SETS = {"tile": ([(24, 24, 20), (20, 18, 22), (16, 16, 16)], 0),
+        "rows": ([(24, 24, 20), (40, 16, 18), (16, 8, 12), (64, 8, 9)], 1)}
 
 
-def _histories(nsteps, seed=21):
-    return np.stack([inputs.ou_gradient_history(nsteps, 30.0, 400.0, seed, box_id=k) for k in range(len(BOXES))],
-                    axis=1)
+@pytest.fixture(params=["tile", "rows"])
+def boxes(request):
+    return SETS[request.param]
 
 
-def test_batch_matches_oracle_per_box(built, oracle_mod):
+def _histories(BOXES, nsteps, seed=21):
+    """OU gradients of each box rescaled by Eq. 15 to a boundary speed of 0.1 on
+    its largest edge (the ensemble's driving): strong enough that a wrong
+    frame origin of one box moves its droplet measurably within the test."""
+    return np.stack([inputs.rescale_to_lattice(inputs.ou_gradient_history(nsteps, 30.0, 400.0, seed, box_id=k), 0.1,
+                                               max(b)) for k, b in enumerate(BOXES)], axis=1)
+
+
+def test_batch_matches_oracle_per_box(built, oracle_mod, boxes):
+    BOXES, kind = boxes
     n = 30
-    hist = _histories(n)
+    hist = _histories(BOXES, n)
     R = [min(b) / 5 for b in BOXES]
     bt = BatchLBM(BOXES, R, W.visc, W.G, rho_lo=W.rho_lo, z_chunk=7)
+    assert bt.launch_kind() == kind
     bt.set_gradients(hist)
     f0 = []
     for k, box in enumerate(BOXES):
@@ -51,11 +66,13 @@ def test_batch_matches_oracle_per_box(built, oracle_mod):
         assert rel_linf(bt.populations(k), o.populations()) <= 2e-5, k
 
 
-def test_batch_matches_single_box_contexts(built):
+def test_batch_matches_single_box_contexts(built, boxes):
+    BOXES, kind = boxes
     n = 41
-    hist = _histories(n, seed=5)
+    hist = _histories(BOXES, n, seed=5)
     R = [min(b) / 5 for b in BOXES]
     bt = BatchLBM(BOXES, R, W.visc, W.G, rho_lo=W.rho_lo)
+    assert bt.launch_kind() == kind
     bt.set_gradients(hist)
     bt.step(n)
     D, axes, c = bt.deformation()
@@ -69,8 +86,9 @@ def test_batch_matches_single_box_contexts(built):
         assert rel_linf(bt.populations(k), g.populations()) <= 1e-5
 
 
-def test_batch_graph_replay_is_deterministic(built):
-    hist = _histories(12, seed=9)
+def test_batch_graph_replay_is_deterministic(built, boxes):
+    BOXES, kind = boxes
+    hist = _histories(BOXES, 12, seed=9)
     R = [min(b) / 5 for b in BOXES]
     a = BatchLBM(BOXES, R, W.visc, W.G, rho_lo=W.rho_lo)
     b = BatchLBM(BOXES, R, W.visc, W.G, rho_lo=W.rho_lo)
@@ -83,13 +101,17 @@ def test_batch_graph_replay_is_deterministic(built):
         assert np.array_equal(a.populations(k), b.populations(k))
 
 
-def test_batch_autotune_restores_initial_state(built):
-    hist = _histories(10, seed=2)
+def test_batch_autotune_restores_initial_state(built, boxes):
+    BOXES, kind = boxes
+    hist = _histories(BOXES, 10, seed=2)
     R = [min(b) / 5 for b in BOXES]
     a = BatchLBM(BOXES, R, W.visc, W.G, rho_lo=W.rho_lo)
     a.set_gradients(hist)
     zc, per = a.autotune(trial_steps=2)
-    assert zc in (8, 16, 32, 64) and per in (0, 2, 4)
+    if kind:
+        assert zc in (16, 22, 32, 43, 64) and per == 0
+    else:
+        assert zc in (8, 16, 32, 64) and per in (0, 2, 4)
     a.step(10)
     b = BatchLBM(BOXES, R, W.visc, W.G, rho_lo=W.rho_lo, z_chunk=zc)
     b.set_gradients(hist)
