@@ -288,10 +288,11 @@ def cpu_baseline(w, hist, steps=None):
 
 
 def ensemble_bench(steps, stream, dev):
-    """Droplet trajectories per second: the 512-box ensemble in one persistent
-    launch per step (graph replay, autotuned) against the plain single-box
-    path running the same boxes one after another, and the D difference
-    between the two after `steps` steps."""
+    """Droplet trajectories per second: the 512-box ensemble in one
+    stream-collide launch per step (the staged row kernel over every box's
+    row groups, rows padded to 64; graph replay, z chunk autotuned) against
+    the plain single-box path running the same boxes one after another, and
+    the D difference between the two after `steps` steps."""
     import numpy as np
     import torch
 
@@ -319,6 +320,7 @@ def ensemble_bench(steps, stream, dev):
     t_batch = ev0.elapsed_time(ev1) / 1e3 / steps  # seconds per ensemble step
     D_batch, _, _ = bt.deformation()
     zc_used, ctas, items = bt.shape()
+    bt_kind = bt.launch_kind()
     bt.close()
     # plain path: one box of each edge, timed per step, weighted by the ensemble's mix
     per_edge, D_err = {}, []
@@ -347,6 +349,7 @@ def ensemble_bench(steps, stream, dev):
         "speedup": round(t_plain / t_batch, 2),
         "batched_mlups": round(nodes / t_batch / 1e6, 1),
         "max_rel_D_difference_batched_vs_plain": float(max(D_err)),
+        "launch": "row kernel, padded rows" if bt_kind else "persistent tile march",
         "autotuned": {"z_chunk": zc_used, "ctas_per_sm": per, "ctas": ctas, "items": items},
         "setup_s": round(setup_s, 2),
     }
