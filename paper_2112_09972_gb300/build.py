@@ -19,7 +19,7 @@ LIB = os.path.join(OUT_DIR, "liblbm_gb300.so")
 SOURCES = ["lbm_abi.cu", "lbm_step.cu", "lbm_fast.cu", "lbm_reduce.cu", "lbm_static.cu", "lbm_batch.cu",
            "lbm_mlp.cu", "lbm_mm.cu"]
 HEADERS = ["lbm_internal.h", "lbm_lattice.cuh", "lbm_tile.cuh", "lbm_eigen.cuh", "lbm_dev.cuh", "lbm_centre.cuh",
-           "lbm_pdl.cuh"]
+           "lbm_pdl.cuh", "lbm_ghost.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-O2",
          "-I", os.path.join(ROOT, "include")]

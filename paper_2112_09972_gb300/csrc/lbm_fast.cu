@@ -44,9 +44,9 @@
 // Sums over opposite velocity pairs are differenced first (c_{2k} = -c_{2k-1}),
 // and the equilibria of a pair share their even part.
 //
-// Variants (lbm_opts.row_variant): the direct loads above (the automatic
-// choice); whole pulled rows staged in shared memory by bulk copies
-// (k_stream_collide_rows<..., STAGED = true>); and loader and collider
+// Variants (lbm_opts.row_variant): the direct loads above; whole pulled rows
+// staged in shared memory by bulk copies (k_stream_collide_rows<..., STAGED =
+// true>, the automatic choice); and loader and collider
 // threads per row (k_stream_collide_ws).  All three share collide_node.  The
 // direct variant also has an MRT instance for float32 storage
 // (collide_node<..., MRT = true>).
@@ -700,9 +700,12 @@ struct FastLayout {
 
 // Shared memory of the staged variant beyond the density ring: NST stage
 // mbarriers, then (128-byte aligned) NST plane images, then the outer-halo
-// prefetch slots (HaloPrefetch).  March plane k lives in stage k mod 2: while
-// plane k is collided (from registers), the copies of planes k + 2 and k + 3
-// are in flight, and so are the halo copies of plane k + 2.
+// prefetch slots (HaloPrefetch).  March plane k lives in stage k mod NST:
+// while plane k is collided (from registers), the copies of planes k + 2 ..
+// k + 1 + NST are in flight, and so are the halo copies of plane k + 2.
+// (A third stage was measured: no faster for 16-bit storage, where 128-wide
+// rows keep 4 resident CTAs per SM with it, and slower for float32, where it
+// costs resident CTAs.)
 template <int TX, int CY, typename ST>
 struct StagedLayout {
     static constexpr int NST = 2;
@@ -1065,7 +1068,7 @@ __global__ void __launch_bounds__(TX, MINB)
     unsigned pending = 0u;  // lane 0 of warp 0: stages with copies it has not seen complete
 
     // March plane K (counted over all segments of the CTA) uses ring slot
-    // K mod S, whose barrier's wait parity is (K / S) mod 2, and stage K mod 2.
+    // K mod S, whose barrier's wait parity is (K / S) mod 2, and stage K mod NST.
     int K0 = 0;
     for (int j = 0; j < plan.nseg; ++j) {
         const Segment sg = plan.seg(j);
@@ -1205,27 +1208,27 @@ __global__ void __launch_bounds__(TX, MINB)
         // FastLayout), and the first collision follows the __syncthreads of
         // the step that pushes plane 2.
         if constexpr (STAGED) {
-            // Planes k + 1 .. k + 3 are in the stages or in flight while plane
-            // k is collided from the registers its density pass filled.
+            // Planes k + 1 .. k + 1 + NST are in the stages or in flight while
+            // plane k is collided from the registers its density pass filled.
             typename SP::Raw cur, nxt;
             if (x < 32) {
                 fence_proxy_async();  // a previous segment read the stages
-                fill(0);
-                fill(1);
+#pragma unroll
+                for (int k = 0; k < NST; ++k) fill(k);
             }
             if constexpr (PREF) prefetch_halo(0);
             densities(0, &nxt);
-            __syncthreads();  // march plane 0 read by all: its stage takes plane 2
+            __syncthreads();  // march plane 0 read by all: its stage takes plane NST
             if (x < 32) {
                 fence_proxy_async();
-                fill(2);
+                fill(NST);
             }
             wait_rows(0);
             densities(1, &cur);
             __syncthreads();
             if (x < 32) {
                 fence_proxy_async();
-                fill(3);
+                fill(NST + 1);
             }
             wait_rows(1);
             // one march step: the density pass of plane k + 1 into `next`,
@@ -1235,7 +1238,7 @@ __global__ void __launch_bounds__(TX, MINB)
                 __syncthreads();  // own row of plane k + 1 complete; its stage read by all
                 if (x < 32) {
                     fence_proxy_async();
-                    fill(k + 3);
+                    fill(k + 1 + NST);
                 }
                 wait_rows(k + 1);
                 if (xact) {

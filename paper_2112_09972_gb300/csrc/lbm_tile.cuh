@@ -5,11 +5,10 @@
 
 #include <cuda_runtime.h>
 
-#include <cmath>
 #include <cstring>
-#include <limits>
 
 #include "lbm_dev.cuh"
+#include "lbm_ghost.cuh"
 #include "lbm_internal.h"
 #include "lbm_centre.cuh"
 #include "lbm_lattice.cuh"
@@ -290,30 +289,6 @@ __device__ __forceinline__ void store_sector_part(E* sector, int lane, E v, int 
     }
 }
 
-// Parameters of the ghost kernels in their arithmetic type C, converted once
-// on the host: the float32 ghost kernels then run no FP64 instruction (this
-// GPU's FP64 pipe runs at 1/64 of the float32 rate).
-template <typename C>
-struct GhostParams {
-    C A[9];     // the boundary gradient of the step, row-major
-    C rho_b[2]; // ghost densities
-    C mach2;    // |u|^2 above this sets the Mach flag
-    int frame;  // 1: the flow is centred on the droplet's centre of mass
-};
-// mach2 for type C: in float32 the largest float not above the double guard
-// g, so that for every float u, u > mach2 exactly when (double)u > g.
-template <typename C>
-GhostParams<C> ghost_params(const Model& m, const double (&A)[9]) {
-    GhostParams<C> p;
-    for (int j = 0; j < 9; ++j) p.A[j] = (C)A[j];
-    for (int s = 0; s < 2; ++s) p.rho_b[s] = (C)m.rho_b[s];
-    C g = (C)m.mach2;
-    if ((double)g > m.mach2) g = std::nextafter(g, -std::numeric_limits<C>::infinity());
-    p.mach2 = g;
-    p.frame = m.droplet_frame;
-    return p;
-}
-
 // Ghost populations of shell node (x, y, z) of box L (Eq. 8 at the boundary
 // density and the flow A (p - x_c), p measured from the box centre; Eq. 14):
 // written only for the directions that stream into the box.  Sets error
@@ -325,14 +300,7 @@ GhostParams<C> ghost_params(const Model& m, const double (&A)[9]) {
 template <typename S, typename C>
 __device__ __forceinline__ void ghost_node(S* __restrict__ f, const Layout& L, const GhostParams<C>& g, C xc, C yc,
                                            C zc, int x, int y, int z, int half, int* __restrict__ d_err) {
-    const C (&A)[9] = g.A;
-    const C px = (C(x) - C(0.5) * C(L.Lx - 1)) - xc, py = (C(y) - C(0.5) * C(L.Ly - 1)) - yc,
-            pz = (C(z) - C(0.5) * C(L.Lz - 1)) - zc;
-    const C ux = A[0] * px + A[1] * py + A[2] * pz;
-    const C uy = A[3] * px + A[4] * py + A[5] * pz;
-    const C uz = A[6] * px + A[7] * py + A[8] * pz;
-    const C usq = ux * ux + uy * uy + uz * uz;
-    const C u2x = C(1.5) * usq;
+    const GhostFlow<C> u = ghost_flow<C>(g, L, xc, yc, zc, x, y, z);
     // An x-face ghost sits alone in a 32-byte sector of row padding (x0 is
     // one sector; when Lx fills whole sectors, so is the stretch after the
     // row).  That sector is written whole -- the value and zero padding,
@@ -348,12 +316,12 @@ __device__ __forceinline__ void ghost_node(S* __restrict__ f, const Layout& L, c
         any = true;
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            const S v = (S)feq<C>(i, g.rho_b[s], ux, uy, uz, u2x);
+            const S v = (S)ghost_feq<C>(g, u, i, s);
             if (whole) store_sector_part<S>(f + L.at(s, i, x, y, z) - lane, lane, v, half);
             else if (half <= 0) f[L.at(s, i, x, y, z)] = v;
         }
     }
-    if (any && usq > g.mach2) atomicOr(d_err, 2);
+    if (any && u.usq > g.mach2) atomicOr(d_err, 2);
 }
 
 // The same for 16-bit deviation storage: the deviation of each inward ghost
@@ -365,14 +333,7 @@ template <typename T, typename C>
 __device__ __forceinline__ void ghost_node_dev(Dev<T>* __restrict__ f, const Layout& L, const GhostParams<C>& gp,
                                                C xc, C yc, C zc, int x, int y, int z, int half,
                                                int* __restrict__ d_err) {
-    const C (&A)[9] = gp.A;
-    const C px = (C(x) - C(0.5) * C(L.Lx - 1)) - xc, py = (C(y) - C(0.5) * C(L.Ly - 1)) - yc,
-            pz = (C(z) - C(0.5) * C(L.Lz - 1)) - zc;
-    const C ux = A[0] * px + A[1] * py + A[2] * pz;
-    const C uy = A[3] * px + A[4] * py + A[5] * pz;
-    const C uz = A[6] * px + A[7] * py + A[8] * pz;
-    const C usq = ux * ux + uy * uy + uz * uz;
-    const C u2x = C(1.5) * usq;
+    const GhostFlow<C> u = ghost_flow<C>(gp, L, xc, yc, zc, x, y, z);
     const float4* nb = reinterpret_cast<const float4*>(f);
     unsigned* w32 = reinterpret_cast<unsigned*>(f);
     // words of a row: x0 padding words, the Lx nodes, padding up to pitch
@@ -389,15 +350,12 @@ __device__ __forceinline__ void ghost_node_dev(Dev<T>* __restrict__ f, const Lay
         const C rs[2] = {(C)r.x, (C)r.y};
         unsigned short h[2];
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const C g = feq<C>(i, gp.rho_b[s], ux, uy, uz, u2x);
-            h[s] = dev_from_f<T>((float)(g - wgt<C>(i) * rs[s]));
-        }
+        for (int s = 0; s < 2; ++s) h[s] = ghost_dev<T, C>(ghost_feq<C>(gp, u, i, s), wgt<C>(i), rs[s]);
         const unsigned word = (unsigned)h[0] | ((unsigned)h[1] << 16);  // A in the low half
         if (whole) store_sector_part<unsigned>(w32 + L.dev_word(i, x, y, z) - lane, lane, word, half);
         else if (half <= 0) w32[L.dev_word(i, x, y, z)] = word;
     }
-    if (any && usq > gp.mach2) atomicOr(d_err, 2);
+    if (any && u.usq > gp.mach2) atomicOr(d_err, 2);
 }
 
 // Shell node of face `face` at face coordinates (a, b), or false when

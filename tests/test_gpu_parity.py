@@ -231,10 +231,14 @@ def test_checkpoint_resume_is_bit_identical(built, tmp_path):
     assert e.value.code == -7
 
 
-def test_mach_guard_is_reported_not_faulted(built):
+@pytest.mark.parametrize("box,precision", [((16, 16, 16), "fp32"), ((32, 16, 16), "fp32"), ((32, 16, 16), "fp16dev")])
+def test_mach_guard_is_reported_not_faulted(built, box, precision):
+    """The ghost kernel latches the Mach guard's error, before the generic
+    kernel (16^3) and before the staged row kernel (32 x 16 x 16, float32
+    and 16-bit deviation storage)."""
     w = workloads.C1_PARITY
-    g = DropletLBM((16, 16, 16), 4.0, w.visc, w.G, precision="fp32", rho_lo=w.rho_lo, mach_limit=0.5)
-    g.set_gradient(inputs.simple_shear(0.2), 0)  # |u| = 1.6 at the boundary
+    g = DropletLBM(box, 4.0, w.visc, w.G, precision=precision, rho_lo=w.rho_lo, mach_limit=0.5)
+    g.set_gradient(inputs.simple_shear(0.2), 0)  # |u| >= 1.6 at the boundary
     g.step(2)
     with pytest.raises(LBMError) as e:
         g.sync()
@@ -316,3 +320,4 @@ def test_row_variants_bit_identical(built, oracle_mod, precision, box, z_chunk):
     for other in states[1:]:
         assert np.array_equal(states[0][0], other[0])
         assert states[0][1] == other[1]
+
