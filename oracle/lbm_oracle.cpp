@@ -45,7 +45,9 @@
 // is the BGK operator.
 //
 // Build: g++ -O2 -ffp-contract=off -fopenmp -shared -fPIC (see build.py).
-// Loops over nodes run in parallel over z planes; every node's result is
+// Loops over nodes run in parallel over the rows (z, y) of boxes of at
+// least 32768 nodes; smaller boxes run on one thread, where starting the
+// threads would cost more than the work.  Every node's result is
 // independent of the thread count.  The moment and checksum sums are serial
 // and ordered z, y, x.
 
@@ -58,6 +60,9 @@
 #endif
 
 namespace {
+
+// Whether a loop over the nodes of an Lx x Ly x Lz box is worth threads.
+bool parallel_worth(int Lx, int Ly, int Lz) { return (long long)Ly * Lz > 1 && (long long)Lx * Ly * Lz >= 32768; }
 
 // D3Q19 velocity set, in the order used throughout this repository:
 // rest, the six axis vectors (+x,-x,+y,-y,+z,-z), then the twelve
@@ -193,7 +198,7 @@ struct Oracle {
             }
             return rs[(size_t)(s * N + node(x, y, z))];
         };
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static) if (parallel_worth(L[0], L[1], L[2]))
         for (int z = 0; z < L[2]; ++z)
             for (int y = 0; y < L[1]; ++y)
                 for (int x = 0; x < L[0]; ++x) {
@@ -329,7 +334,7 @@ void orc_step(void* h, const double* A, const double* centre, double* flux_in, d
     }
 
     // (i)+(ii) pull streaming, with ghost equilibria outside the box.
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static) if (parallel_worth(Lx, Ly, Lz))
     for (int z = 0; z < Lz; ++z)
         for (int y = 0; y < Ly; ++y)
             for (int x = 0; x < Lx; ++x) {
@@ -380,7 +385,7 @@ void orc_step(void* h, const double* A, const double* centre, double* flux_in, d
     }
 
     // (iii) densities after streaming.
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static) if (parallel_worth(Lx, Ly, Lz))
     for (int z = 0; z < Lz; ++z)
         for (int y = 0; y < Ly; ++y)
             for (int x = 0; x < Lx; ++x) {
@@ -393,7 +398,7 @@ void orc_step(void* h, const double* A, const double* centre, double* flux_in, d
             }
 
     // (iv)-(vi) force, velocities, collision.
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static) if (parallel_worth(Lx, Ly, Lz))
     for (int z = 0; z < Lz; ++z)
         for (int y = 0; y < Ly; ++y)
             for (int x = 0; x < Lx; ++x) {
